@@ -1,0 +1,225 @@
+/*
+ * plic.h -- C ABI of the GB300 (sm_103a) PLIC library (libplic.so).
+ *
+ * Lehmann & Gekle, "Analytic Solution to the Piecewise Linear Interface
+ * Construction Problem and its Application in Curvature Calculation for
+ * Volume-of-Fluid Simulation Codes", arXiv 2006.12838.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every data pointer is caller-owned DEVICE memory (cudaMalloc'd or a torch
+ *   tensor's storage), contiguous, structure-of-arrays.  The library never
+ *   keeps a pointer after the call returns and allocates nothing; scratch
+ *   memory is passed in as `workspace` (size from plic_workspace_bytes()).
+ * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *   asynchronous on that stream: they return once the kernels are queued.
+ * - Arguments are validated on the host before anything is launched; an
+ *   invalid argument returns PLIC_ERR_ARG (or PLIC_ERR_ALIGN) and launches
+ *   nothing.  A launch failure returns PLIC_ERR_CUDA; the CUDA error text is
+ *   available from plic_last_error() on the calling thread.
+ * - FP32 precisions take float arrays, PLIC_FP64 takes double arrays.
+ * - Fill fields are float, laid out x-fastest: phi[x + nx*(y + ny*z)].
+ *   Interface-cell lists hold int32 linear indices into that layout.
+ * - No entry point throws, blocks on the device, or keeps global state other
+ *   than the thread-local error text; all are safe to call from several host
+ *   threads at once.
+ * - Vectorised loads are used when every array is 16-byte aligned; any other
+ *   alignment takes a scalar-load path of the same kernel (never a CPU path).
+ */
+#ifndef PLIC_H
+#define PLIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PLIC_OK = 0,
+    PLIC_ERR_ARG = 1,          /* bad size, NULL pointer, unknown enum value   */
+    PLIC_ERR_ALIGN = 2,        /* a pointer is not aligned to its element size  */
+    PLIC_ERR_CUDA = 3,         /* a CUDA call failed; see plic_last_error()     */
+    PLIC_ERR_UNSUPPORTED = 4,  /* valid but unsupported combination             */
+    PLIC_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up            */
+} plic_status;
+
+/* The five PLIC inversions compared in Sec. 2.3-2.5 of the paper. */
+typedef enum {
+    PLIC_ANALYTIC = 0,  /* the paper's analytic inversion (Sec. 2.3, Eqs. 11-25)   */
+    PLIC_SZ_ORIG = 1,   /* Scardovelli-Zaleski as implemented by Kawano (Sec. 2.4)  */
+    PLIC_SZ_OPT = 2,    /* the paper's micro-optimised SZ with edge cases (Sec. 2.4) */
+    PLIC_NEWTON = 3,    /* Newton-Raphson for cases (1), (3), (4) (Sec. 2.5)        */
+    PLIC_NESTED = 4     /* nested intervals for cases (3), (4) (Sec. 2.5)           */
+} plic_method;
+
+typedef enum {
+    PLIC_FP32 = 0,           /* float in/out, fast-math solver                      */
+    PLIC_FP32_POLISHED = 1,  /* float in/out, solver + one Newton step on Eq. 10    */
+    PLIC_FP64 = 2            /* double in/out, the solver in double                 */
+} plic_precision;
+
+enum {
+    /* Paper-literal variants: the listing front end V = 1/2 - |V0 - 1/2| and
+     * n2 = |nx|+|ny|+|nz|-n1-n3, the printed iteration counts of the Newton
+     * and nested-interval solvers, no clamp of the SZ asin argument. */
+    PLIC_FLAG_FAITHFUL = 1u,
+    /* Curvature: use the centroid of each neighbour's cut polygon instead of
+     * the foot point of Eq. 36. */
+    PLIC_FLAG_POINT_CENTROID = 2u,
+    /* Curvature: return Eq. 42 as printed (negative for a convex fluid region
+     * with the Parker-Youngs normal); default is -(Eq. 42). */
+    PLIC_FLAG_KAPPA_PAPER_SIGN = 4u,
+    /* Curvature: solve the 5x5 normal equations in FP32 instead of FP64. */
+    PLIC_FLAG_FIT_FP32 = 8u,
+    /* Curvature: solve the 5x5 normal equations in double-float (pairs of FP32
+     * numbers, about 48 significant bits) on the FP32 pipes. */
+    PLIC_FLAG_FIT_DF32 = 16u
+};
+
+/* plic_volume -- forward problem ("inverse PLIC", Sec. 2.2, Eq. 10 with Eqs.
+ * 2-8): V0[i] = volume of {x in [-1/2,1/2]^3 : n_i . x <= d0[i]} for a unit
+ * normal n_i = (nx[i], ny[i], nz[i]).  d0 outside [-L/2, L/2] (L = |n|_1)
+ * gives 0 or 1.  NaN inputs or n = 0 give NaN.
+ * Arrays: nx, ny, nz, d0 (in), V0 (out), n elements each. */
+plic_status plic_volume(const void *nx, const void *ny, const void *nz, const void *d0,
+                        void *V0, int64_t n, plic_precision p, void *stream);
+
+/* plic_offset -- the PLIC problem (Sec. 2, Eq. 1): for each cell, the plane
+ * offset d0[i] in [-L/2, L/2] such that the plane n_i . x = d0[i] cuts the
+ * volume V0[i] in [0, 1] from the unit cube, by solver `m`.  The normal must be
+ * unit length (the analytic, Newton and nested-interval solvers assume it, as
+ * the paper does; SZ normalises by L1 itself).  V0 = 0 / 1 give -L/2 / +L/2.
+ * Invalid cells (NaN input, V0 outside [0,1], n = 0) give NaN and, when
+ * d_invalid_count (device int64, nullable) is given, are added to it.
+ * PLIC_SZ_ORIG reproduces Kawano's -NaN for axis-aligned n with V0 in {0,1}
+ * (Sec. 2.4); those cells are not counted as invalid.
+ * Arrays: nx, ny, nz, V0 (in), d0 (out), n elements each. */
+plic_status plic_offset(const void *nx, const void *ny, const void *nz, const void *V0,
+                        void *d0, int64_t n, plic_method m, plic_precision p, uint32_t flags,
+                        int64_t *d_invalid_count, void *stream);
+
+/* plic_offset_backward -- vector-Jacobian product of plic_offset at its
+ * solution d0 (implicit function theorem on Eq. 1 for unit n):
+ *   g_V0 = g_d0 / A,    g_n = g_d0 * c,
+ * with A the area and c the centroid (cube-centred) of the cut polygon of the
+ * plane n . x = d0.  Cells with A = 0 (V0 in {0,1}) get g_V0 = +inf*g (sign of
+ * g), g_n = g * c.  Arrays: nx, ny, nz, d0, g_d0 (in); g_V0, g_nx, g_ny, g_nz
+ * (out); any output may be NULL to skip it.  FP32 precisions only use float;
+ * PLIC_FP64 uses double. */
+plic_status plic_offset_backward(const void *nx, const void *ny, const void *nz,
+                                 const void *d0, const void *g_d0, void *g_V0, void *g_nx,
+                                 void *g_ny, void *g_nz, int64_t n, plic_precision p,
+                                 void *stream);
+
+/* plic_volume_backward -- vector-Jacobian product of plic_volume (unit n):
+ *   g_d0 = g_V0 * A,    g_n = -g_V0 * A * c.
+ * Arrays: nx, ny, nz, d0, g_V0 (in); g_d0, g_nx, g_ny, g_nz (out, nullable). */
+plic_status plic_volume_backward(const void *nx, const void *ny, const void *nz,
+                                 const void *d0, const void *g_V0, void *g_d0, void *g_nx,
+                                 void *g_ny, void *g_nz, int64_t n, plic_precision p,
+                                 void *stream);
+
+/* vof_interface_compact -- the interface set of the VOF model (Sec. 4.1,
+ * Eq. 33): the linear indices of all cells with 0 < phi < 1 whose 26
+ * neighbours lie inside the field, in ascending order, written to idx
+ * (capacity idx_capacity entries); the count goes to *d_count (device int64).
+ * If the count exceeds idx_capacity, only the first idx_capacity indices are
+ * written and *d_count still holds the full count.
+ * workspace: >= plic_workspace_bytes(PLIC_WS_COMPACT, nx*ny*nz) bytes of device
+ * memory, 256-byte aligned; its contents on entry do not matter.  Fields up to
+ * 2^31 - 1 cells. */
+plic_status vof_interface_compact(const float *phi, int nx, int ny, int nz, int32_t *idx,
+                                  int64_t idx_capacity, int64_t *d_count, void *workspace,
+                                  size_t ws_bytes, void *stream);
+
+/* vof_curvature -- curvature step of Sec. 4.2 with Appendix B, per interface
+ * cell idx[k]: 3^3 stencil -> Parker-Youngs normal (Eq. 38) -> local frame ->
+ * PLIC offsets d0(phi_i, n) of the centre and of every interface neighbour
+ * with the centre normal (Eq. 36), by solver m in FP32 with one Newton polish
+ * -> least-squares paraboloid (Appendix B, FP64 solve unless a FIT flag says
+ * otherwise) -> mean curvature (Eq. 42) into kappa[k].
+ * n_iface: number of list entries (host).  d_n_iface (device int64, nullable):
+ * if given, only the first min(n_iface, *d_n_iface) entries are processed, so
+ * the call can follow vof_interface_compact without a host round trip.
+ * Sign: kappa = -(Eq. 42), positive for a convex fluid region (1/R for a
+ * sphere of radius R); PLIC_FLAG_KAPPA_PAPER_SIGN returns Eq. 42 as printed.
+ * A degenerate normal (zero weighted gradient) or no interface neighbour gives
+ * kappa = 0.  Every listed cell must have its 26 neighbours inside the field
+ * (as vof_interface_compact guarantees); this is not re-checked. */
+plic_status vof_curvature(const float *phi, int nx, int ny, int nz, const int32_t *idx,
+                          int64_t n_iface, const int64_t *d_n_iface, float *kappa,
+                          plic_method m, uint32_t flags, void *stream);
+
+/* vof_curvature_backward -- vector-Jacobian product of vof_curvature with
+ * respect to the fill field: g_phi = d(sum_k g_kappa[k] kappa[k]) / d phi,
+ * with the interface set (idx and the neighbour flags 0 < phi < 1) held fixed.
+ * g_phi is dense (nx*ny*nz floats) and overwritten.  Per interface cell the 27
+ * partial derivatives are written to the workspace and gathered per field
+ * cell, so the result is deterministic (no atomics).
+ * workspace: >= plic_curv_bwd_workspace_bytes(nx*ny*nz, n_iface) bytes,
+ * 256-byte aligned; its contents on entry do not matter. */
+plic_status vof_curvature_backward(const float *phi, int nx, int ny, int nz,
+                                   const int32_t *idx, int64_t n_iface,
+                                   const int64_t *d_n_iface, const float *g_kappa,
+                                   float *g_phi, plic_method m, uint32_t flags,
+                                   void *workspace, size_t ws_bytes, void *stream);
+
+/* One field of a batched curvature call (all pointers device memory). */
+typedef struct {
+    const float *phi;        /* fill field, nx*ny*nz floats                     */
+    int nx, ny, nz;
+    const int32_t *idx;      /* interface-cell list of this field               */
+    int64_t n_iface;         /* entries in idx                                  */
+    float *kappa;            /* output, n_iface floats                          */
+} vof_field;
+
+/* Launch shape of the batched curvature kernel (chosen by an autotuner). */
+typedef struct {
+    int block_threads;       /* threads per block (multiple of 32, <= 1024)     */
+    int cells_per_chunk;     /* interface cells claimed per work-queue ticket   */
+    int blocks_per_sm;       /* resident blocks per SM of the persistent grid   */
+} vof_tuning;
+
+/* vof_curvature_batched -- vof_curvature over many fields of uneven size in
+ * ONE persistent launch: the interface lists are concatenated logically, and
+ * a grid of (#SMs x blocks_per_sm) blocks claims chunks of cells from a
+ * device-side ticket counter until the work is exhausted (no waiting on other
+ * blocks).  `fields` is a HOST array of n_fields descriptors; it is copied to
+ * the workspace before the launch and may be reused once the call returns.
+ * tuning: nullable (defaults are used).  workspace: >=
+ * plic_workspace_bytes(PLIC_WS_BATCHED, n_fields) bytes, 256-byte aligned. */
+plic_status vof_curvature_batched(const vof_field *fields, int n_fields,
+                                  const vof_tuning *tuning, plic_method m, uint32_t flags,
+                                  void *workspace, size_t ws_bytes, void *stream);
+
+/* Workspace kinds for plic_workspace_bytes(). */
+enum {
+    PLIC_WS_COMPACT = 0,     /* arg: number of field cells nx*ny*nz             */
+    PLIC_WS_BATCHED = 2      /* arg: number of fields                           */
+};
+
+/* Workspace bytes for an operation (0 if it needs none). */
+size_t plic_workspace_bytes(int op, int64_t arg);
+
+/* Workspace bytes of vof_curvature_backward for a field of `cells` cells and
+ * an interface list of n_iface entries: a dense int32 slot map of the field
+ * plus 27 floats per interface cell, each part 256-byte aligned. */
+size_t plic_curv_bwd_workspace_bytes(int64_t cells, int64_t n_iface);
+
+/* Human-readable name of a status code (static storage). */
+const char *plic_status_string(plic_status s);
+
+/* Text of the last CUDA error seen on this host thread (static storage of the
+ * thread; empty when none). */
+const char *plic_last_error(void);
+
+/* Library version, for the binding's load check. */
+int plic_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLIC_H */

@@ -1,0 +1,33 @@
+// host_common.h -- host-side helpers shared by the entry points of libplic.so:
+// status/error bookkeeping, argument checks, and launch geometry.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/plic.h"
+
+namespace plic {
+
+// Thread-local text of the last CUDA error (plic_last_error()).
+void set_last_error(const char* where, cudaError_t e);
+
+// Returns PLIC_ERR_CUDA (and records the text) if the last launch failed.
+plic_status check_launch(const char* where);
+
+inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// Blocks of `kernel` that fit on one SM with `threads` threads and `smem` bytes
+// of dynamic shared memory (cached per kernel pointer).
+int blocks_per_sm(const void* kernel, int threads, size_t smem);
+
+// A grid for a grid-stride loop over `work` items of `threads` threads each:
+// min(ceil(work/threads), SMs x resident blocks per SM), at least 1.
+int stride_grid(const void* kernel, int threads, int64_t work, size_t smem = 0);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace plic

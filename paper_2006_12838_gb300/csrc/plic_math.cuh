@@ -1,0 +1,97 @@
+// plic_math.cuh -- scalar math for the PLIC kernels, per precision.
+//
+// Fm<float>  : the FP32 fast path: MUFU-based sin/cos (__sinf/__cosf), MUFU
+//              reciprocal square root, a cube root from the MUFU exp2/log2 pair
+//              refined by one Newton step, and CUDA's asinf/acosf/atanf.
+// Fm<double> : plain double-precision library functions.
+//
+// Constants are written as their closed forms (the decimals printed in the
+// paper's listings are the FP32 roundings of these, Sec. 2.3 Eqs. 13-22).
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace plic {
+
+template <typename T> struct Fm;
+
+template <> struct Fm<float> {
+    typedef float T;
+    static __device__ __forceinline__ T sqrt_(T x) { return sqrtf(x); }
+    static __device__ __forceinline__ T rsqrt_(T x) { return rsqrtf(x); }
+    // Cube root for x >= 0: 2^(log2(x)/3) from the MUFU pair (about 2^-22
+    // relative), then one Newton step on r^3 = x, r <- r - (r^3 - x)/(3 r^2).
+    static __device__ __forceinline__ T cbrt_(T x) {
+        if (!(x > 0.0f)) return 0.0f;
+        float s = 1.0f;
+        if (x < 1e-30f) { x *= 4.7223665e21f; s = 5.9604645e-08f; }   // 2^72, 2^-24
+        float r = exp2f_approx(__log2f_approx(x) * (1.0f / 3.0f));
+        float r2 = r * r;
+        return s * fmaf(-(r2 * r - x), __fdividef(1.0f, 3.0f * r2), r);
+    }
+    static __device__ __forceinline__ T sin_(T x) { return __sinf(x); }
+    static __device__ __forceinline__ T cos_(T x) { return __cosf(x); }
+    static __device__ __forceinline__ T asin_(T x) { return asinf(x); }
+    static __device__ __forceinline__ T acos_(T x) { return acosf(x); }
+    static __device__ __forceinline__ T atan_(T x) { return atanf(x); }
+    static __device__ __forceinline__ T div_(T a, T b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ T fdim_(T a, T b) { return fmaxf(a - b, 0.0f); }
+    static __device__ __forceinline__ T tiny() { return 1.17549435e-38f; }   // FLT_MIN
+    static __device__ __forceinline__ T eps() { return 5.9604645e-08f; }    // 2^-24
+    // number of halvings that shrink a width w to the unit roundoff, as the
+    // nested-interval listing computes it: floor(log2(w * 2^24)) from the
+    // exponent bits (w > 0)
+    static __device__ __forceinline__ int log2_halvings(T w) {
+        return (int)((__float_as_uint(w * 16777216.0f) >> 23) & 0xff) - 127;
+    }
+    static __device__ __forceinline__ float exp2f_approx(float x) {
+        float r;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float __log2f_approx(float x) {
+        float r;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+};
+
+template <> struct Fm<double> {
+    typedef double T;
+    static __device__ __forceinline__ T sqrt_(T x) { return sqrt(x); }
+    static __device__ __forceinline__ T rsqrt_(T x) { return rsqrt(x); }
+    static __device__ __forceinline__ T cbrt_(T x) { return cbrt(x); }
+    static __device__ __forceinline__ T sin_(T x) { return sin(x); }
+    static __device__ __forceinline__ T cos_(T x) { return cos(x); }
+    static __device__ __forceinline__ T asin_(T x) { return asin(x); }
+    static __device__ __forceinline__ T acos_(T x) { return acos(x); }
+    static __device__ __forceinline__ T atan_(T x) { return atan(x); }
+    static __device__ __forceinline__ T div_(T a, T b) { return a / b; }
+    static __device__ __forceinline__ T fdim_(T a, T b) { return fmax(a - b, 0.0); }
+    static __device__ __forceinline__ T tiny() { return 2.2250738585072014e-308; }  // DBL_MIN
+    static __device__ __forceinline__ T eps() { return 1.1102230246251565e-16; }    // 2^-53
+    static __device__ __forceinline__ int log2_halvings(T w) {
+        return (int)((__double_as_longlong(w * 9007199254740992.0) >> 52) & 0x7ff) - 1023;
+    }
+};
+
+// Closed-form constants (Sec. 2.3, Eqs. 13-22; Sec. 2.4).
+template <typename T> struct Kc {
+    static constexpr T two_cbrt54 = (T)7.559526299369239;          // 2 * 54^(1/3)
+    static constexpr T two_over_cbrt432 = (T)0.26456684199469993;  // 2 / 432^(1/3)
+    static constexpr T two_over_cbrt864 = (T)0.20998684164914555;  // 2 / 864^(1/3)
+    static constexpr T two_over_cbrt3456 = (T)0.13228342099734997; // 2 / 3456^(1/3)
+    static constexpr T inv_sqrt12 = (T)0.28867513459481287;        // 1 / sqrt(12)
+    static constexpr T pi_6 = (T)0.52359877559829887;              // pi / 6
+    static constexpr T four_pi_3 = (T)4.1887902047863905;          // 4 pi / 3
+    static constexpr T third = (T)0.33333333333333333;
+    static constexpr T sixth = (T)0.16666666666666667;
+    static constexpr T ninth = (T)0.11111111111111111;
+    static constexpr T inv27 = (T)0.037037037037037037;
+};
+
+template <typename T> __device__ __forceinline__ T sq(T x) { return x * x; }
+template <typename T> __device__ __forceinline__ T cb(T x) { return x * x * x; }
+
+}  // namespace plic

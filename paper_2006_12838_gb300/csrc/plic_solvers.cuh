@@ -1,0 +1,492 @@
+// plic_solvers.cuh -- per-cell device functions of the PLIC hot path.
+//
+// Reduced space (Sec. 2.1, Eqs. 2-8): n1 <= n2 <= n3 are the sorted |n_k|,
+// V = min(V0, 1 - V0) in [0, 1/2], d in [0, (n1+n2+n3)/2] is the offset from
+// the cube corner, and d0 = sign(V0 - 1/2) ((n1+n2+n3)/2 - d).
+//
+// Solvers (reduced space, one function each, templated on float/double):
+//   solve_analytic  -- the paper's inversion (Sec. 2.3, Eqs. 11-25): a-priori
+//                      tests for cases (5), (2), (1) (Eq. 24, with the factor 2
+//                      of the case-(2) test that the derivation d2 <= n2 gives),
+//                      then the trigonometric root f(x, y, a, b, c) of Eq. 11
+//                      for case (3) and, if d3 > n3, for case (4).
+//   solve_sz_orig   -- Scardovelli-Zaleski as Kawano implements it (Sec. 2.4):
+//                      L1-normalised n, thresholds v1, v3, the cubic solved by
+//                      the cosine form.
+//   solve_sz_opt    -- the paper's optimised SZ (Sec. 2.4): order 5 -> 2 -> 1,
+//                      cases (3)/(4) merged through the coefficients (a, b, c)
+//                      and the sine/arcsine form.
+//   solve_newton    -- Newton-Raphson for cases (1), (3), (4) (Sec. 2.5).
+//   solve_nested    -- nested intervals for cases (3), (4) (Sec. 2.5).
+// FAITHFUL selects the paper-literal variant of each (printed iteration counts,
+// no argument clamps); the default adds clamps, convergence tests and a
+// cancellation-free cubic where the printed form loses digits.
+//
+// polish()          -- one Newton step on the reduced volume (Eq. 10) written
+//                      without cancellation; used by PLIC_FP32_POLISHED.
+// reduced_volume()  -- the forward problem (Eq. 10).
+// cut_polygon()     -- area and centroid of the cut polygon (for the adjoints).
+#pragma once
+#include "plic_math.cuh"
+
+namespace plic {
+
+enum { M_ANALYTIC = 0, M_SZ_ORIG = 1, M_SZ_OPT = 2, M_NEWTON = 3, M_NESTED = 4 };
+
+// ----------------------------------------------------------------------------
+// Sec. 2.1: sort |n| (Eqs. 2-4) and reduce V (Eq. 5).
+// Default: exact median and exact V = V0 or 1 - V0.  Faithful: the listing's
+// n2 = |nx| + |ny| + |nz| - n1 - n3 and V = 1/2 - |V0 - 1/2|.
+// ----------------------------------------------------------------------------
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ void reduce_normal(T nx, T ny, T nz, T& n1, T& n2, T& n3) {
+    const T ax = fabs(nx), ay = fabs(ny), az = fabs(nz);
+    n1 = fmin(fmin(ax, ay), az);
+    n3 = fmax(fmax(ax, ay), az);
+    if (FAITHFUL) n2 = ax - n1 + ay + az - n3;
+    else n2 = fmax(fmin(ax, ay), fmin(fmax(ax, ay), az));
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T reduce_volume(T V0) {
+    if (FAITHFUL) return T(0.5) - fabs(V0 - T(0.5));
+    return V0 <= T(0.5) ? V0 : T(1) - V0;
+}
+
+// ----------------------------------------------------------------------------
+// Eq. 10 without cancellation: g(d) = 6 n2 n3 (V(d) - V) and g'(d) for
+// 0 < d < n1 + n2 (cases 1-4), with 1/n1 passed in (0 when n1 = 0, where only
+// case (2) reaches this function and the 1/n1 terms vanish).
+//   d <  n1 : g = d^3/n1 - 6 n2 n3 V
+//   d >= n1 : g = 3 d (d - n1) + n1^2 - ((d-n2)_+^3 + (d-n3)_+^3)/n1 - 6 n2 n3 V
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void reduced_residual(T d, T rhs, T n1, T n2, T n3, T inv_n1,
+                                                 T& g, T& gp) {
+    if (d < n1) {
+        g = d * d * d * inv_n1 - rhs;
+        gp = T(3) * d * d * inv_n1;
+    } else {
+        const T e2 = fmax(d - n2, T(0)), e3 = fmax(d - n3, T(0));
+        g = T(3) * d * (d - n1) + n1 * n1 - (e2 * e2 * e2 + e3 * e3 * e3) * inv_n1 - rhs;
+        gp = T(6) * d - T(3) * n1 - T(3) * (e2 * e2 + e3 * e3) * inv_n1;
+    }
+}
+
+// One Newton step d <- d - g/g' on Eq. 10 (cases 1-4 only; case (5) is
+// linear and its closed form already exact).
+template <typename T>
+__device__ __forceinline__ T polish(T d, T V, T n1, T n2, T n3) {
+    if (!(d > T(0)) || d >= n1 + n2) return d;
+    const T inv_n1 = n1 > T(0) ? T(1) / n1 : T(0);
+    T g, gp;
+    reduced_residual<T>(d, T(6) * n2 * n3 * V, n1, n2, n3, inv_n1, g, gp);
+    return gp > T(0) ? d - Fm<T>::div_(g, gp) : d;
+}
+
+// ----------------------------------------------------------------------------
+// Sec. 2.3: the analytic solution (Eq. 25 with the a-priori tests of Eq. 24).
+// ----------------------------------------------------------------------------
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_analytic(T V, T n1, T n2, T n3) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T n12 = n1 + n2, n3V = n3 * V;
+    if (n12 <= T(2) * n3V) return n3V + T(0.5) * n12;                          // case (5)
+    const T V6n2n3 = T(6) * n2 * n3V, sqn1 = n1 * n1;
+    if (V6n2n3 >= sqn1 && T(3) * n2 * (T(2) * n3V + n1 - n2) <= sqn1)            // case (2)
+        return T(0.5) * n1 + K::inv_sqrt12 * F::sqrt_(T(24) * n2 * n3V - sqn1);
+    if (V6n2n3 < sqn1) return F::cbrt_(V6n2n3 * n1);                             // case (1)
+    // case (3): f(x3, y3, a3, b3, c3); x3 > 0 since n1, n2 > 0 here
+    const T n1n2 = n1 * n2;
+    const T x3 = T(81) * n1n2 * (n12 - T(2) * n3V);
+    const T y32 = F::fdim_(T(23328) * cb(n1n2), x3 * x3);
+    const T u3 = F::cbrt_(x3 * x3 + y32);
+    const T d3 = n12 - (K::two_cbrt54 * n1n2 + K::two_over_cbrt432 * u3) * F::rsqrt_(u3) *
+                           F::sin_(K::pi_6 - K::third * F::atan_(F::div_(F::sqrt_(y32), x3)));
+    if (d3 <= n3) return d3;
+    // case (4): f(x4, y4, a4, b4, c4); x4 kept > 0 so that atan(y/x) replaces atan2
+    const T t4 = T(9) * sq(n12 + n3) - T(18);
+    const T x4 = fmax(n1n2 * n3 * (T(324) - T(648) * V), F::tiny());
+    T y42 = T(4) * cb(t4) - x4 * x4;
+    if (!FAITHFUL) y42 = fmax(y42, T(0));
+    const T u4 = F::cbrt_(x4 * x4 + y42);
+    return T(0.5) * (n12 + n3) -
+           (K::two_over_cbrt864 * t4 + K::two_over_cbrt3456 * u4) * F::rsqrt_(u4) *
+               F::sin_(K::pi_6 - K::third * F::atan_(F::div_(F::sqrt_(y42), x4)));
+}
+
+// ----------------------------------------------------------------------------
+// Sec. 2.4: Scardovelli-Zaleski as in Kawano's implementation.  Inputs are
+// the L1-normalised reduced quantities (m1 <= m2 <= m3, m1 + m2 + m3 = 1) and
+// the reduced volume w; returns the reduced offset alpha in L1 units.
+// For m = (0, 0, 1) and w = 0 the cubic branch is re-entered with alpha == 0
+// and its square-root argument is -1/4: the result is NaN, as the paper
+// reports for this implementation.
+// ----------------------------------------------------------------------------
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_sz_orig(T w, T m1, T m2, T m3) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T m12 = m1 + m2;
+    T alpha = T(0);
+    const T v1 = sq(m1) / (T(6) * m2 * m3 + T(1e-25));
+    const T w6 = T(6) * m1 * m2 * m3 * w;
+    if (w < v1) {
+        alpha = F::cbrt_(w6);                                                     // case (1)
+    } else if (w < v1 + T(0.5) * (m2 - m1) / m3) {
+        alpha = T(0.5) * (m1 + F::sqrt_(sq(m1) + T(8) * m2 * m3 * (w - v1)));     // case (2)
+    } else {
+        T v3;
+        if (m3 < m12) {
+            v3 = (sq(m3) * (T(3) * m12 - m3) + sq(m1) * (m1 - T(3) * m3) +
+                  sq(m2) * (m2 - T(3) * m3)) / (T(6) * m1 * m2 * m3);
+        } else {
+            v3 = T(0.5) * m12 / m3;
+            if (v3 <= w) alpha = m3 * w + T(0.5) * m12;                           // case (5)
+        }
+        if (alpha == T(0)) {
+            T a0, a1, a2;
+            if (w < v3) {                                                         // case (3)
+                a2 = T(-3) * m12;
+                a1 = T(3) * (sq(m1) + sq(m2));
+                a0 = w6 - cb(m1) - cb(m2);
+            } else {                                                              // case (4)
+                a2 = T(-1.5);
+                a1 = T(1.5) * (sq(m1) + sq(m2) + sq(m3));
+                a0 = T(0.5) * (w6 - cb(m1) - cb(m2) - cb(m3));
+            }
+            const T q0 = K::sixth * (a1 * a2 - T(3) * a0) - K::inv27 * cb(a2);
+            const T sp = F::sqrt_(K::ninth * sq(a2) - K::third * a1);
+            T arg = q0 / cb(sp);
+            if (!FAITHFUL) arg = fmin(fmax(arg, T(-1)), T(1));
+            alpha = T(2) * sp * F::cos_(K::four_pi_3 + K::third * F::acos_(arg)) - K::third * a2;
+        }
+    }
+    return alpha;
+}
+
+// ----------------------------------------------------------------------------
+// Sec. 2.4: the paper's optimised SZ solution (L1-normalised inputs, the
+// reduced volume V; returns the reduced offset in L1 units).
+// ----------------------------------------------------------------------------
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_sz_opt(T V, T n1, T n2, T n3) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T n12 = n1 + n2, n3V = n3 * V;
+    if (n12 <= T(2) * n3V) return n3V + T(0.5) * n12;                          // case (5)
+    const T sqn1 = n1 * n1, n26 = T(6) * n2, v1 = sqn1 / n26;                   // n2 > 0 here
+    if (v1 <= n3V && n3V < v1 + T(0.5) * (n2 - n1))                              // case (2)
+        return T(0.5) * (n1 + F::sqrt_(sqn1 + T(8) * n2 * (n3V - v1)));
+    const T V6 = n1 * n26 * n3V;
+    if (n3V < v1) return F::cbrt_(V6);                                           // case (1)
+    // n1 > 0 here
+    const T v3 = n3 < n12 ? (sq(n3) * (T(3) * n12 - n3) + sqn1 * (n1 - T(3) * n3) +
+                             sq(n2) * (n2 - T(3) * n3)) / (n1 * n26)
+                          : T(0.5) * n12;
+    const T sqn12 = sqn1 + sq(n2), V6cbn12 = V6 - cb(n1) - cb(n2);
+    const bool case3 = n3V < v3;                                                 // else case (4)
+    const T a = case3 ? V6cbn12 : T(0.5) * (V6cbn12 - cb(n3));
+    const T b = case3 ? sqn12 : T(0.5) * (sqn12 + sq(n3));
+    const T c = case3 ? n12 : T(0.5);
+    const T t = F::sqrt_(sq(c) - b);
+    T arg = (cb(c) - T(0.5) * a - T(1.5) * b * c) / cb(t);
+    if (!FAITHFUL) arg = fmin(fmax(arg, T(-1)), T(1));
+    return c - T(2) * t * F::sin_(K::third * F::asin_(arg));
+}
+
+// ----------------------------------------------------------------------------
+// Sec. 2.5: Newton-Raphson.  Cases (5) and (2) in closed form; case (1) by
+// Newton on d^3 = 6 V n1 n2 n3; cases (3) and (4) by Newton on the cubic of
+// Eq. 10 from the midpoints of [n2, n1+n2] and [n3, L/2].
+// Faithful: 7 steps from n1/2 (case 1), 4 steps (cases 3, 4), the cubic as
+// printed.  Default: the cancellation-free cubic g of reduced_residual(), a
+// start for case (1) from the exponent of 6 V n1 n2 n3, steps until
+// |dd| <= 2 ulp (at most 64) and a bracket safeguard (bisection whenever a step
+// leaves the bracket).
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T newton_bracketed(T d, T lo, T hi, T rhs, T n1, T n2, T n3,
+                                              T inv_n1) {
+    for (int it = 0; it < 64; ++it) {
+        T g, gp;
+        reduced_residual<T>(d, rhs, n1, n2, n3, inv_n1, g, gp);
+        if (g < T(0)) lo = d; else hi = d;
+        T dn = gp > T(0) ? d - g / gp : T(0.5) * (lo + hi);
+        if (!(dn > lo && dn < hi)) dn = T(0.5) * (lo + hi);
+        const T step = fabs(dn - d);
+        d = dn;
+        if (step <= T(2) * Fm<T>::eps() * d || hi - lo <= T(2) * Fm<T>::eps() * d) break;
+    }
+    return d;
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_newton(T V, T n1, T n2, T n3) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T n1pn2 = n1 + n2, n3xV = n3 * V;
+    if (n1pn2 <= T(2) * n3xV) return n3xV + T(0.5) * n1pn2;                     // case (5)
+    const T V6n2n3 = T(6) * n2 * n3xV, sqn1 = n1 * n1;
+    if (V6n2n3 >= sqn1 && T(3) * n2 * (T(2) * n3xV + n1 - n2) <= sqn1)          // case (2)
+        return T(0.5) * n1 + K::inv_sqrt12 * F::sqrt_(T(24) * n2 * n3xV - sqn1);
+    const T V6n1n2n3 = V6n2n3 * n1;
+    if (FAITHFUL) {
+        T d;
+        if (V6n2n3 < sqn1) {                                                     // case (1)
+            d = T(0.5) * n1;
+            for (int i = 0; i < 7; ++i) d -= (cb(d) - V6n1n2n3) / (T(3) * sq(d));
+            return d;
+        }
+        d = T(0.5) * (n2 + n1pn2);                                               // case (3)
+        for (int i = 0; i < 4; ++i) {
+            const T f = cb(d) - cb(d - n1) - cb(d - n2) - V6n1n2n3;
+            const T fs = T(3) * (sq(d) - sq(d - n1) - sq(d - n2));
+            d -= f / fs;
+        }
+        if (d <= n3) return d;
+        d = T(0.5) * (n3 + T(0.5) * (n1pn2 + n3));                               // case (4)
+        for (int i = 0; i < 4; ++i) {
+            const T f = cb(d) - cb(d - n1) - cb(d - n2) - cb(d - n3) - V6n1n2n3;
+            const T fs = T(3) * (sq(d) - sq(d - n1) - sq(d - n2) - sq(d - n3));
+            d -= f / fs;
+        }
+        return d;
+    }
+    const T inv_n1 = T(1) / n1;                                                  // n1 > 0 here
+    const T rhs = V6n2n3;
+    if (V6n2n3 < sqn1) {                                                         // case (1)
+        // start within a factor 2^(2/3) of the root from the binary exponent of
+        // X = 6 V n1 n2 n3 (the "log2 hack" of the nested-interval listing)
+        const T X = V6n1n2n3;
+        if (!(X > T(0))) return T(0);
+        const int e = F::log2_halvings(X) - (sizeof(T) == 4 ? 24 : 53);
+        const T d0 = fmin(ldexp(T(1), e / 3), n1);
+        return newton_bracketed<T>(d0, T(0), n1, rhs, n1, n2, n3, inv_n1);
+    }
+    T d = newton_bracketed<T>(T(0.5) * (n2 + n1pn2), n2, n1pn2, rhs, n1, n2, n3, inv_n1);
+    if (d <= n3) return d;                                                       // case (3)
+    const T hl = T(0.5) * (n1pn2 + n3);
+    return newton_bracketed<T>(T(0.5) * (n3 + hl), n3, hl, rhs, n1, n2, n3, inv_n1);  // (4)
+}
+
+// ----------------------------------------------------------------------------
+// Sec. 2.5: nested intervals.  Cases (5), (2), (1) in closed form; case (3) by
+// halving [n2, n1+n2] and, if the result exceeds n3, case (4) by halving
+// [n3, L/2].  Faithful: the printed predicate (cubes of Eq. 10) and
+// floor(log2(width * 2^24)) + 1 halvings (2^53 in double), with the count
+// clamped at 0 (the listing's unsigned count would wrap for widths below the
+// unit roundoff).  Default: the cancellation-free predicate and halving until
+// the ends are adjacent floating-point numbers (at most 128 halvings).
+// ----------------------------------------------------------------------------
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T bisect(T dmin, T dmax, T n1, T n2, T n3, bool with_n3, T V6n1n2n3,
+                                    T rhs, T inv_n1) {
+    T d = T(0.5) * (dmin + dmax);
+    if (FAITHFUL) {
+        int k = Fm<T>::log2_halvings(dmax - dmin);
+        k = k < 0 ? 0 : (k > 1100 ? 1100 : k);
+        for (int i = 0; i <= k; ++i) {
+            T f = cb(d) - cb(d - n1) - cb(d - n2);
+            if (with_n3) f -= cb(d - n3);
+            if (f < V6n1n2n3) dmin = d; else dmax = d;
+            d = T(0.5) * (dmin + dmax);
+        }
+        return d;
+    }
+    for (int i = 0; i < 128; ++i) {
+        T g, gp;
+        reduced_residual<T>(d, rhs, n1, n2, n3, inv_n1, g, gp);
+        if (g < T(0)) dmin = d; else dmax = d;
+        const T m = T(0.5) * (dmin + dmax);
+        if (m <= dmin || m >= dmax) break;
+        d = m;
+    }
+    return d;
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_nested(T V, T n1, T n2, T n3) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T n1pn2 = n1 + n2, n3xV = n3 * V;
+    if (n1pn2 <= T(2) * n3xV) return n3xV + T(0.5) * n1pn2;                     // case (5)
+    const T V6n2n3 = T(6) * n2 * n3xV, sqn1 = n1 * n1;
+    if (V6n2n3 >= sqn1 && T(3) * n2 * (T(2) * n3xV + n1 - n2) <= sqn1)          // case (2)
+        return T(0.5) * n1 + K::inv_sqrt12 * F::sqrt_(T(24) * n2 * n3xV - sqn1);
+    if (V6n2n3 < sqn1) return F::cbrt_(V6n2n3 * n1);                             // case (1)
+    const T V6n1n2n3 = V6n2n3 * n1;
+    const T inv_n1 = T(1) / n1;
+    T d = bisect<T, FAITHFUL>(n2, n1pn2, n1, n2, n3, false, V6n1n2n3, V6n2n3, inv_n1);
+    if (d <= n3) return d;                                                       // case (3)
+    return bisect<T, FAITHFUL>(n3, T(0.5) * (n1pn2 + n3), n1, n2, n3, true, V6n1n2n3,
+                               V6n2n3, inv_n1);                                  // case (4)
+}
+
+// ----------------------------------------------------------------------------
+// Whole cell: d0(V0, n) (Sec. 2, Eq. 1) for one method and precision.
+// Invalid input (NaN, V0 outside [0,1], n = 0 or non-finite) gives NaN and
+// sets `bad`.
+// ----------------------------------------------------------------------------
+template <int METHOD, typename T, bool POLISH, bool FAITHFUL>
+__device__ __forceinline__ T offset_cell(T nx, T ny, T nz, T V0, int& bad) {
+    T n1, n2, n3;
+    reduce_normal<T, FAITHFUL>(nx, ny, nz, n1, n2, n3);
+    const T L = fabs(nx) + fabs(ny) + fabs(nz);
+    const bool ok = (V0 >= T(0)) && (V0 <= T(1)) && (L > T(0)) && (L <= T(3));
+    if (!ok) {
+        bad += 1;
+        return T(NAN);
+    }
+    const T V = reduce_volume<T, FAITHFUL>(V0);
+    if (METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT) {
+        // L1 normalisation (Sec. 2.4); the solvers return the offset in L1 units
+        const T l = L;
+        const T m1 = n1 / l, m3 = n3 / l;
+        const T m2 = Fm<T>::fdim_(T(1), m1 + m3);
+        T a = METHOD == M_SZ_ORIG ? solve_sz_orig<T, FAITHFUL>(V, m1, m2, m3)
+                                  : solve_sz_opt<T, FAITHFUL>(V, m1, m2, m3);
+        if (POLISH) a = polish<T>(a, V, m1, m2, m3);
+        return l * copysign(T(0.5) - a, V0 - T(0.5));
+    } else {
+        T d = METHOD == M_ANALYTIC ? solve_analytic<T, FAITHFUL>(V, n1, n2, n3)
+            : METHOD == M_NEWTON   ? solve_newton<T, FAITHFUL>(V, n1, n2, n3)
+                                   : solve_nested<T, FAITHFUL>(V, n1, n2, n3);
+        if (POLISH) d = polish<T>(d, V, n1, n2, n3);
+        return copysign(T(0.5) * (n1 + n2 + n3) - d, V0 - T(0.5));
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Forward problem, Eq. 10 (cases written without cancellation), for
+// 0 <= d <= L/2 with n1 <= n2 <= n3, n3 > 0.  Case (5) requires
+// n1 + n2 <= d <= n3 (the form min(n1+n2, n3) <= d of Eq. 10 would also admit
+// d = n3 when n3 < n1 + n2, where the case-(5) formula does not hold).
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T reduced_volume(T d, T n1, T n2, T n3) {
+    const T n12 = n1 + n2;
+    if (!(d > T(0))) return T(0);
+    if (d >= n12) return (d - T(0.5) * n12) / n3;                                // case (5)
+    if (d < n1) return d * d * d / (T(6) * n1 * n2 * n3);                         // case (1)
+    T num = T(3) * d * (d - n1) + n1 * n1;                                        // case (2)
+    if (d > n2) {                                                                // cases (3), (4)
+        const T e2 = d - n2, e3 = fmax(d - n3, T(0));
+        num -= (e2 * e2 * e2 + e3 * e3 * e3) / n1;
+    }
+    return num / (T(6) * n2 * n3);
+}
+
+template <typename T>
+__device__ __forceinline__ T volume_cell(T nx, T ny, T nz, T d0) {
+    T n1, n2, n3;
+    reduce_normal<T, false>(nx, ny, nz, n1, n2, n3);
+    const T L = n1 + n2 + n3;
+    if (!(L > T(0)) || !(L <= T(3)) || d0 != d0) return T(NAN);
+    const T h = T(0.5) * L, ad = fabs(d0);
+    if (ad >= h) return d0 > T(0) ? T(1) : T(0);
+    const T V = reduced_volume<T>(h - ad, n1, n2, n3);
+    return d0 > T(0) ? T(1) - V : V;
+}
+
+// ----------------------------------------------------------------------------
+// Cut polygon of the plane n . x = d0 with the cube [-1/2,1/2]^3 (unit n):
+// area A and centroid c (cube-centred).  In reduced corner coordinates the
+// polygon's vertices are known per case (Sec. 2.2, Fig. 1): a triangle (1), a
+// quadrilateral (2), a pentagon (3), a hexagon (4), a parallelogram (5); they
+// are listed in cyclic order and summed as a triangle fan.  Returns false
+// where the polygon degenerates (d0 at +-L/2 or invalid input).
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ bool cut_polygon(T nx, T ny, T nz, T d0, T& A, T& cx, T& cy, T& cz) {
+    const T ax = fabs(nx), ay = fabs(ny), az = fabs(nz);
+    // sorting permutation: which original axis holds n1, n2, n3
+    int i1, i2, i3;
+    if (ax <= ay) {
+        if (ay <= az) { i1 = 0; i2 = 1; i3 = 2; }
+        else if (ax <= az) { i1 = 0; i2 = 2; i3 = 1; }
+        else { i1 = 2; i2 = 0; i3 = 1; }
+    } else {
+        if (ax <= az) { i1 = 1; i2 = 0; i3 = 2; }
+        else if (ay <= az) { i1 = 1; i2 = 2; i3 = 0; }
+        else { i1 = 2; i2 = 1; i3 = 0; }
+    }
+    const T a3[3] = {ax, ay, az};
+    const T n1 = a3[i1], n2 = a3[i2], n3 = a3[i3];
+    const T L = n1 + n2 + n3, h = T(0.5) * L;
+    const T d = h - fabs(d0);
+    A = T(0); cx = cy = cz = T(0);
+    if (!(L > T(0)) || !(d > T(0))) return false;
+    const T r2 = n2 > T(0) ? T(1) / n2 : T(0), r3 = T(1) / n3;
+    const T r1 = n1 > T(0) ? T(1) / n1 : T(0);
+    T p[6][3];
+    int np;
+    const T n12 = n1 + n2;
+    if (d >= n12) {                                   // (5) parallelogram over the unit square
+        p[0][0] = 0; p[0][1] = 0; p[0][2] = d * r3;
+        p[1][0] = 1; p[1][1] = 0; p[1][2] = (d - n1) * r3;
+        p[2][0] = 1; p[2][1] = 1; p[2][2] = (d - n12) * r3;
+        p[3][0] = 0; p[3][1] = 1; p[3][2] = (d - n2) * r3;
+        np = 4;
+    } else if (d < n1) {                              // (1) triangle
+        p[0][0] = d * r1; p[0][1] = 0; p[0][2] = 0;
+        p[1][0] = 0; p[1][1] = d * r2; p[1][2] = 0;
+        p[2][0] = 0; p[2][1] = 0; p[2][2] = d * r3;
+        np = 3;
+    } else if (d <= n2) {                             // (2) quadrilateral
+        p[0][0] = 0; p[0][1] = 0; p[0][2] = d * r3;
+        p[1][0] = 0; p[1][1] = d * r2; p[1][2] = 0;
+        p[2][0] = 1; p[2][1] = (d - n1) * r2; p[2][2] = 0;
+        p[3][0] = 1; p[3][1] = 0; p[3][2] = (d - n1) * r3;
+        np = 4;
+    } else if (d <= n3) {                             // (3) pentagon
+        p[0][0] = 0; p[0][1] = 0; p[0][2] = d * r3;
+        p[1][0] = 0; p[1][1] = 1; p[1][2] = (d - n2) * r3;
+        p[2][0] = (d - n2) * r1; p[2][1] = 1; p[2][2] = 0;
+        p[3][0] = 1; p[3][1] = (d - n1) * r2; p[3][2] = 0;
+        p[4][0] = 1; p[4][1] = 0; p[4][2] = (d - n1) * r3;
+        np = 5;
+    } else {                                          // (4) hexagon
+        p[0][0] = 1; p[0][1] = 0; p[0][2] = (d - n1) * r3;
+        p[1][0] = (d - n3) * r1; p[1][1] = 0; p[1][2] = 1;
+        p[2][0] = 0; p[2][1] = (d - n3) * r2; p[2][2] = 1;
+        p[3][0] = 0; p[3][1] = 1; p[3][2] = (d - n2) * r3;
+        p[4][0] = (d - n2) * r1; p[4][1] = 1; p[4][2] = 0;
+        p[5][0] = 1; p[5][1] = (d - n1) * r2; p[5][2] = 0;
+        np = 6;
+    }
+    // triangle fan from p[0]; signed areas along the unit normal (n1,n2,n3)/|n|
+    const T inv_len = Fm<T>::rsqrt_(n1 * n1 + n2 * n2 + n3 * n3);
+    const T u1 = n1 * inv_len, u2 = n2 * inv_len, u3 = n3 * inv_len;
+    T s = T(0), m1 = T(0), m2 = T(0), m3 = T(0);
+#pragma unroll
+    for (int k = 1; k < 5; ++k) {
+        if (k + 1 < np) {
+            const T a1 = p[k][0] - p[0][0], a2 = p[k][1] - p[0][1], a3_ = p[k][2] - p[0][2];
+            const T b1 = p[k + 1][0] - p[0][0], b2 = p[k + 1][1] - p[0][1], b3 = p[k + 1][2] - p[0][2];
+            const T t = T(0.5) * (u1 * (a2 * b3 - a3_ * b2) + u2 * (a3_ * b1 - a1 * b3) +
+                                  u3 * (a1 * b2 - a2 * b1));
+            s += t;
+            m1 += t * (p[0][0] + p[k][0] + p[k + 1][0]);
+            m2 += t * (p[0][1] + p[k][1] + p[k + 1][1]);
+            m3 += t * (p[0][2] + p[k][2] + p[k + 1][2]);
+        }
+    }
+    A = fabs(s);
+    if (!(A > T(0))) return false;
+    const T inv3s = T(1) / (T(3) * s);
+    // centroid in reduced corner coordinates, then back: mirror for V0 > 1/2
+    // (d0 > 0), unsort, shift to the cube centre, restore the signs of n
+    T c[3];
+    const T red[3] = {m1 * inv3s, m2 * inv3s, m3 * inv3s};
+    c[i1] = red[0]; c[i2] = red[1]; c[i3] = red[2];
+    const bool mirror = d0 > T(0);
+    const T sx = nx < T(0) ? T(-1) : T(1), sy = ny < T(0) ? T(-1) : T(1), sz = nz < T(0) ? T(-1) : T(1);
+    cx = sx * ((mirror ? T(1) - c[0] : c[0]) - T(0.5));
+    cy = sy * ((mirror ? T(1) - c[1] : c[1]) - T(0.5));
+    cz = sz * ((mirror ? T(1) - c[2] : c[2]) - T(0.5));
+    return true;
+}
+
+}  // namespace plic

@@ -1,0 +1,308 @@
+// vof_curvature.cuh -- the per-cell curvature step (Sec. 4.2, Appendix B),
+// shared by the single-field and the batched kernels.
+//
+// For one interface cell c of a field phi (x-fastest):
+//   1. gather the 3^3 stencil (D3Q27 order of Appendix B);
+//   2. Parker-Youngs normal n = -sum w_i e_i phi_i / |.| (Eq. 38; the weights
+//      4/2/1 make it a separable [1 2 1] x [1 2 1] smoothed central difference);
+//   3. frame b_z = n, b_y = (n x r)/|.|, b_x = b_y x b_z (Sec. 4.2), r rotated
+//      cyclically in the event that it is parallel to n;
+//   4. PLIC offsets d0(phi_0, n) and d0(phi_i, n) of the interface neighbours,
+//      all with the centre normal (FP32 solver + one Newton polish), giving the
+//      points p_i = (e_i . b_x, e_i . b_y, e_i . b_z + d0_i - d0_0) (Eq. 36), or
+//      the cut-polygon centroids with PLIC_FLAG_POINT_CENTROID;
+//   5. normal equations M = sum Q Q^T, b = sum z Q, Q = (x^2, y^2, xy, x, y),
+//      accumulated in FP32 (Appendix B);
+//   6. LDL^T solve of the leading block (dimension min(m, 5), reduced while a
+//      pivot is <= 1e-6 trace(M)) in FP64, FP32 or double-float;
+//   7. mean curvature of the paraboloid at the origin (Eq. 42), negated by
+//      default so that a convex fluid region has kappa > 0.
+#pragma once
+#include "plic_solvers.cuh"
+
+namespace plic {
+
+enum { FIT_FP64 = 0, FIT_FP32 = 1, FIT_DF32 = 2 };
+
+// D3Q27 directions e_0..e_26, packed as (ex+1) + 3 (ey+1) + 9 (ez+1).
+__constant__ unsigned char c_e27[27] = {
+    13,
+    14, 12, 16, 10, 22, 4,
+    17, 9, 23, 3, 25, 1,
+    11, 15, 5, 21, 19, 7,
+    26, 0, 8, 18, 20, 6,
+    24, 2};
+
+__device__ __forceinline__ void e_of(int i, int& ex, int& ey, int& ez) {
+    const int p = c_e27[i];
+    ex = p % 3 - 1;
+    ey = (p / 3) % 3 - 1;
+    ez = p / 9 - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (a value is hi + lo with |lo| <= ulp(hi)/2), built
+// from the error-free transformations two-sum (Knuth) and two-product via FMA
+// (Dekker/Ogita-Rump-Oishi): about 48 significant bits on the FP32 pipes.
+// ---------------------------------------------------------------------------
+struct df { float hi, lo; };
+__device__ __forceinline__ df df_make(float a) { return {a, 0.0f}; }
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    df t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+    const float q1 = a.hi / b.hi;
+    const df r = df_add(a, df_neg(df_mul(b, df_make(q1))));
+    const float q2 = r.hi / b.hi;
+    return quick_two_sum(q1, q2);
+}
+
+template <int FIT> struct FitReal;
+template <> struct FitReal<FIT_FP64> {
+    typedef double R;
+    static __device__ __forceinline__ R mk(float a) { return (double)a; }
+    static __device__ __forceinline__ R add(R a, R b) { return a + b; }
+    static __device__ __forceinline__ R sub(R a, R b) { return a - b; }
+    static __device__ __forceinline__ R mul(R a, R b) { return a * b; }
+    static __device__ __forceinline__ R div(R a, R b) { return a / b; }
+    static __device__ __forceinline__ float tof(R a) { return (float)a; }
+    static __device__ __forceinline__ bool gt(R a, R b) { return a > b; }
+};
+template <> struct FitReal<FIT_FP32> {
+    typedef float R;
+    static __device__ __forceinline__ R mk(float a) { return a; }
+    static __device__ __forceinline__ R add(R a, R b) { return a + b; }
+    static __device__ __forceinline__ R sub(R a, R b) { return a - b; }
+    static __device__ __forceinline__ R mul(R a, R b) { return a * b; }
+    static __device__ __forceinline__ R div(R a, R b) { return a / b; }
+    static __device__ __forceinline__ float tof(R a) { return a; }
+    static __device__ __forceinline__ bool gt(R a, R b) { return a > b; }
+};
+template <> struct FitReal<FIT_DF32> {
+    typedef df R;
+    static __device__ __forceinline__ R mk(float a) { return df_make(a); }
+    static __device__ __forceinline__ R add(R a, R b) { return df_add(a, b); }
+    static __device__ __forceinline__ R sub(R a, R b) { return df_add(a, df_neg(b)); }
+    static __device__ __forceinline__ R mul(R a, R b) { return df_mul(a, b); }
+    static __device__ __forceinline__ R div(R a, R b) { return df_div(a, b); }
+    static __device__ __forceinline__ float tof(R a) { return a.hi + a.lo; }
+    static __device__ __forceinline__ bool gt(R a, R b) {
+        return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+    }
+};
+
+// Packed upper triangle of the symmetric 5x5 normal matrix.
+__host__ __device__ constexpr int uidx(int i, int j) {
+    return i <= j ? i * 5 - i * (i - 1) / 2 + (j - i) : j * 5 - j * (j - 1) / 2 + (i - j);
+}
+
+// Solve the leading block of M x = b by LDL^T (Appendix B reduces the fit
+// dimension when fewer than 5 points exist).  The dimension is min(m, 5),
+// reduced to j at the first pivot D_j <= 1e-6 trace(M) (D_j is the ratio of
+// consecutive leading principal minors).  Unused parameters are 0.  Returns
+// the dimension used.
+template <int FIT>
+__device__ __forceinline__ int fit_solve(const float* Mf, const float* bf, int m, float x[5]) {
+    typedef FitReal<FIT> F;
+    typedef typename F::R R;
+    const float trace = Mf[uidx(0, 0)] + Mf[uidx(1, 1)] + Mf[uidx(2, 2)] + Mf[uidx(3, 3)] + Mf[uidx(4, 4)];
+    const R tol = F::mk(1e-6f * trace);
+    R Lm[5][5], D[5];
+    int dim = m < 5 ? m : 5;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        R dj = F::mk(Mf[uidx(j, j)]);
+#pragma unroll
+        for (int k = 0; k < j; ++k) dj = F::sub(dj, F::mul(F::mul(Lm[j][k], Lm[j][k]), D[k]));
+        const bool act = j < dim;
+        if (act && !F::gt(dj, tol)) dim = j;
+        D[j] = dj;
+        const bool use = j < dim;
+        const R inv = use ? F::div(F::mk(1.0f), dj) : F::mk(0.0f);
+#pragma unroll
+        for (int i = j + 1; i < 5; ++i) {
+            R s = F::mk(Mf[uidx(i, j)]);
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = F::sub(s, F::mul(F::mul(Lm[i][k], Lm[j][k]), D[k]));
+            Lm[i][j] = F::mul(s, inv);
+        }
+    }
+    R y[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        R s = F::mk(bf[i]);
+#pragma unroll
+        for (int k = 0; k < i; ++k) s = F::sub(s, F::mul(Lm[i][k], y[k]));
+        y[i] = i < dim ? s : F::mk(0.0f);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) y[i] = i < dim ? F::div(y[i], D[i]) : F::mk(0.0f);
+    R xs[5];
+#pragma unroll
+    for (int i = 4; i >= 0; --i) {
+        R s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 5; ++k) s = F::sub(s, F::mul(Lm[k][i], xs[k]));
+        xs[i] = i < dim ? s : F::mk(0.0f);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) x[i] = F::tof(xs[i]);
+    return dim;
+}
+
+// Eq. 42 at the origin: (A (I^2+1) + B (H^2+1) - C H I) / (H^2 + I^2 + 1)^(3/2).
+__device__ __forceinline__ float paraboloid_kappa(const float x[5]) {
+    const float A = x[0], B = x[1], C = x[2], H = x[3], I = x[4];
+    const float s = fmaf(H, H, fmaf(I, I, 1.0f));
+    const float r = rsqrtf(s);
+    return (A * fmaf(I, I, 1.0f) + B * fmaf(H, H, 1.0f) - C * H * I) * (r * r * r);
+}
+
+// The reduced normal of the centre cell, shared by all PLIC solves of the cell.
+template <int METHOD>
+struct CellPlic {
+    float n1, n2, n3, L, m1, m2, m3;
+    __device__ __forceinline__ void prepare(float nx, float ny, float nz) {
+        reduce_normal<float, false>(nx, ny, nz, n1, n2, n3);
+        L = fabsf(nx) + fabsf(ny) + fabsf(nz);
+        if (METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT) {
+            m1 = n1 / L;
+            m3 = n3 / L;
+            m2 = fmaxf(1.0f - (m1 + m3), 0.0f);
+        }
+    }
+    // d0(V0, n) in FP32 with one Newton polish (PLIC_FP32_POLISHED); V0 in (0, 1).
+    __device__ __forceinline__ float offset(float V0) const {
+        const float V = V0 <= 0.5f ? V0 : 1.0f - V0;
+        if (METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT) {
+            float a = METHOD == M_SZ_ORIG ? solve_sz_orig<float, false>(V, m1, m2, m3)
+                                          : solve_sz_opt<float, false>(V, m1, m2, m3);
+            a = polish<float>(a, V, m1, m2, m3);
+            return L * copysignf(0.5f - a, V0 - 0.5f);
+        }
+        float d = METHOD == M_ANALYTIC ? solve_analytic<float, false>(V, n1, n2, n3)
+                : METHOD == M_NEWTON   ? solve_newton<float, false>(V, n1, n2, n3)
+                                       : solve_nested<float, false>(V, n1, n2, n3);
+        d = polish<float>(d, V, n1, n2, n3);
+        return copysignf(0.5f * (n1 + n2 + n3) - d, V0 - 0.5f);
+    }
+};
+
+struct CurvOut {
+    float kappa;
+    int dim, npts;
+};
+
+// Curvature of one interface cell.  `c` is its linear index; the caller
+// guarantees that all 26 neighbours are inside the field.
+template <int METHOD, int FIT>
+__device__ __forceinline__ CurvOut curvature_cell(const float* __restrict__ phi, int64_t c,
+                                                  int nx, int64_t nxy, uint32_t flags) {
+    CurvOut out{0.0f, 0, 0};
+    // 1-2: stencil and Parker-Youngs gradient (separable [1 2 1] weights)
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const float* row = phi + c + dz * nxy + (int64_t)dy * nx;
+            const float a = __ldg(row - 1), b = __ldg(row), e = __ldg(row + 1);
+            const float wy = dy == 0 ? 2.0f : 1.0f, wz = dz == 0 ? 2.0f : 1.0f;
+            const float sum = a + 2.0f * b + e;
+            gx += wy * wz * (e - a);
+            gy += dy * wz * sum;
+            gz += dz * wy * sum;
+        }
+    // dy, dz weights for gy: [1 2 1] over x and z; for gz: over x and y
+    const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
+    if (!(gl > 0.0f)) return out;
+    const float inv = -1.0f / gl;
+    const float nx_ = gx * inv, ny_ = gy * inv, nz_ = gz * inv;
+    // 3: frame
+    float rx = 0.56270900f, ry = 0.32704452f, rz = 0.75921047f;
+    float byx = ny_ * rz - nz_ * ry, byy = nz_ * rx - nx_ * rz, byz = nx_ * ry - ny_ * rx;
+    float bl = byx * byx + byy * byy + byz * byz;
+    if (!(bl > 1e-12f)) {
+        rx = 0.32704452f; ry = 0.75921047f; rz = 0.56270900f;
+        byx = ny_ * rz - nz_ * ry; byy = nz_ * rx - nx_ * rz; byz = nx_ * ry - ny_ * rx;
+        bl = byx * byx + byy * byy + byz * byz;
+    }
+    const float ib = rsqrtf(bl);
+    byx *= ib; byy *= ib; byz *= ib;
+    const float bxx = byy * nz_ - byz * ny_, bxy = byz * nx_ - byx * nz_, bxz = byx * ny_ - byy * nx_;
+    // 4: PLIC offsets with the centre normal
+    CellPlic<METHOD> pl;
+    pl.prepare(nx_, ny_, nz_);
+    const float phi0 = __ldg(phi + c);
+    const float d00 = pl.offset(phi0);
+    const bool centroid = (flags & PLIC_FLAG_POINT_CENTROID) != 0;
+    float c0x = 0.0f, c0y = 0.0f, c0z = 0.0f;
+    if (centroid) {
+        float A;
+        cut_polygon<float>(nx_, ny_, nz_, d00, A, c0x, c0y, c0z);
+    }
+    // 5: normal equations
+    float M[15], bv[5];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) M[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) bv[k] = 0.0f;
+    int m = 0;
+#pragma unroll 1
+    for (int i = 1; i < 27; ++i) {
+        int ex, ey, ez;
+        e_of(i, ex, ey, ez);
+        const float v = __ldg(phi + c + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
+        if (!(v > 0.0f && v < 1.0f)) continue;
+        const float d0i = pl.offset(v);
+        float qx = (float)ex, qy = (float)ey, qz = (float)ez, z;
+        if (centroid) {
+            float A, cx, cy, cz;
+            cut_polygon<float>(nx_, ny_, nz_, d0i, A, cx, cy, cz);
+            qx += cx - c0x; qy += cy - c0y; qz += cz - c0z;
+            z = qx * nx_ + qy * ny_ + qz * nz_;
+        } else {
+            z = qx * nx_ + qy * ny_ + qz * nz_ + (d0i - d00);
+        }
+        const float x = qx * bxx + qy * bxy + qz * bxz;
+        const float y = qx * byx + qy * byy + qz * byz;
+        const float Q[5] = {x * x, y * y, x * y, x, y};
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+#pragma unroll
+            for (int b = a; b < 5; ++b) M[uidx(a, b)] = fmaf(Q[a], Q[b], M[uidx(a, b)]);
+            bv[a] = fmaf(z, Q[a], bv[a]);
+        }
+        ++m;
+    }
+    out.npts = m;
+    // 6-7: solve and Eq. 42
+    float xs[5];
+    out.dim = fit_solve<FIT>(M, bv, m, xs);
+    if (out.dim == 0) return out;
+    const float k = paraboloid_kappa(xs);
+    out.kappa = (flags & PLIC_FLAG_KAPPA_PAPER_SIGN) ? k : -k;
+    return out;
+}
+
+}  // namespace plic

@@ -42,99 +42,113 @@ Q = 32              # quantum: coordinates are integers in units of 1/Q cell
 # PLIC cell batches
 # ---------------------------------------------------------------------------
 def gaussian_normals(rng: np.random.Generator, m: int) -> np.ndarray:
-    g = rng.standard_normal((m, 3))
-    nrm = np.linalg.norm(g, axis=1, keepdims=True)
-    nrm[nrm == 0] = 1.0
-    return g / nrm
+    """m unit normals g/|g|, g ~ N(0, I3) (uniform on the sphere), shape (3, m)."""
+    g = rng.standard_normal((3, m))
+    r2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2]
+    r2[r2 == 0] = 1.0
+    g *= 1.0 / np.sqrt(r2)
+    return g
 
 
 def edge_case_cells(rng: np.random.Generator, m: int):
     """m edge-case cells in five equal parts: V0 in {0, 1, 1/2} with random n;
     axis-aligned n with random V0 (including 0 and 1); one zero component; two
-    zero components; |nx| = |ny| = |nz| with all 8 sign patterns."""
+    zero components; |nx| = |ny| = |nz| with all 8 sign patterns.
+    Returns (n of shape (3, m), V0)."""
     parts = np.array_split(np.arange(m), 5)
-    n = np.empty((m, 3))
+    n = np.empty((3, m))
     V0 = np.empty(m)
     # (a) special V0, random n
     i = parts[0]
-    n[i] = gaussian_normals(rng, i.size)
+    n[:, i] = gaussian_normals(rng, i.size)
     V0[i] = rng.choice([0.0, 1.0, 0.5], i.size)
     # (b) axis-aligned n, random V0 with 0/1 included
     i = parts[1]
     ax = rng.integers(0, 3, i.size)
-    n[i] = 0.0
-    n[i, ax] = rng.choice([-1.0, 1.0], i.size)
+    n[:, i] = 0.0
+    n[ax, i] = rng.choice([-1.0, 1.0], i.size)
     V0[i] = rng.random(i.size)
     V0[i[::7]] = 0.0
     V0[i[3::7]] = 1.0
     # (c) one zero component (random 2D normal in a coordinate plane)
     i = parts[2]
     g = gaussian_normals(rng, i.size)
-    g[np.arange(i.size), rng.integers(0, 3, i.size)] = 0.0
-    n[i] = g / np.linalg.norm(g, axis=1, keepdims=True)
+    g[rng.integers(0, 3, i.size), np.arange(i.size)] = 0.0
+    n[:, i] = g / np.sqrt((g * g).sum(0))
     V0[i] = rng.random(i.size)
     # (d) two zero components
     i = parts[3]
     ax = rng.integers(0, 3, i.size)
-    n[i] = 0.0
-    n[i, ax] = rng.choice([-1.0, 1.0], i.size)
+    n[:, i] = 0.0
+    n[ax, i] = rng.choice([-1.0, 1.0], i.size)
     V0[i] = rng.random(i.size)
     V0[i[::5]] = rng.choice([0.0, 1.0], i[::5].size)
     # (e) |nx| = |ny| = |nz| = 1/sqrt 3, all sign patterns
     i = parts[4]
     signs = np.array([[sx, sy, sz] for sx in (1, -1) for sy in (1, -1) for sz in (1, -1)], float)
-    n[i] = signs[np.arange(i.size) % 8] / math.sqrt(3.0)
+    n[:, i] = (signs[np.arange(i.size) % 8] / math.sqrt(3.0)).T
     V0[i] = rng.random(i.size)
     return n, V0
 
 
-def plic_cells(m: int, seed: int, edge_frac: float = 0.0, vertex_frac: float = 0.0,
+def plic_cells(m: int, seed, edge_frac: float = 0.0, vertex_frac: float = 0.0,
                vertex_eps: float = 1e-6):
     """Normals and fill fractions for m PLIC cells (FP64 numpy arrays).
 
-    Returns dict(n=(m,3), V0=(m,), vertex=(m,) bool, d0_vertex=(m,)).
-    For ``vertex`` cells V0 is NaN and ``d0_vertex`` holds a plane offset that
-    passes within ``vertex_eps`` of a cube vertex (other than the two extreme
-    vertices where V0 is 0 or 1); the caller computes V0 = V0(n, d0_vertex)
-    with its own forward volume.  Edge cases occupy the last ``edge_frac``
-    share; vertex cells are spread over the rest."""
+    Returns dict(n=(3, m) [rows nx, ny, nz], V0=(m,), vertex=(m,) bool,
+    d0_vertex=(m,)).  For ``vertex`` cells V0 is NaN and ``d0_vertex`` holds a
+    plane offset that passes within ``vertex_eps`` of a cube vertex (other
+    than the two extreme vertices where V0 is 0 or 1); the caller computes
+    V0 = V0(n, d0_vertex) with its own forward volume.  Edge cases occupy the
+    last ``edge_frac`` share; each other cell is a vertex cell with probability
+    ``vertex_frac``."""
     rng = np.random.default_rng(seed)
     n = gaussian_normals(rng, m)
     V0 = rng.random(m)
     m_edge = int(round(edge_frac * m))
     if m_edge:
         ne, Ve = edge_case_cells(rng, m_edge)
-        n[m - m_edge:] = ne
+        n[:, m - m_edge:] = ne
         V0[m - m_edge:] = Ve
     vertex = np.zeros(m, bool)
     d0v = np.full(m, np.nan)
     if vertex_frac > 0:
         pool = m - m_edge
-        k = int(round(vertex_frac * pool))
-        pick = rng.choice(pool, size=k, replace=False)
-        vertex[pick] = True
-        sgn_n = np.where(n[pick] >= 0, 1.0, -1.0)
+        vertex[:pool] = rng.random(pool) < vertex_frac
+        pick = np.flatnonzero(vertex)
+        k = pick.size
+        npk = n[:, pick]
+        sgn_n = np.where(npk >= 0, 1.0, -1.0)
         # vertex v = s/2 with a sign pattern s that is neither +sign(n) nor -sign(n)
         pat = rng.integers(1, 7, k)                   # 3-bit patterns 1..6
-        flips = np.stack([(pat >> b) & 1 for b in range(3)], 1).astype(float)
+        flips = np.stack([(pat >> b) & 1 for b in range(3)], 0).astype(float)
         s = sgn_n * (1.0 - 2.0 * flips)
-        d0v[pick] = 0.5 * (n[pick] * s).sum(1) + rng.uniform(-vertex_eps, vertex_eps, k)
+        d0v[pick] = 0.5 * (npk * s).sum(0) + rng.uniform(-vertex_eps, vertex_eps, k)
         V0[pick] = np.nan
     return {"n": n, "V0": V0, "vertex": vertex, "d0_vertex": d0v}
 
 
+def plic_cells_chunks(m: int, seed: int, chunk: int = 1 << 22, **kw):
+    """The recipe of :func:`plic_cells` for large m, generated in chunks of
+    ``chunk`` cells; chunk i uses its own generator seeded with (seed, i), so
+    any chunk can be regenerated alone.  Yields (start, cells_dict)."""
+    for i, start in enumerate(range(0, m, chunk)):
+        k = min(chunk, m - start)
+        yield start, plic_cells(k, seed=np.random.SeedSequence([seed, i]), **kw)
+
+
 def paper_normals(m: int, seed: int) -> np.ndarray:
-    """Normal set of the paper's benchmarks (Sec. 2.5): (1,0,0),
+    """Normal set (shape (3, m)) of the paper's benchmarks (Sec. 2.5): (1,0,0),
     (1/sqrt2, 1/sqrt2, 0), then one eighth minus two random 2D normals in the
     x-y plane (510 of 4096; 8 388 606 of 67 108 864), the rest random 3D."""
     rng = np.random.default_rng(seed)
-    n = np.empty((m, 3))
-    n[0] = [1.0, 0.0, 0.0]
-    n[1] = [1 / math.sqrt(2), 1 / math.sqrt(2), 0.0]
+    n = np.empty((3, m))
+    n[:, 0] = [1.0, 0.0, 0.0]
+    n[:, 1] = [1 / math.sqrt(2), 1 / math.sqrt(2), 0.0]
     m2 = m // 8 - 2
     phi = rng.uniform(0, 2 * math.pi, m2)
-    n[2:2 + m2] = np.stack([np.cos(phi), np.sin(phi), np.zeros(m2)], 1)
-    n[2 + m2:] = gaussian_normals(rng, m - 2 - m2)
+    n[:, 2:2 + m2] = np.stack([np.cos(phi), np.sin(phi), np.zeros(m2)], 0)
+    n[:, 2 + m2:] = gaussian_normals(rng, m - 2 - m2)
     return n
 
 

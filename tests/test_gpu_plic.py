@@ -1,0 +1,168 @@
+"""GPU parity of the PLIC kernels (C ABI via the ctypes binding) against the
+FP64 oracle, element by element.
+
+Tolerances (from the stated targets): |d0 - d0_ref| <= 1e-12 in FP64 and
+<= 2e-6 in FP32 with the Newton polish; round trip |V0(n, d0) - V0| <= 1e-6 in
+FP32.  Inputs are the float/double values both sides see; the oracle promotes
+them to double and uses the general-normal definition.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2006_12838_gb300 import plic, synth  # noqa: E402
+
+METHODS = list(plic.METHODS)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_12838_gb300 import build
+    build.build()
+    plic.load()
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def c1(orc):
+    """1e5 cells: Gaussian unit normals, V0 ~ U[0,1], last 2 % edge cases."""
+    c = synth.plic_cells(100_000, seed=1, edge_frac=0.02)
+    n, V0 = c["n"], c["V0"]
+    return n, V0, orc.offset(n[0], n[1], n[2], V0)
+
+
+def _to(dev, dtype, *arrs):
+    return [torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=dev) for a in arrs]
+
+
+def _kawano_nan_set(n, V0):
+    # axis-aligned normal (two zero components) with V0 in {0, 1} (Sec. 2.4)
+    zeros = (n == 0).sum(0)
+    return (zeros >= 2) & ((V0 == 0) | (V0 == 1))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_offset_fp64_c1(dev, c1, method):
+    n, V0, ref = c1
+    t = _to(dev, torch.float64, n[0], n[1], n[2], V0)
+    inv = torch.zeros(1, dtype=torch.int64, device=dev)
+    d0 = plic.offset(*t, method=method, precision="fp64", invalid=inv).cpu().numpy()
+    assert inv.item() == 0
+    nanset = _kawano_nan_set(n, V0) if method == "sz_orig" else np.zeros(V0.size, bool)
+    assert np.array_equal(np.isnan(d0), nanset)
+    err = np.abs(d0[~nanset] - ref[~nanset])
+    print("%s fp64 max|dd0| %.3e" % (method, err.max()))
+    assert err.max() <= 1e-12, (method, err.max(), np.argmax(err))
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("precision", ["fp32", "fp32p"])
+def test_offset_fp32_c1(dev, orc, c1, method, precision):
+    n, V0, _ = c1
+    t = _to(dev, torch.float32, n[0], n[1], n[2], V0)
+    nf = [x.cpu().numpy().astype(np.float64) for x in t]
+    ref = orc.offset(*nf)
+    d0t = plic.offset(*t, method=method, precision=precision)
+    d0 = d0t.cpu().numpy().astype(np.float64)
+    nanset = _kawano_nan_set(np.stack(nf[:3]), nf[3]) if method == "sz_orig" else np.zeros(V0.size, bool)
+    assert np.array_equal(np.isnan(d0), nanset)
+    err = np.abs(d0[~nanset] - ref[~nanset])
+    # round trip through the GPU forward volume (FP32)
+    Vb = plic.volume(t[0], t[1], t[2], d0t).cpu().numpy().astype(np.float64)
+    rt = np.abs(Vb - nf[3])[~nanset]
+    print("%s %s max|dd0| %.3e  p99.9 %.3e  round-trip max %.3e mean %.3e" % (
+        method, precision, err.max(), np.percentile(err, 99.9), rt.max(), rt.mean()))
+    assert err.max() <= 2e-6, (method, precision, err.max())
+    assert rt.max() <= 1e-6
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_faithful_variants_run(dev, orc, c1, method):
+    # paper-literal variants: reported, not gated (Sec. 2.3-2.5 as printed)
+    n, V0, ref = c1
+    t = _to(dev, torch.float64, n[0], n[1], n[2], V0)
+    d0 = plic.offset(*t, method=method, precision="fp64", faithful=True).cpu().numpy()
+    ok = ~np.isnan(d0)
+    err = np.abs(d0[ok] - ref[ok])
+    print("%s faithful fp64: NaN %d, max|dd0| %.3e, median %.3e" % (method, (~ok).sum(), err.max(), np.median(err)))
+    assert ok.mean() > 0.95
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_volume_forward(dev, orc, dtype):
+    c = synth.plic_cells(50_000, seed=7, edge_frac=0.02)
+    n = c["n"]
+    rng = np.random.default_rng(8)
+    h = 0.5 * np.abs(n).sum(0)
+    d0 = rng.uniform(-1.1, 1.1, n.shape[1]) * h
+    t = _to(dev, dtype, n[0], n[1], n[2], d0)
+    nf = [x.cpu().numpy().astype(np.float64) for x in t]
+    ref = orc.volume(*nf)
+    V = plic.volume(*t).cpu().numpy().astype(np.float64)
+    err = np.abs(V - ref).max()
+    print("volume %s max err %.3e" % (dtype, err))
+    assert err <= (1e-14 if dtype == torch.float64 else 1e-6)
+
+
+def test_invalid_inputs_and_counter(dev):
+    nx = torch.tensor([0.6, np.nan, 0.0, 0.6, 0.6, 0.6, 1.0], dtype=torch.float64, device=dev)
+    ny = torch.tensor([0.8, 0.0, 0.0, 0.8, 0.8, 0.8, 0.0], dtype=torch.float64, device=dev)
+    nz = torch.zeros(7, dtype=torch.float64, device=dev)
+    V0 = torch.tensor([0.3, 0.3, 0.3, -0.1, 1.5, np.nan, 0.25], dtype=torch.float64, device=dev)
+    for m in METHODS:
+        for prec, dt in (("fp64", torch.float64), ("fp32p", torch.float32), ("fp32", torch.float32)):
+            inv = torch.zeros(1, dtype=torch.int64, device=dev)
+            d0 = plic.offset(nx.to(dt), ny.to(dt), nz.to(dt), V0.to(dt), method=m, precision=prec,
+                             invalid=inv).cpu().numpy()
+            assert inv.item() == 5, (m, prec)
+            assert np.isnan(d0[1:6]).all() and np.isfinite(d0[[0, 6]]).all()
+            assert abs(d0[6] + 0.25) < 1e-6
+
+
+@pytest.mark.parametrize("n_cells", [1, 3, 5, 17, 4097, 100_003])
+def test_ragged_and_misaligned(dev, n_cells):
+    c = synth.plic_cells(n_cells + 1, seed=9)
+    for dtype, prec in ((torch.float32, "fp32p"), (torch.float64, "fp64")):
+        big = _to(dev, dtype, c["n"][0], c["n"][1], c["n"][2], c["V0"])
+        aligned = [x[:n_cells] for x in big]
+        shifted = [x[1:] for x in big]           # data_ptr + 1 element: scalar-load path
+        ref = plic.offset(*[x.contiguous() for x in aligned], method="sz_opt", precision=prec)
+        sh = plic.offset(*shifted, method="sz_opt", precision=prec)
+        ref_sh = plic.offset(*[x.clone() for x in shifted], method="sz_opt", precision=prec)
+        assert torch.equal(sh, ref_sh)
+        assert ref.shape[0] == n_cells
+
+
+def test_empty(dev):
+    z = torch.empty(0, device=dev)
+    assert plic.offset(z, z, z, z).numel() == 0
+    assert plic.volume(z, z, z, z).numel() == 0
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_adjoints_against_oracle(dev, orc, dtype):
+    c = synth.plic_cells(40_000, seed=10, edge_frac=0.0)
+    n = c["n"]
+    V0 = np.clip(c["V0"], 0.01, 0.99)
+    g = np.random.default_rng(11).standard_normal(V0.size)
+    t = _to(dev, dtype, n[0], n[1], n[2], V0, g)
+    d0 = plic.offset(*t[:4], method="sz_opt")
+    nf = [x.cpu().numpy().astype(np.float64) for x in t]
+    d0f = d0.cpu().numpy().astype(np.float64)
+    gV, gx, gy, gz = (x.cpu().numpy().astype(np.float64) for x in plic.offset_backward(t[0], t[1], t[2], d0, t[4]))
+    rV, rx, ry, rz = orc.offset_grad(nf[0], nf[1], nf[2], d0f, nf[4])
+    tol = 1e-10 if dtype == torch.float64 else 2e-4
+    A, *_ = orc.area_centroid(nf[0], nf[1], nf[2], d0f)
+    keep = A > 0.02
+    for a, b in ((gV, rV), (gx, rx), (gy, ry), (gz, rz)):
+        rel = np.abs(a - b)[keep] / np.maximum(np.abs(b[keep]), np.abs(nf[4][keep]))
+        assert rel.max() <= tol, rel.max()
+    gd, vx, vy, vz = (x.cpu().numpy().astype(np.float64) for x in plic.volume_backward(t[0], t[1], t[2], d0, t[4]))
+    sd, sx, sy, sz = orc.volume_grad(nf[0], nf[1], nf[2], d0f, nf[4])
+    for a, b in ((gd, sd), (vx, sx), (vy, sy), (vz, sz)):
+        rel = np.abs(a - b) / np.maximum(np.abs(b), np.abs(nf[4]))
+        assert rel.max() <= tol, rel.max()
