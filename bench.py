@@ -1,0 +1,527 @@
+"""Benchmark of the GB300 PLIC hot path.
+
+Headline step (config "2^28 cells"): PLIC offsets of 2^28 SoA FP32 cells by the
+optimised SZ solver with one Newton polish, followed by the forward-volume
+round trip V0(n, d0) -- the paper's accuracy check -- on the same cells.
+Inputs: Gaussian unit normals, V0 ~ U[0,1], 10 % of the cells with the plane
+within 1e-6 of a cube vertex (case boundaries); 4 GiB of input, larger than
+L2, so every step streams from HBM.
+
+Reported beside it (``sections``): every solver in FP32-polished and FP64,
+the forward volume, the offset adjoint, interface compaction + curvature on a
+256^3 field with 8 spheres, the batched curvature of 64 uneven fields, and the
+curvature adjoint -- each with its own roofline figure.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--quick] [--no-sections]
+Under torchrun each rank processes its own 2^28 cells (weak scaling, no
+data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G PLIC solves/s & curvature cells/s vs roofline, FP32-polished vs FP64"
+UNIT = "G solves/s"
+CELLS = 1 << 28
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2006_12838_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel_key):
+    """DRAM bytes per launch of `kernel_key` from the committed ncu summary,
+    if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[kernel_key]
+        if e.get("src_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def make_cells_gpu(cells, seed, dtype, dev, vertex_frac=0.1, edge_frac=0.0):
+    """The 2^28-cell workload, generated chunkwise (seeded) straight into device
+    tensors.  Vertex cells get V0 from the GPU forward volume of their offset."""
+    import torch
+    from paper_2006_12838_gb300 import plic, synth
+    out = [torch.empty(cells, dtype=dtype, device=dev) for _ in range(4)]
+    for start, c in synth.plic_cells_chunks(cells, seed, vertex_frac=vertex_frac,
+                                            edge_frac=edge_frac):
+        k = c["V0"].size
+        n = torch.from_numpy(c["n"]).to(dev, dtype)
+        V0 = torch.from_numpy(c["V0"]).to(dev, dtype)
+        vm = torch.from_numpy(c["vertex"]).to(dev)
+        if bool(vm.any()):
+            d0v = torch.from_numpy(c["d0_vertex"]).to(dev, dtype)
+            Vv = plic.volume(n[0].contiguous(), n[1].contiguous(), n[2].contiguous(),
+                             torch.nan_to_num(d0v).contiguous())
+            V0 = torch.where(vm, Vv, V0)
+        for j in range(3):
+            out[j][start:start + k] = n[j]
+        out[3][start:start + k] = V0
+    return out
+
+
+def timed(fn, steps, warmup, stream, events_per_step=None):
+    """Run fn() warmup times, then `steps` times between CUDA events on
+    `stream`; returns total seconds."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def frac(x, p):
+    return None if x is None or p in (None, 0) else x / p
+
+
+# ---------------------------------------------------------------------------
+# sections (each returns a dict)
+# ---------------------------------------------------------------------------
+def section_solvers(t32, dev, pk, steps):
+    import torch
+    from paper_2006_12838_gb300 import plic
+    s = torch.cuda.current_stream()
+    out = {}
+    n = t32[0].numel()
+    d0 = torch.empty_like(t32[0])
+    for m in plic.METHODS:
+        for prec in ("fp32p", "fp32"):
+            sec = timed(lambda: plic.offset(*t32, method=m, precision=prec, out=d0), steps, 2, s)
+            gbs = 20.0 * n * steps / sec / 1e9
+            out["offset_%s_%s" % (m, prec)] = {"g_solves_s": n * steps / sec / 1e9,
+                                              "ms": sec / steps * 1e3, "hbm_gbs": gbs,
+                                              "hbm_frac": frac(gbs, pk["hbm_gbs"])}
+    sec = timed(lambda: plic.volume(*t32[:3], t32[3], out=d0), steps, 2, s)
+    gbs = 20.0 * n * steps / sec / 1e9
+    out["volume_fp32"] = {"g_cells_s": n * steps / sec / 1e9, "ms": sec / steps * 1e3,
+                          "hbm_gbs": gbs, "hbm_frac": frac(gbs, pk["hbm_gbs"])}
+    return out
+
+
+def section_fp64(dev, pk, steps, cells):
+    import torch
+    from paper_2006_12838_gb300 import plic
+    t64 = make_cells_gpu(cells, 2, torch.float64, dev)
+    s = torch.cuda.current_stream()
+    out = {}
+    d0 = torch.empty_like(t64[0])
+    for m in plic.METHODS:
+        sec = timed(lambda: plic.offset(*t64, method=m, precision="fp64", out=d0), steps, 1, s)
+        gbs = 40.0 * cells * steps / sec / 1e9
+        out["offset_%s_fp64" % m] = {"g_solves_s": cells * steps / sec / 1e9,
+                                     "ms": sec / steps * 1e3, "hbm_gbs": gbs,
+                                     "hbm_frac": frac(gbs, pk["hbm_gbs"]), "cells": cells}
+    del t64
+    torch.cuda.empty_cache()
+    return out
+
+
+def section_adjoint(t32, dev, pk, steps):
+    import torch
+    from paper_2006_12838_gb300 import plic
+    n = 1 << 26
+    t = [x[:n] for x in t32]
+    d0 = plic.offset(*t, method="sz_opt")
+    g = torch.ones_like(d0)
+    outs = [torch.empty_like(d0) for _ in range(4)]
+    L = plic.load()
+    import ctypes
+    P = lambda x: ctypes.c_void_p(x.data_ptr())  # noqa: E731
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def run():
+        L.plic_offset_backward(P(t[0]), P(t[1]), P(t[2]), P(d0), P(g), P(outs[0]), P(outs[1]),
+                               P(outs[2]), P(outs[3]), n, 0, st)
+    sec = timed(run, steps, 2, torch.cuda.current_stream())
+    gbs = 36.0 * n * steps / sec / 1e9
+    return {"offset_backward_fp32": {"g_cells_s": n * steps / sec / 1e9, "ms": sec / steps * 1e3,
+                                     "hbm_gbs": gbs, "hbm_frac": frac(gbs, pk["hbm_gbs"]),
+                                     "cells": n}}
+
+
+def section_curvature(dev, pk, steps):
+    import torch
+    from paper_2006_12838_gb300 import plic, synth
+    phi, _ = synth.curvature_field(seed=3, edge=256, device=dev)
+    idx, cnt = plic.interface_compact(phi)
+    k = int(cnt.item())
+    it = idx[:k].contiguous()
+    kap = torch.empty(k, device=dev)
+    s = torch.cuda.current_stream()
+    ws = torch.empty(plic.workspace_bytes(plic.WS_COMPACT, phi.numel()), dtype=torch.uint8, device=dev)
+    cnt2 = torch.empty(1, dtype=torch.int64, device=dev)
+    out = {"interface_cells": k, "field": "256^3 f32, 8 spheres R~U[6,40]"}
+    sec = timed(lambda: plic.interface_compact(phi, idx=idx, count=cnt2, workspace=ws), steps, 3, s)
+    out["compact"] = {"ms": sec / steps * 1e3,
+                      "hbm_gbs": (phi.numel() * 4 + k * 4) * steps / sec / 1e9}
+    for fit, name in ((0, "fit64"), (plic.FLAG_FIT_DF32, "fitdf32"), (plic.FLAG_FIT_FP32, "fit32")):
+        sec = timed(lambda: plic.curvature(phi, it, kappa=kap, flags=fit), steps, 3, s)
+        out["curvature_sz_opt_" + name] = {"ms": sec / steps * 1e3,
+                                            "m_cells_s": k * steps / sec / 1e6}
+    for m in plic.METHODS:
+        sec = timed(lambda: plic.curvature(phi, it, kappa=kap, method=m), steps, 2, s)
+        out["curvature_%s_fit64" % m] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+
+    def pipeline():
+        plic.interface_compact(phi, idx=idx, count=cnt2, workspace=ws)
+        plic.curvature(phi, idx, n_iface=k, count=cnt2, kappa=kap)
+    sec = timed(pipeline, steps, 3, s)
+    out["compact_plus_curvature"] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+    return out
+
+
+def section_batched(dev, pk, steps):
+    import torch
+    from paper_2006_12838_gb300 import plic, synth
+    fields = synth.batched_fields(seed=5, n_fields=64, device=dev)
+    args = []
+    tot = 0
+    cells = 0
+    for phi, _ in fields:
+        idx, cnt = plic.interface_compact(phi)
+        k = int(cnt.item())
+        it = idx[:k].contiguous()
+        args.append((phi, it, k, torch.empty(max(k, 1), device=dev)))
+        tot += k
+        cells += phi.numel()
+    s = torch.cuda.current_stream()
+    out = {"fields": len(args), "field_cells": cells, "interface_cells": tot}
+    for fit, name in ((0, "fit64"), (plic.FLAG_FIT_DF32, "fitdf32"), (plic.FLAG_FIT_FP32, "fit32")):
+        sec = timed(lambda: plic.curvature_batched(args, flags=fit), steps, 2, s)
+        out["batched_" + name] = {"ms": sec / steps * 1e3, "m_cells_s": tot * steps / sec / 1e6}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(cells, seed=2):
+    """A bounded sample of the headline workload for the CPU oracle: the
+    first `cells` cells of the same seeded chunk stream, with vertex-cell V0
+    from the oracle's own forward volume."""
+    import oracle
+    from paper_2006_12838_gb300 import synth
+    nx, ny, nz, V0 = [], [], [], []
+    got = 0
+    for _, c in synth.plic_cells_chunks(CELLS, seed, vertex_frac=0.1):
+        n = c["n"].astype(np.float32).astype(np.float64)
+        v = c["V0"].copy()
+        vm = c["vertex"]
+        if vm.any():
+            v[vm] = oracle.volume(n[0][vm], n[1][vm], n[2][vm],
+                                  c["d0_vertex"][vm].astype(np.float32).astype(np.float64))
+        v = v.astype(np.float32).astype(np.float64)
+        take = min(cells - got, v.size)
+        nx.append(n[0][:take]); ny.append(n[1][:take]); nz.append(n[2][:take]); V0.append(v[:take])
+        got += take
+        if got >= cells:
+            break
+    return [np.concatenate(a) for a in (nx, ny, nz, V0)]
+
+
+def oracle_step(sample):
+    import oracle
+    d0 = oracle.offset(*sample)
+    oracle.volume(sample[0], sample[1], sample[2], d0)
+
+
+def cpu_baseline(cells=1 << 22):
+    import oracle
+    sample = oracle_sample(cells)
+    oracle_step([a[:4096] for a in sample])
+    t0 = time.perf_counter()
+    oracle_step(sample)
+    sec = time.perf_counter() - t0
+    return {"value": cells / sec / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "first %d cells of the 2^28-cell workload (same seeded stream), FP64 bisection "
+                      "offset + forward round trip, OpenMP over host cores" % cells,
+            "seconds": sec}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    per = 1 << 21
+    sample = oracle_sample(per)
+    for _ in range(args.warmup):
+        oracle_step([a[:4096] for a in sample])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(sample)
+    sec = time.perf_counter() - t0
+    v = per * args.steps / sec / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "plic_offset + plic_volume round trip, FP64 CPU oracle, "
+                                   "%d-cell sample of the 2^28-cell workload per step" % per},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle",
+                             "cores": oracle.num_threads(),
+                             "sample": "%d cells per step" % per},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--quick", action="store_true", help="smaller sections")
+    ap.add_argument("--no-sections", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2006_12838_gb300 import build as B
+    from paper_2006_12838_gb300 import plic
+    from paper_2006_12838_gb300.pipeline import HostOffsetPipeline
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    B.build()
+    plic.load()
+    pk = peaks()
+
+    t32 = make_cells_gpu(CELLS, 2 + rank, torch.float32, dev)
+    d0 = torch.empty_like(t32[0])
+    Vrt = torch.empty_like(t32[0])
+    s = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    step_i = [0]
+
+    def step(record=False):
+        if record:
+            ev[step_i[0]][0].record(s)
+        plic.offset(*t32, method="sz_opt", precision="fp32p", out=d0)
+        if record:
+            ev[step_i[0]][1].record(s)
+            step_i[0] += 1
+        plic.volume(t32[0], t32[1], t32[2], d0, out=Vrt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        a.record(s)
+        for _ in range(args.steps):
+            step(record=True)
+        b.record(s)
+        torch.cuda.synchronize()
+        time.sleep(0.3)
+    sec = a.elapsed_time(b) / 1e3
+    if world > 1:
+        tt = torch.tensor([sec], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        sec = float(tt.item())
+        dist.barrier()
+    kern_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+    value = CELLS * world * args.steps / sec / 1e9
+    # accuracy of the timed result: round trip on a sample of the output
+    rt = (Vrt - t32[3]).abs()
+    rt_max = float(rt.max().item())
+    rt_mean = float(rt.double().mean().item())
+
+    # e2e: same step through the ABI from pinned host buffers (H2D + D2H in the timed region)
+    e2e = None
+    try:
+        hn = [x.cpu().pin_memory() for x in t32]
+        hd = torch.empty(CELLS, dtype=torch.float32).pin_memory()
+        hV = torch.empty(CELLS, dtype=torch.float32).pin_memory()
+        pipe = HostOffsetPipeline(1 << 24, torch.float32, dev, "sz_opt", "fp32p")
+        esteps = max(2, min(args.steps, 5))
+        for _ in range(2):
+            pipe.run(*hn, hd, hV)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a.record(s)
+        for _ in range(esteps):
+            pipe.run(*hn, hd, hV)
+        b.record(s)
+        torch.cuda.synchronize()
+        esec = time.perf_counter() - t0
+        e2e = {"value": CELLS * world * esteps / esec / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 16 * CELLS, "d2h_bytes_per_step": 8 * CELLS,
+               "steps": esteps, "chunk_cells": 1 << 24,
+               "note": "pinned host SoA -> 3-stream chunked H2D / plic_offset+plic_volume / D2H"}
+        del hn, hd, hV, pipe
+    except Exception as ex:  # report, do not hide
+        e2e = {"value": None, "unit": UNIT, "error": repr(ex)[:200],
+               "h2d_bytes_per_step": 16 * CELLS, "d2h_bytes_per_step": 8 * CELLS}
+
+    alg_bytes = 20.0 * CELLS
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_plic_offset<SZ_OPT,float,polish>",
+            "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": profile_traffic("plic_offset_sz_opt_fp32p"),
+            "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": alg_bytes}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "plic_offset (sz_opt, fp32 + 1 Newton polish) + plic_volume "
+                                   "round trip, 2^28 SoA f32 cells per GPU, 10% within 1e-6 of "
+                                   "a cube vertex",
+                       "cells_per_gpu": CELLS, "method": "sz_opt", "precision": "fp32_polished",
+                       "l2": "inputs 4 GiB per step > 129 MB L2 (no flush needed)"},
+            "roofline": roof, "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+            "accuracy": {"roundtrip_max": rt_max, "roundtrip_mean": rt_mean}}
+
+    if rank == 0 and world == 1 and not args.no_sections:
+        steps = 3 if args.quick else 5
+        sec_out = {}
+        try:
+            sec_out.update(section_solvers(t32, dev, pk, steps))
+            sec_out.update(section_adjoint(t32, dev, pk, steps))
+            del t32, d0, Vrt
+            torch.cuda.empty_cache()
+            sec_out.update(section_fp64(dev, pk, 2 if args.quick else 3, CELLS))
+            sec_out["curvature_256"] = section_curvature(dev, pk, steps)
+            sec_out["batched_64_fields"] = section_batched(dev, pk, steps)
+        except Exception as ex:
+            sec_out["error"] = repr(ex)[:300]
+        line["sections"] = sec_out
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as ex:
+            line["cpu_baseline"] = {"value": None, "error": repr(ex)[:200]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,75 @@
+"""Host-buffer entry points: PLIC offsets for arrays that live in (pinned) host
+memory, streamed through the device in chunks.
+
+The GPU work is the same C ABI call as :func:`plic.offset`; this module only
+stages data: chunk i is copied host->device on one stream while chunk i-1 is
+solved on a second and chunk i-2 is copied back on a third, so the copies over
+the host link and the kernels overlap.  Host arrays should be pinned
+(``tensor.pin_memory()``) for the copies to be asynchronous.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import plic
+
+
+class HostOffsetPipeline:
+    """Reusable device staging buffers and streams for host-resident batches.
+
+    ``run(nx, ny, nz, V0, d0_out, V0_roundtrip_out=None)`` solves
+    d0 = plic_offset(n, V0) for host tensors (pinned) and, if
+    ``V0_roundtrip_out`` is given, also the forward volume of the result."""
+
+    def __init__(self, chunk: int, dtype=torch.float32, device="cuda", method="sz_opt",
+                 precision=None, depth: int = 3):
+        self.chunk = int(chunk)
+        self.dtype = dtype
+        self.device = torch.device(device)
+        self.method = method
+        self.precision = precision
+        self.depth = depth
+        mk = lambda: torch.empty(self.chunk, dtype=dtype, device=self.device)  # noqa: E731
+        self.bufs = [[mk() for _ in range(6)] for _ in range(depth)]
+        self.h2d = torch.cuda.Stream(self.device)
+        self.comp = torch.cuda.Stream(self.device)
+        self.d2h = torch.cuda.Stream(self.device)
+        self.launches = 0
+
+    def run(self, nx, ny, nz, V0, d0_out, V_out=None):
+        n = V0.numel()
+        ev_in = [torch.cuda.Event() for _ in range(self.depth)]
+        ev_done = [torch.cuda.Event() for _ in range(self.depth)]
+        ev_free = [None] * self.depth
+        cur = torch.cuda.current_stream(self.device)
+        for s in (self.h2d, self.comp, self.d2h):
+            s.wait_stream(cur)
+        self.launches = 0
+        for j, start in enumerate(range(0, n, self.chunk)):
+            k = min(self.chunk, n - start)
+            b = j % self.depth
+            bx, by, bz, bv, bd, bw = (t[:k] for t in self.bufs[b])
+            if ev_free[b] is not None:
+                self.h2d.wait_event(ev_free[b])
+            with torch.cuda.stream(self.h2d):
+                for dst, src in ((bx, nx), (by, ny), (bz, nz), (bv, V0)):
+                    dst.copy_(src[start:start + k], non_blocking=True)
+                ev_in[b].record(self.h2d)
+            self.comp.wait_event(ev_in[b])
+            plic.offset(bx, by, bz, bv, method=self.method, precision=self.precision, out=bd,
+                        stream=self.comp)
+            self.launches += 1
+            if V_out is not None:
+                plic.volume(bx, by, bz, bd, out=bw, stream=self.comp)
+                self.launches += 1
+            ev_done[b].record(self.comp)
+            self.d2h.wait_event(ev_done[b])
+            with torch.cuda.stream(self.d2h):
+                d0_out[start:start + k].copy_(bd, non_blocking=True)
+                if V_out is not None:
+                    V_out[start:start + k].copy_(bw, non_blocking=True)
+                e = torch.cuda.Event()
+                e.record(self.d2h)
+                ev_free[b] = e
+        for s in (self.h2d, self.comp, self.d2h):
+            cur.wait_stream(s)

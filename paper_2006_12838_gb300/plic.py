@@ -259,7 +259,9 @@ def curvature_batched(fields, method="sz_opt", flags=0, tuning=None, workspace=N
     dev = fields[0][0].device
     for i, (phi, idx, n, kappa) in enumerate(fields):
         _cuda(phi, kappa, dtype=torch.float32)
-        _cuda(phi, idx, dtype=torch.int32)
+        _cuda(idx, dtype=torch.int32)
+        if idx.device != phi.device:
+            raise PlicError("tensors must be on one device")
         nz, ny, nx = phi.shape
         arr[i] = VofField(phi.data_ptr(), nx, ny, nz, idx.data_ptr(), int(n), kappa.data_ptr())
     ws_n = workspace_bytes(WS_BATCHED, len(fields))
