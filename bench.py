@@ -327,7 +327,7 @@ def oracle_step(sample):
     oracle.volume(sample[0], sample[1], sample[2], d0)
 
 
-def cpu_baseline(cells=1 << 22):
+def cpu_baseline(cells=1 << 24):
     import oracle
     sample = oracle_sample(cells)
     oracle_step([a[:4096] for a in sample])
@@ -369,6 +369,45 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_case(args):
+    """A small single-kernel run for ncu captures (not a benchmark line)."""
+    import torch
+    from paper_2006_12838_gb300 import build as B
+    from paper_2006_12838_gb300 import plic, synth
+    B.build()
+    dev = torch.device("cuda", 0)
+    if args.case in ("offset", "volume"):
+        t = make_cells_gpu(args.cells, 2, torch.float32, dev)
+        d0 = torch.empty_like(t[0])
+        for _ in range(args.steps):
+            if args.case == "offset":
+                plic.offset(*t, method="sz_opt", precision="fp32p", out=d0)
+            else:
+                plic.volume(*t[:3], t[3], out=d0)
+    elif args.case == "offset_fp64":
+        t = make_cells_gpu(args.cells, 2, torch.float64, dev)
+        d0 = torch.empty_like(t[0])
+        for _ in range(args.steps):
+            plic.offset(*t, method="sz_opt", precision="fp64", out=d0)
+    elif args.case == "curvature":
+        phi, _ = synth.curvature_field(seed=3, edge=256, device=dev)
+        for _ in range(args.steps):
+            idx, cnt = plic.interface_compact(phi)
+            k = int(cnt.item())
+            plic.curvature(phi, idx[:k].contiguous())
+    elif args.case == "batched":
+        fields = synth.batched_fields(seed=5, n_fields=16, device=dev)
+        a = []
+        for phi, _ in fields:
+            idx, cnt = plic.interface_compact(phi)
+            k = int(cnt.item())
+            a.append((phi, idx[:k].contiguous(), k, torch.empty(max(k, 1), device=dev)))
+        for _ in range(args.steps):
+            plic.curvature_batched(a)
+    torch.cuda.synchronize()
+    print("case %s done" % args.case)
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -379,9 +418,15 @@ def main():
     ap.add_argument("--quick", action="store_true", help="smaller sections")
     ap.add_argument("--no-sections", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="profiling case: run only one kernel on --cells cells "
+                         "(offset | volume | offset_fp64 | curvature | batched)")
+    ap.add_argument("--cells", type=int, default=1 << 24)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
 
     import torch
     import torch.distributed as dist

@@ -1,8 +1,9 @@
 // plic_math.cuh -- scalar math for the PLIC kernels, per precision.
 //
 // Fm<float>  : the FP32 fast path: MUFU-based sin/cos (__sinf/__cosf), MUFU
-//              reciprocal square root, a cube root from the MUFU exp2/log2 pair
-//              refined by one Newton step, and CUDA's asinf/acosf/atanf.
+//              reciprocal and reciprocal square root for division and sqrt, a
+//              cube root from the MUFU exp2/log2 pair refined by one Newton
+//              step, and arcsine/arccosine/arctangent from one arcsine series.
 // Fm<double> : plain double-precision library functions.
 //
 // Constants are written as their closed forms (the decimals printed in the
@@ -16,9 +17,33 @@ namespace plic {
 
 template <typename T> struct Fm;
 
+// Arcsine for |x| <= 1 on the FP32 pipes, from the Maclaurin series of
+// arcsin, asin(s) = sum_k C(2k,k) / (4^k (2k+1)) s^(2k+1), truncated after
+// s^17 and used only for s <= 1/2 (truncation error < 2.4e-8), with the
+// half-angle reduction asin(x) = pi/2 - 2 asin(sqrt((1 - x)/2)) for x > 1/2.
+__device__ __forceinline__ float fast_asinf(float x) {
+    const float a = fabsf(x);
+    const bool big = a > 0.5f;
+    const float z = big ? 0.5f * (1.0f - a) : a * a;
+    const float s = big ? (z > 0.0f ? z * rsqrtf(z) : 0.0f) : a;
+    float p = 0.011551800896139705f;                 // 6435/557056
+    p = fmaf(p, z, 0.01396484375f);                  // 143/10240
+    p = fmaf(p, z, 0.017352764423076924f);           // 231/13312
+    p = fmaf(p, z, 0.022372159090909092f);           // 63/2816
+    p = fmaf(p, z, 0.030381944444444444f);           // 35/1152
+    p = fmaf(p, z, 0.044642857142857144f);           // 5/112
+    p = fmaf(p, z, 0.075f);                          // 3/40
+    p = fmaf(p, z, 0.16666666666666666f);            // 1/6
+    p = fmaf(s * z, p, s);
+    const float r = big ? fmaf(-2.0f, p, 1.5707963267948966f) : p;
+    return copysignf(r, x);
+}
+
 template <> struct Fm<float> {
     typedef float T;
-    static __device__ __forceinline__ T sqrt_(T x) { return sqrtf(x); }
+    // sqrt and division: MUFU-based (rsqrt, rcp) forms; 1-2 ulp, enough for a
+    // solver whose result is either used as is (FP32) or Newton-polished
+    static __device__ __forceinline__ T sqrt_(T x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
     static __device__ __forceinline__ T rsqrt_(T x) { return rsqrtf(x); }
     // Cube root for x >= 0: 2^(log2(x)/3) from the MUFU pair (about 2^-22
     // relative), then one Newton step on r^3 = x, r <- r - (r^3 - x)/(3 r^2).
@@ -32,10 +57,18 @@ template <> struct Fm<float> {
     }
     static __device__ __forceinline__ T sin_(T x) { return __sinf(x); }
     static __device__ __forceinline__ T cos_(T x) { return __cosf(x); }
-    static __device__ __forceinline__ T asin_(T x) { return asinf(x); }
-    static __device__ __forceinline__ T acos_(T x) { return acosf(x); }
-    static __device__ __forceinline__ T atan_(T x) { return atanf(x); }
+    static __device__ __forceinline__ T asin_(T x) { return fast_asinf(x); }
+    static __device__ __forceinline__ T acos_(T x) { return 1.5707963267948966f - fast_asinf(x); }
+    // atan(u) for u >= 0 through the arcsine: atan(u) = asin(u / sqrt(1+u^2)),
+    // evaluated on min(u, 1/u) so that the arcsine argument stays <= 1/sqrt 2
+    static __device__ __forceinline__ T atan_(T u) {
+        const bool inv = u > 1.0f;
+        const float w = inv ? __fdividef(1.0f, u) : u;
+        const float r = fast_asinf(w * rsqrtf(fmaf(w, w, 1.0f)));
+        return inv ? 1.5707963267948966f - r : r;
+    }
     static __device__ __forceinline__ T div_(T a, T b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ T rcp_(T a) { return __fdividef(1.0f, a); }
     static __device__ __forceinline__ T fdim_(T a, T b) { return fmaxf(a - b, 0.0f); }
     static __device__ __forceinline__ T tiny() { return 1.17549435e-38f; }   // FLT_MIN
     static __device__ __forceinline__ T eps() { return 5.9604645e-08f; }    // 2^-24
@@ -68,6 +101,7 @@ template <> struct Fm<double> {
     static __device__ __forceinline__ T acos_(T x) { return acos(x); }
     static __device__ __forceinline__ T atan_(T x) { return atan(x); }
     static __device__ __forceinline__ T div_(T a, T b) { return a / b; }
+    static __device__ __forceinline__ T rcp_(T a) { return 1.0 / a; }
     static __device__ __forceinline__ T fdim_(T a, T b) { return fmax(a - b, 0.0); }
     static __device__ __forceinline__ T tiny() { return 2.2250738585072014e-308; }  // DBL_MIN
     static __device__ __forceinline__ T eps() { return 1.1102230246251565e-16; }    // 2^-53

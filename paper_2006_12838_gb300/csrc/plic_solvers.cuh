@@ -73,15 +73,23 @@ __device__ __forceinline__ void reduced_residual(T d, T rhs, T n1, T n2, T n3, T
     }
 }
 
-// One Newton step d <- d - g/g' on Eq. 10 (cases 1-4 only; case (5) is
-// linear and its closed form already exact).
+// One Newton step d <- d - g/g' on Eq. 10, valid in every case: for
+// d >= n1 + n2 (the case-(5) range) the volume is linear in d and the step
+// lands on the exact case-(5) solution; otherwise g is the cancellation-free
+// cubic of reduced_residual().  A trigonometric root that left its case
+// (possible where a case is a sliver, e.g. case (3) for n1 << n2) is moved back
+// by this step onto the neighbouring case's solution, which agrees with the
+// true root up to O(n1^2).
 template <typename T>
 __device__ __forceinline__ T polish(T d, T V, T n1, T n2, T n3) {
-    if (!(d > T(0)) || d >= n1 + n2) return d;
-    const T inv_n1 = n1 > T(0) ? T(1) / n1 : T(0);
+    typedef Fm<T> F;
+    const T n12 = n1 + n2;
+    if (d >= n12) return n3 * V + T(0.5) * n12;
+    if (!(d > T(0))) return d;
+    const T inv_n1 = n1 > T(0) ? F::rcp_(n1) : T(0);
     T g, gp;
     reduced_residual<T>(d, T(6) * n2 * n3 * V, n1, n2, n3, inv_n1, g, gp);
-    return gp > T(0) ? d - Fm<T>::div_(g, gp) : d;
+    return gp > T(0) ? d - F::div_(g, gp) : d;
 }
 
 // ----------------------------------------------------------------------------
@@ -130,35 +138,50 @@ __device__ __forceinline__ T solve_sz_orig(T w, T m1, T m2, T m3) {
     typedef Kc<T> K;
     const T m12 = m1 + m2;
     T alpha = T(0);
-    const T v1 = sq(m1) / (T(6) * m2 * m3 + T(1e-25));
+    const T v1 = F::div_(sq(m1), T(6) * m2 * m3 + T(1e-25));
     const T w6 = T(6) * m1 * m2 * m3 * w;
     if (w < v1) {
         alpha = F::cbrt_(w6);                                                     // case (1)
-    } else if (w < v1 + T(0.5) * (m2 - m1) / m3) {
+    } else if (w < v1 + F::div_(T(0.5) * (m2 - m1), m3)) {
         alpha = T(0.5) * (m1 + F::sqrt_(sq(m1) + T(8) * m2 * m3 * (w - v1)));     // case (2)
     } else {
         T v3;
         if (m3 < m12) {
             v3 = (sq(m3) * (T(3) * m12 - m3) + sq(m1) * (m1 - T(3) * m3) +
-                  sq(m2) * (m2 - T(3) * m3)) / (T(6) * m1 * m2 * m3);
+                  sq(m2) * (m2 - T(3) * m3)) * F::rcp_(T(6) * m1 * m2 * m3);
         } else {
-            v3 = T(0.5) * m12 / m3;
+            v3 = F::div_(T(0.5) * m12, m3);
             if (v3 <= w) alpha = m3 * w + T(0.5) * m12;                           // case (5)
         }
         if (alpha == T(0)) {
-            T a0, a1, a2;
-            if (w < v3) {                                                         // case (3)
-                a2 = T(-3) * m12;
-                a1 = T(3) * (sq(m1) + sq(m2));
-                a0 = w6 - cb(m1) - cb(m2);
-            } else {                                                              // case (4)
-                a2 = T(-1.5);
-                a1 = T(1.5) * (sq(m1) + sq(m2) + sq(m3));
-                a0 = T(0.5) * (w6 - cb(m1) - cb(m2) - cb(m3));
+            const bool case3 = w < v3;
+            T q0, sp, a2;
+            if (FAITHFUL) {
+                T a0, a1;
+                if (case3) {                                                      // case (3)
+                    a2 = T(-3) * m12;
+                    a1 = T(3) * (sq(m1) + sq(m2));
+                    a0 = w6 - cb(m1) - cb(m2);
+                } else {                                                          // case (4)
+                    a2 = T(-1.5);
+                    a1 = T(1.5) * (sq(m1) + sq(m2) + sq(m3));
+                    a0 = T(0.5) * (w6 - cb(m1) - cb(m2) - cb(m3));
+                }
+                q0 = K::sixth * (a1 * a2 - T(3) * a0) - K::inv27 * cb(a2);
+                sp = F::sqrt_(K::ninth * sq(a2) - K::third * a1);
+            } else {
+                // the same q0 and sp multiplied out: q0 = 1.5 m1 m2 (m12 - 2 m3 w),
+                // sp^2 = 2 m1 m2 in case (3); q0 = 0.75 m1 m2 m3 (1 - 2w),
+                // sp^2 = (m1 (2 (m2 + m3) - m1) - (m3 - m2)^2)/4 in case (4), using
+                // m1 + m2 + m3 = 1.  The printed forms subtract O(1) terms to get
+                // O(sp^3) and lose all digits when m1 << m2.
+                a2 = case3 ? T(-3) * m12 : T(-1.5);
+                q0 = case3 ? T(1.5) * m1 * m2 * (m12 - T(2) * m3 * w)
+                           : T(0.75) * m1 * m2 * m3 * (T(1) - T(2) * w);
+                sp = F::sqrt_(case3 ? T(2) * m1 * m2
+                                    : T(0.25) * (m1 * (T(2) * (m2 + m3) - m1) - sq(m3 - m2)));
             }
-            const T q0 = K::sixth * (a1 * a2 - T(3) * a0) - K::inv27 * cb(a2);
-            const T sp = F::sqrt_(K::ninth * sq(a2) - K::third * a1);
-            T arg = q0 / cb(sp);
+            T arg = F::div_(q0, cb(sp));
             if (!FAITHFUL) arg = fmin(fmax(arg, T(-1)), T(1));
             alpha = T(2) * sp * F::cos_(K::four_pi_3 + K::third * F::acos_(arg)) - K::third * a2;
         }
@@ -170,8 +193,8 @@ __device__ __forceinline__ T solve_sz_orig(T w, T m1, T m2, T m3) {
 // Sec. 2.4: the paper's optimised SZ solution (L1-normalised inputs, the
 // reduced volume V; returns the reduced offset in L1 units).
 // ----------------------------------------------------------------------------
-template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T solve_sz_opt(T V, T n1, T n2, T n3) {
+template <typename T>
+__device__ __forceinline__ T solve_sz_opt_listing(T V, T n1, T n2, T n3) {
     typedef Fm<T> F;
     typedef Kc<T> K;
     const T n12 = n1 + n2, n3V = n3 * V;
@@ -191,9 +214,56 @@ __device__ __forceinline__ T solve_sz_opt(T V, T n1, T n2, T n3) {
     const T b = case3 ? sqn12 : T(0.5) * (sqn12 + sq(n3));
     const T c = case3 ? n12 : T(0.5);
     const T t = F::sqrt_(sq(c) - b);
-    T arg = (cb(c) - T(0.5) * a - T(1.5) * b * c) / cb(t);
-    if (!FAITHFUL) arg = fmin(fmax(arg, T(-1)), T(1));
+    const T arg = (cb(c) - T(0.5) * a - T(1.5) * b * c) / cb(t);
     return c - T(2) * t * F::sin_(K::third * F::asin_(arg));
+}
+
+// Default form of the optimised SZ solution.  Same cases, thresholds and
+// trigonometric root as the listing, with
+//  - the case tests multiplied out so that no division is needed
+//    (v1 <= n3 V  <=>  n1^2 <= 6 n2 n3 V;  n3 V < v3  <=>  6 n1 n2 n3 V < num3),
+//  - the arcsine argument (c^3 - a/2 - 3bc/2)/t^3 written without cancellation:
+//    case (3): 1.5 n1 n2 (n1 + n2 - 2 n3 V) / (2 n1 n2)^(3/2),
+//    case (4): 0.75 n1 n2 n3 (1 - 2V) / t^3, t^2 = (n1 (2(n2+n3) - n1) - (n3-n2)^2)/4,
+//    (algebraically identical for n1 + n2 + n3 = 1), clamped to [-1, 1].
+// In FP32 every case is evaluated and the result selected (no divergent
+// branches; the warp pays for cases (1), (2) and (5) a few instructions each).
+// In FP64 the cases branch (the FP64 pipe is the bottleneck there).
+template <typename T>
+__device__ __forceinline__ T solve_sz_opt_default(T V, T n1, T n2, T n3) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T n12 = n1 + n2, n3V = n3 * V;
+    const T V6n2n3 = T(6) * n2 * n3V, sqn1 = n1 * n1;
+    const bool c5 = n12 <= T(2) * n3V;
+    const bool c1 = V6n2n3 < sqn1;
+    const bool c2 = !c1 && T(3) * n2 * (T(2) * n3V + n1 - n2) < sqn1;
+    const T n1n2 = n1 * n2;
+    const T num3 = sq(n3) * (T(3) * n12 - n3) + sqn1 * (n1 - T(3) * n3) + sq(n2) * (n2 - T(3) * n3);
+    const bool c3 = !(n3 < n12) || V6n2n3 * n1 < num3;
+    if (sizeof(T) == 8) {
+        if (c5) return n3V + T(0.5) * n12;
+        if (c2) return T(0.5) * (n1 + F::sqrt_(T(8) * n2 * n3V - K::third * sqn1));
+        if (c1) return F::cbrt_(V6n2n3 * n1);
+    }
+    const T q = c3 ? T(1.5) * n1n2 * (n12 - T(2) * n3V) : T(0.75) * n1n2 * n3 * (T(1) - T(2) * V);
+    const T t2 = c3 ? T(2) * n1n2 : T(0.25) * (n1 * (T(2) * (n2 + n3) - n1) - sq(n3 - n2));
+    const T c = c3 ? n12 : T(0.5);
+    const T rt = F::rsqrt_(t2);
+    const T t = t2 * rt;
+    const T arg = fmin(fmax(q * (rt * rt * rt), T(-1)), T(1));
+    const T d34 = c - T(2) * t * F::sin_(K::third * F::asin_(arg));
+    if (sizeof(T) == 8) return d34;
+    const T d5 = n3V + T(0.5) * n12;
+    const T d2 = T(0.5) * (n1 + F::sqrt_(T(8) * n2 * n3V - K::third * sqn1));
+    const T d1 = F::cbrt_(V6n2n3 * n1);
+    return c5 ? d5 : (c2 ? d2 : (c1 ? d1 : d34));
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_sz_opt(T V, T n1, T n2, T n3) {
+    if (FAITHFUL) return solve_sz_opt_listing<T>(V, n1, n2, n3);
+    return solve_sz_opt_default<T>(V, n1, n2, n3);
 }
 
 // ----------------------------------------------------------------------------
@@ -209,15 +279,18 @@ __device__ __forceinline__ T solve_sz_opt(T V, T n1, T n2, T n3) {
 template <typename T>
 __device__ __forceinline__ T newton_bracketed(T d, T lo, T hi, T rhs, T n1, T n2, T n3,
                                               T inv_n1) {
-    for (int it = 0; it < 64; ++it) {
+    // Newton converges quadratically from the bracket midpoint; 16 (FP64) or 10
+    // (FP32) steps are never reached in practice and bound the loop
+    constexpr int cap = sizeof(T) == 8 ? 16 : 10;
+    for (int it = 0; it < cap; ++it) {
         T g, gp;
         reduced_residual<T>(d, rhs, n1, n2, n3, inv_n1, g, gp);
         if (g < T(0)) lo = d; else hi = d;
-        T dn = gp > T(0) ? d - g / gp : T(0.5) * (lo + hi);
-        if (!(dn > lo && dn < hi)) dn = T(0.5) * (lo + hi);
+        T dn = gp > T(0) ? d - Fm<T>::div_(g, gp) : T(0.5) * (lo + hi);
+        if (!(dn >= lo && dn <= hi)) dn = T(0.5) * (lo + hi);
         const T step = fabs(dn - d);
         d = dn;
-        if (step <= T(2) * Fm<T>::eps() * d || hi - lo <= T(2) * Fm<T>::eps() * d) break;
+        if (step <= T(4) * Fm<T>::eps() * d) break;
     }
     return d;
 }
@@ -343,7 +416,8 @@ __device__ __forceinline__ T offset_cell(T nx, T ny, T nz, T V0, int& bad) {
     if (METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT) {
         // L1 normalisation (Sec. 2.4); the solvers return the offset in L1 units
         const T l = L;
-        const T m1 = n1 / l, m3 = n3 / l;
+        const T il = FAITHFUL ? T(1) / l : Fm<T>::rcp_(l);
+        const T m1 = n1 * il, m3 = n3 * il;
         const T m2 = Fm<T>::fdim_(T(1), m1 + m3);
         T a = METHOD == M_SZ_ORIG ? solve_sz_orig<T, FAITHFUL>(V, m1, m2, m3)
                                   : solve_sz_opt<T, FAITHFUL>(V, m1, m2, m3);
