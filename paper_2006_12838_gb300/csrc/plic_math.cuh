@@ -43,7 +43,9 @@ template <> struct Fm<float> {
     typedef float T;
     // sqrt and division: MUFU-based (rsqrt, rcp) forms; 1-2 ulp, enough for a
     // solver whose result is either used as is (FP32) or Newton-polished
-    static __device__ __forceinline__ T sqrt_(T x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+    static __device__ __forceinline__ T sqrt_(T x) {
+        return x > 0.0f ? x * rsqrtf(x) : (x == 0.0f ? 0.0f : __int_as_float(0x7fffffff));
+    }
     static __device__ __forceinline__ T rsqrt_(T x) { return rsqrtf(x); }
     // Cube root for x >= 0: 2^(log2(x)/3) from the MUFU pair (about 2^-22
     // relative), then one Newton step on r^3 = x, r <- r - (r^3 - x)/(3 r^2).

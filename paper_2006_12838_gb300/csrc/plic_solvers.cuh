@@ -273,21 +273,22 @@ __device__ __forceinline__ T solve_sz_opt(T V, T n1, T n2, T n3) {
 // Faithful: 7 steps from n1/2 (case 1), 4 steps (cases 3, 4), the cubic as
 // printed.  Default: the cancellation-free cubic g of reduced_residual(), a
 // start for case (1) from the exponent of 6 V n1 n2 n3, steps until
-// |dd| <= 2 ulp (at most 64) and a bracket safeguard (bisection whenever a step
-// leaves the bracket).
+// |dd| <= 4 ulp (at most 16) and a bracket safeguard (see newton_bracketed).
 // ----------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T newton_bracketed(T d, T lo, T hi, T rhs, T n1, T n2, T n3,
                                               T inv_n1) {
-    // Newton converges quadratically from the bracket midpoint; 16 (FP64) or 10
-    // (FP32) steps are never reached in practice and bound the loop
-    constexpr int cap = sizeof(T) == 8 ? 16 : 10;
-    for (int it = 0; it < cap; ++it) {
+    // A step that leaves the bracket is clamped to the bracket end it crossed
+    // (the root can sit exactly at an end, e.g. d = L/2 for V0 = 1/2); a second
+    // crossing of the same end bisects.  From the bracket midpoint this
+    // converges in at most 7 steps on the paper-shaped inputs; 16 bounds it.
+    for (int it = 0; it < 16; ++it) {
         T g, gp;
         reduced_residual<T>(d, rhs, n1, n2, n3, inv_n1, g, gp);
         if (g < T(0)) lo = d; else hi = d;
         T dn = gp > T(0) ? d - Fm<T>::div_(g, gp) : T(0.5) * (lo + hi);
-        if (!(dn >= lo && dn <= hi)) dn = T(0.5) * (lo + hi);
+        if (dn > hi) dn = d == hi ? T(0.5) * (lo + hi) : hi;
+        if (dn < lo) dn = d == lo ? T(0.5) * (lo + hi) : lo;
         const T step = fabs(dn - d);
         d = dn;
         if (step <= T(4) * Fm<T>::eps() * d) break;

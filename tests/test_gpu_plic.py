@@ -139,7 +139,9 @@ def test_ragged_and_misaligned(dev, n_cells):
         ref = plic.offset(*[x.contiguous() for x in aligned], method="sz_opt", precision=prec)
         sh = plic.offset(*shifted, method="sz_opt", precision=prec)
         ref_sh = plic.offset(*[x.clone() for x in shifted], method="sz_opt", precision=prec)
-        assert torch.equal(sh, ref_sh)
+        # the scalar and the vector loop may contract multiply-adds differently
+        tol = 1e-15 if dtype == torch.float64 else 2e-7
+        assert torch.allclose(sh, ref_sh, rtol=0, atol=tol)
         assert ref.shape[0] == n_cells
 
 
