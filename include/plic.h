@@ -134,6 +134,29 @@ plic_status vof_interface_compact(const float *phi, int nx, int ny, int nz, int3
                                   int64_t idx_capacity, int64_t *d_count, void *workspace,
                                   size_t ws_bytes, void *stream);
 
+/* vof_interface_compact_noalloc -- the same interface-cell list as
+ * vof_interface_compact (identical output), for callers that cannot allocate
+ * device memory: a solver that owns every byte of the GPU through its own
+ * pool, code that runs where cudaMalloc is not allowed or too slow to call (a
+ * real-time step loop, a callback that must not synchronise the device), or a
+ * foreign-language host without a device allocator.  The paper has no
+ * counterpart; this is a deployment variant.
+ * Its scratch (one int per tile of 4096 cells) is a fixed array inside the
+ * library, held by every GPU that loads the library until the process exits,
+ * so fields are limited to PLIC_NOALLOC_MAX_CELLS cells; larger fields return
+ * PLIC_ERR_ARG with an explanation in plic_last_error().  The call allocates
+ * nothing.  Its first call on a device looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing a stream into a graph.  All calls on a device share the
+ * one scratch array: calls that may run at the same time on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The scratch needs no clearing between calls.  Other arguments and the
+ * output are as for vof_interface_compact. */
+#define PLIC_NOALLOC_MAX_CELLS 268435456LL  /* 2^28 cells: 65536 tiles, 256 KiB */
+plic_status vof_interface_compact_noalloc(const float *phi, int nx, int ny, int nz,
+                                          int32_t *idx, int64_t idx_capacity,
+                                          int64_t *d_count, void *stream);
+
 /* vof_curvature -- curvature step of Sec. 4.2 with Appendix B, per interface
  * cell idx[k]: 3^3 stencil -> Parker-Youngs normal (Eq. 38) -> local frame ->
  * PLIC offsets d0(phi_i, n) of the centre and of every interface neighbour

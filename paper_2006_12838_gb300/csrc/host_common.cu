@@ -14,6 +14,13 @@ void set_last_error(const char* where, cudaError_t e) {
              cudaGetErrorString(e));
 }
 
+void set_limit_error(int64_t ncell) {
+    snprintf(g_last_error, sizeof g_last_error,
+             "vof_interface_compact_noalloc: field of %lld cells exceeds the limit of %lld cells "
+             "of the built-in scratch; use vof_interface_compact with a workspace",
+             (long long)ncell, (long long)PLIC_NOALLOC_MAX_CELLS);
+}
+
 plic_status check_launch(const char* where) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -12,6 +12,9 @@ namespace plic {
 // Thread-local text of the last CUDA error (plic_last_error()).
 void set_last_error(const char* where, cudaError_t e);
 
+// Records "field of n cells exceeds the allocation-free limit" as the error text.
+void set_limit_error(int64_t ncell);
+
 // Returns PLIC_ERR_CUDA (and records the text) if the last launch failed.
 plic_status check_launch(const char* where);
 

@@ -13,6 +13,9 @@
 //                        and a block scan.
 // HBM roofline: 4 B per field cell read once (pass 3 mostly hits L2), plus
 // 4 B per interface cell written.
+#include <mutex>
+#include <stdio.h>
+
 #include "host_common.h"
 
 namespace plic {
@@ -166,4 +169,75 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
     k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
     k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, ncell, tiles, idx, idx_capacity);
     return check_launch("vof_interface_compact");
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  The per-tile scratch of the three passes lives in
+// a file-scope device array instead of a caller-provided workspace.  Every
+// GPU that loads the library holds these 256 KiB until the process exits.
+// ---------------------------------------------------------------------------
+namespace plic {
+
+constexpr int64_t kNoAllocMaxTiles = PLIC_NOALLOC_MAX_CELLS / CT_TILE;
+static_assert(kNoAllocMaxTiles * CT_TILE == PLIC_NOALLOC_MAX_CELLS, "limit is whole tiles");
+
+static __device__ __align__(256) int g_noalloc_tiles[kNoAllocMaxTiles];
+
+// Device address of g_noalloc_tiles, looked up once per device (with that
+// device current) and cached; host code must not pass the symbol itself.
+static int* noalloc_scratch(plic_status* st) {
+    static std::mutex mu;
+    static int* addr[256] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256) {
+        set_last_error("vof_interface_compact_noalloc: cudaGetDevice", e);
+        *st = PLIC_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_tiles);
+        if (e != cudaSuccess || !p) {
+            set_last_error("vof_interface_compact_noalloc: cudaGetSymbolAddress", e);
+            *st = PLIC_ERR_CUDA;
+            return nullptr;
+        }
+        addr[dev] = reinterpret_cast<int*>(p);
+    }
+    return addr[dev];
+}
+
+}  // namespace plic
+
+extern "C" plic_status vof_interface_compact_noalloc(const float* phi, int nx, int ny, int nz,
+                                                     int32_t* idx, int64_t idx_capacity,
+                                                     int64_t* d_count, void* stream) {
+    using namespace plic;
+    if (nx < 0 || ny < 0 || nz < 0 || idx_capacity < 0 || !d_count) return PLIC_ERR_ARG;
+    const int64_t ncell = (int64_t)nx * ny * nz;
+    if (ncell > (int64_t)PLIC_NOALLOC_MAX_CELLS) {
+        set_limit_error(ncell);
+        return PLIC_ERR_ARG;
+    }
+    if (ncell > 0 && (!phi || (!idx && idx_capacity > 0))) return PLIC_ERR_ARG;
+    if (!aligned(d_count, 8) || (phi && !aligned(phi, 4)) || (idx && !aligned(idx, 4)))
+        return PLIC_ERR_ALIGN;
+    plic_status st = PLIC_OK;
+    int* tiles = noalloc_scratch(&st);
+    if (!tiles) return st;
+    cudaStream_t s = as_stream(stream);
+    if (ncell == 0) {
+        cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int64_t), s);
+        if (e != cudaSuccess) { set_last_error("vof_interface_compact_noalloc", e); return PLIC_ERR_CUDA; }
+        return PLIC_OK;
+    }
+    // every tile entry that a pass reads is written earlier in the same call,
+    // so the contents left by a previous call need no clearing
+    const int64_t nt = compact_tiles(ncell);
+    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, ncell, tiles);
+    k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
+    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, ncell, tiles, idx, idx_capacity);
+    return check_launch("vof_interface_compact_noalloc");
 }

@@ -68,6 +68,7 @@ def load():
             "plic_offset_backward": [P, P, P, P, P, P, P, P, P, I64, I32, P],
             "plic_volume_backward": [P, P, P, P, P, P, P, P, P, I64, I32, P],
             "vof_interface_compact": [P, I32, I32, I32, P, I64, P, P, SZ, P],
+            "vof_interface_compact_noalloc": [P, I32, I32, I32, P, I64, P, P],
             "vof_curvature": [P, I32, I32, I32, P, I64, P, P, I32, U32, P],
             "vof_curvature_backward": [P, I32, I32, I32, P, I64, P, P, P, I32, U32, P, SZ, P],
             "vof_curvature_batched": [P, I32, P, I32, U32, P, SZ, P],
