@@ -10,6 +10,7 @@
 // Roofline: 20 B/cell in FP32 (16 in, 4 out), 40 B/cell in FP64.  The FP32
 // solvers sit near the HBM/ALU balance point; FP64 is bound by the FP64 pipe.
 #include "host_common.h"
+#include "plic_pair.cuh"
 #include "plic_solvers.cuh"
 
 namespace plic {
@@ -60,6 +61,41 @@ k_plic_offset(const T* __restrict__ nx, const T* __restrict__ ny, const T* __res
     count_invalid(bad, invalid);
 }
 
+// The optimised SZ solution in FP32 (the paper's recommended solver, Sec.
+// 2.5) on paired FP32 instructions: each thread takes 4 cells per step as two
+// pairs.  Tail and unaligned cells go through the same pair code with the
+// cell duplicated in both lanes, so every cell sees identical arithmetic.
+template <bool POLISH>
+__global__ void __launch_bounds__(256)
+k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict__ ny,
+                          const float* __restrict__ nz, const float* __restrict__ V0,
+                          float* __restrict__ d0, int64_t n, int vec_ok,
+                          unsigned long long* invalid) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    const int64_t nvec = vec_ok ? n / 4 : 0;
+    for (int64_t i = tid; i < nvec; i += stride) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(nx) + i);
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(ny) + i);
+        const float4 c = __ldcs(reinterpret_cast<const float4*>(nz) + i);
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(V0) + i);
+        const float2 r0 = p2::offset_sz_opt<POLISH>(make_float2(a.x, a.y), make_float2(b.x, b.y),
+                                                    make_float2(c.x, c.y), make_float2(v.x, v.y), bad);
+        const float2 r1 = p2::offset_sz_opt<POLISH>(make_float2(a.z, a.w), make_float2(b.z, b.w),
+                                                    make_float2(c.z, c.w), make_float2(v.z, v.w), bad);
+        __stcs(reinterpret_cast<float4*>(d0) + i, make_float4(r0.x, r0.y, r1.x, r1.y));
+    }
+    for (int64_t i = nvec * 4 + tid; i < n; i += stride) {
+        int bad2 = 0;
+        const float2 r = p2::offset_sz_opt<POLISH>(make_float2(nx[i], nx[i]), make_float2(ny[i], ny[i]),
+                                                   make_float2(nz[i], nz[i]), make_float2(V0[i], V0[i]), bad2);
+        bad += bad2 >> 1;
+        d0[i] = r.x;
+    }
+    count_invalid(bad, invalid);
+}
+
 typedef void (*offset_kernel_t)(const void*, const void*, const void*, const void*, void*,
                                 int64_t, int, unsigned long long*);
 
@@ -100,7 +136,13 @@ extern "C" plic_status plic_offset(const void* nx, const void* ny, const void* n
     switch (m) {
         case PLIC_ANALYTIC: k = pick<M_ANALYTIC>(p, faithful); break;
         case PLIC_SZ_ORIG: k = pick<M_SZ_ORIG>(p, faithful); break;
-        case PLIC_SZ_OPT: k = pick<M_SZ_OPT>(p, faithful); break;
+        case PLIC_SZ_OPT:
+            if (p != PLIC_FP64 && !faithful)
+                k = p == PLIC_FP32_POLISHED ? reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<true>)
+                                            : reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<false>);
+            else
+                k = pick<M_SZ_OPT>(p, faithful);
+            break;
         case PLIC_NEWTON: k = pick<M_NEWTON>(p, faithful); break;
         case PLIC_NESTED: k = pick<M_NESTED>(p, faithful); break;
     }

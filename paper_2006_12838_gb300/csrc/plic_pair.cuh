@@ -1,0 +1,170 @@
+// plic_pair.cuh -- the FP32 fast path of the optimised SZ solution (Sec. 2.4)
+// for two cells at once, on the paired FP32 instructions of sm_100+ (one
+// FFMA2/FADD2/FMUL2 issues two FP32 operations).  Comparisons, selects and
+// MUFU operations stay per component.
+//
+// The arithmetic is that of solve_sz_opt_default<float> + polish (see
+// plic_solvers.cuh): the division-free case tests, the cancellation-free
+// arcsine argument, all cases evaluated and selected, and, for the polished
+// precision, one Newton step on the cubic of Eq. 10 for the cells whose root
+// came from the trigonometric formula (cases 3/4; the closed forms of cases
+// 1, 2, 5 are already accurate to a few ulp).
+#pragma once
+#include "plic_solvers.cuh"
+
+namespace plic {
+namespace p2 {
+
+typedef float2 f2;
+
+__device__ __forceinline__ f2 mk(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 sub(f2 a, f2 b) { return __ffma2_rn(b, mk(-1.0f), a); }
+__device__ __forceinline__ f2 fmax0(f2 a) { return make_float2(fmaxf(a.x, 0.0f), fmaxf(a.y, 0.0f)); }
+
+struct b2 { bool x, y; };
+__device__ __forceinline__ f2 sel(b2 c, f2 a, f2 b) { return make_float2(c.x ? a.x : b.x, c.y ? a.y : b.y); }
+__device__ __forceinline__ b2 lt(f2 a, f2 b) { return {a.x < b.x, a.y < b.y}; }
+__device__ __forceinline__ b2 le(f2 a, f2 b) { return {a.x <= b.x, a.y <= b.y}; }
+
+__device__ __forceinline__ f2 rsqrt(f2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ f2 rcp(f2 a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
+__device__ __forceinline__ f2 sqrt_(f2 a) {
+    return make_float2(Fm<float>::sqrt_(a.x), Fm<float>::sqrt_(a.y));
+}
+
+// cube root of x >= 0: MUFU exp2(log2(x)/3) and one Newton step (see Fm<float>)
+__device__ __forceinline__ f2 cbrt_(f2 x) {
+    f2 s = mk(1.0f);
+    if (x.x < 1e-30f) { x.x *= 4.7223665e21f; s.x = 5.9604645e-08f; }
+    if (x.y < 1e-30f) { x.y *= 4.7223665e21f; s.y = 5.9604645e-08f; }
+    f2 r = make_float2(Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.x) * (1.0f / 3.0f)),
+                       Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.y) * (1.0f / 3.0f)));
+    const f2 r2 = mul(r, r);
+    const f2 res = fma(r2, r, make_float2(-x.x, -x.y));           // r^3 - x
+    const f2 inv = rcp(mul(mk(3.0f), r2));
+    r = fma(make_float2(-res.x, -res.y), inv, r);
+    r = mul(s, r);
+    return make_float2(x.x > 0.0f ? r.x : 0.0f, x.y > 0.0f ? r.y : 0.0f);
+}
+
+// arcsine by the series of fast_asinf (Maclaurin series of arcsin to s^17 on
+// s <= 1/2, half-angle reduction above), two lanes at once
+__device__ __forceinline__ f2 asin_(f2 x) {
+    const f2 a = make_float2(fabsf(x.x), fabsf(x.y));
+    const b2 big = lt(mk(0.5f), a);
+    const f2 zb = mul(mk(0.5f), sub(mk(1.0f), a));
+    const f2 z = sel(big, zb, mul(a, a));
+    const f2 sb = make_float2(z.x > 0.0f ? z.x * rsqrtf(z.x) : 0.0f, z.y > 0.0f ? z.y * rsqrtf(z.y) : 0.0f);
+    const f2 s = sel(big, sb, a);
+    f2 p = mk(0.011551800896139705f);
+    p = fma(p, z, mk(0.01396484375f));
+    p = fma(p, z, mk(0.017352764423076924f));
+    p = fma(p, z, mk(0.022372159090909092f));
+    p = fma(p, z, mk(0.030381944444444444f));
+    p = fma(p, z, mk(0.044642857142857144f));
+    p = fma(p, z, mk(0.075f));
+    p = fma(p, z, mk(0.16666666666666666f));
+    p = fma(mul(s, z), p, s);
+    const f2 r = sel(big, fma(mk(-2.0f), p, mk(1.5707963267948966f)), p);
+    return make_float2(copysignf(r.x, x.x), copysignf(r.y, x.y));
+}
+
+// Reduced optimised-SZ solution for two cells (L1-normalised m1 <= m2 <= m3,
+// reduced volume V); returns the reduced offsets and whether the trigonometric
+// root was taken.
+__device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3, b2& trig) {
+    const f2 n12 = add(n1, n2), n3V = mul(n3, V);
+    const f2 n3V2 = add(n3V, n3V);
+    const f2 V6n2n3 = mul(mul(mk(6.0f), n2), n3V), sqn1 = mul(n1, n1);
+    const b2 c5 = le(n12, n3V2);
+    const b2 c1 = lt(V6n2n3, sqn1);
+    // case (2) upper test 3 n2 (2 n3 V + n1 - n2) < n1^2
+    const f2 t2a = mul(mul(mk(3.0f), n2), add(n3V2, sub(n1, n2)));
+    const b2 c2u = lt(t2a, sqn1);
+    const b2 c2 = {!c1.x && c2u.x, !c1.y && c2u.y};
+    const f2 n1n2 = mul(n1, n2);
+    // case (3) vs (4): 6 n1 n2 n3 V < n3^2 (3 n12 - n3) + n1^2 (n1 - 3 n3) + n2^2 (n2 - 3 n3)
+    f2 num3 = mul(mul(n3, n3), fma(mk(3.0f), n12, make_float2(-n3.x, -n3.y)));
+    num3 = fma(sqn1, fma(mk(-3.0f), n3, n1), num3);
+    num3 = fma(mul(n2, n2), fma(mk(-3.0f), n3, n2), num3);
+    const b2 n3small = lt(n3, n12);
+    const b2 v3lt = lt(mul(V6n2n3, n1), num3);
+    const b2 c3 = {!n3small.x || v3lt.x, !n3small.y || v3lt.y};
+    // arcsine argument without cancellation
+    const f2 q3 = mul(mul(mk(1.5f), n1n2), sub(n12, n3V2));
+    const f2 q4 = mul(mul(mul(mk(0.75f), n1n2), n3), fma(mk(-2.0f), V, mk(1.0f)));
+    const f2 d32 = sub(n3, n2);
+    const f2 t24 = mul(mk(0.25f), fma(n1, fma(mk(2.0f), add(n2, n3), make_float2(-n1.x, -n1.y)),
+                                     make_float2(-d32.x * d32.x, -d32.y * d32.y)));
+    const f2 q = sel(c3, q3, q4);
+    const f2 t2 = sel(c3, add(n1n2, n1n2), t24);
+    const f2 c = sel(c3, n12, mk(0.5f));
+    const f2 rt = rsqrt(t2);
+    const f2 t = mul(t2, rt);
+    f2 arg = mul(q, mul(rt, mul(rt, rt)));
+    arg = make_float2(fminf(fmaxf(arg.x, -1.0f), 1.0f), fminf(fmaxf(arg.y, -1.0f), 1.0f));
+    const f2 th = mul(mk(0.33333333333333333f), asin_(arg));
+    const f2 sn = make_float2(__sinf(th.x), __sinf(th.y));
+    const f2 d34 = fma(mul(mk(-2.0f), t), sn, c);
+    // closed forms
+    const f2 d5 = fma(mk(0.5f), n12, n3V);
+    const f2 d2 = mul(mk(0.5f), add(n1, sqrt_(fma(mk(8.0f), mul(n2, n3V), mul(mk(-0.33333333333333333f), sqn1)))));
+    const f2 d1 = cbrt_(mul(V6n2n3, n1));
+    trig = {!c5.x && !c2.x && !c1.x, !c5.y && !c2.y && !c1.y};
+    f2 d = sel(c1, d1, d34);
+    d = sel(c2, d2, d);
+    return sel(c5, d5, d);
+}
+
+// One Newton step on the cubic of Eq. 10 for cases (3)/(4) (d >= n2, n1 > 0):
+// g = 3 d (d - n1) + n1^2 - ((d - n2)^3 + (d - n3)_+^3)/n1 - 6 n2 n3 V
+__device__ __forceinline__ f2 polish34(f2 d, f2 V, f2 n1, f2 n2, f2 n3) {
+    const f2 e2 = fmax0(sub(d, n2)), e3 = fmax0(sub(d, n3));
+    const f2 inv1 = rcp(n1);
+    const f2 e22 = mul(e2, e2), e33 = mul(e3, e3);
+    const f2 cub = fma(e22, e2, mul(e33, e3));
+    const f2 dd = sub(d, n1);
+    f2 g = fma(mk(3.0f), mul(d, dd), mul(n1, n1));
+    g = fma(make_float2(-cub.x, -cub.y), inv1, g);
+    g = fma(mk(-6.0f), mul(mul(n2, n3), V), g);
+    f2 gp = fma(mk(6.0f), d, mul(mk(-3.0f), n1));
+    gp = fma(mk(-3.0f), mul(add(e22, e33), inv1), gp);
+    const f2 step = mul(g, rcp(gp));
+    const f2 dn = sub(d, step);
+    return make_float2(gp.x > 0.0f ? dn.x : d.x, gp.y > 0.0f ? dn.y : d.y);
+}
+
+// Whole cells: two (n, V0) -> d0 by the optimised SZ solution in FP32.
+template <bool POLISH>
+__device__ __forceinline__ f2 offset_sz_opt(f2 nx, f2 ny, f2 nz, f2 V0, int& bad) {
+    const f2 ax = make_float2(fabsf(nx.x), fabsf(nx.y));
+    const f2 ay = make_float2(fabsf(ny.x), fabsf(ny.y));
+    const f2 az = make_float2(fabsf(nz.x), fabsf(nz.y));
+    const f2 n1 = make_float2(fminf(fminf(ax.x, ay.x), az.x), fminf(fminf(ax.y, ay.y), az.y));
+    const f2 n3 = make_float2(fmaxf(fmaxf(ax.x, ay.x), az.x), fmaxf(fmaxf(ax.y, ay.y), az.y));
+    const f2 L = add(add(ax, ay), az);
+    const bool okx = V0.x >= 0.0f && V0.x <= 1.0f && L.x > 0.0f && L.x <= 3.0f;
+    const bool oky = V0.y >= 0.0f && V0.y <= 1.0f && L.y > 0.0f && L.y <= 3.0f;
+    bad += (int)!okx + (int)!oky;
+    const f2 il = rcp(L);
+    const f2 m1 = mul(n1, il), m3 = mul(n3, il);
+    const f2 m2 = fmax0(sub(mk(1.0f), add(m1, m3)));
+    const f2 V = make_float2(V0.x <= 0.5f ? V0.x : 1.0f - V0.x, V0.y <= 0.5f ? V0.y : 1.0f - V0.y);
+    b2 trig;
+    f2 a = sz_opt(V, m1, m2, m3, trig);
+    if (POLISH) {
+        const f2 ap = polish34(a, V, m1, m2, m3);
+        a = sel(trig, ap, a);
+    }
+    const f2 h = sub(mk(0.5f), a);
+    f2 r = mul(L, make_float2(copysignf(h.x, V0.x - 0.5f), copysignf(h.y, V0.y - 0.5f)));
+    if (!okx) r.x = __int_as_float(0x7fffffff);
+    if (!oky) r.y = __int_as_float(0x7fffffff);
+    return r;
+}
+
+}  // namespace p2
+}  // namespace plic
