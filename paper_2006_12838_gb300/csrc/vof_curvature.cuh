@@ -116,58 +116,71 @@ __host__ __device__ constexpr int uidx(int i, int j) {
     return i <= j ? i * 5 - i * (i - 1) / 2 + (j - i) : j * 5 - j * (j - 1) / 2 + (i - j);
 }
 
-// Solve the leading block of M x = b by LDL^T (Appendix B reduces the fit
-// dimension when fewer than 5 points exist).  The dimension is min(m, 5),
-// reduced to j at the first pivot D_j <= 1e-6 trace(M) (D_j is the ratio of
-// consecutive leading principal minors).  Unused parameters are 0.  Returns
-// the dimension used.
+// LDL^T factorisation of the leading block of the symmetric normal matrix
+// (Appendix B reduces the fit dimension when fewer than 5 points exist).  The
+// dimension is min(m, 5), reduced to j at the first pivot D_j <= 1e-6 trace(M)
+// (D_j is the ratio of consecutive leading principal minors).  solve() uses
+// the factors for any right-hand side (the fit, and the adjoint system of the
+// backward pass); unused parameters are 0.
 template <int FIT>
-__device__ __forceinline__ int fit_solve(const float* Mf, const float* bf, int m, float x[5]) {
+struct Ldlt {
     typedef FitReal<FIT> F;
     typedef typename F::R R;
-    const float trace = Mf[uidx(0, 0)] + Mf[uidx(1, 1)] + Mf[uidx(2, 2)] + Mf[uidx(3, 3)] + Mf[uidx(4, 4)];
-    const R tol = F::mk(1e-6f * trace);
     R Lm[5][5], D[5];
-    int dim = m < 5 ? m : 5;
+    int dim;
+    __device__ __forceinline__ void factor(const float* Mf, int m) {
+        const float trace = Mf[uidx(0, 0)] + Mf[uidx(1, 1)] + Mf[uidx(2, 2)] + Mf[uidx(3, 3)] + Mf[uidx(4, 4)];
+        const R tol = F::mk(1e-6f * trace);
+        dim = m < 5 ? m : 5;
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        R dj = F::mk(Mf[uidx(j, j)]);
+        for (int j = 0; j < 5; ++j) {
+            R dj = F::mk(Mf[uidx(j, j)]);
 #pragma unroll
-        for (int k = 0; k < j; ++k) dj = F::sub(dj, F::mul(F::mul(Lm[j][k], Lm[j][k]), D[k]));
-        const bool act = j < dim;
-        if (act && !F::gt(dj, tol)) dim = j;
-        D[j] = dj;
-        const bool use = j < dim;
-        const R inv = use ? F::div(F::mk(1.0f), dj) : F::mk(0.0f);
+            for (int k = 0; k < j; ++k) dj = F::sub(dj, F::mul(F::mul(Lm[j][k], Lm[j][k]), D[k]));
+            const bool act = j < dim;
+            if (act && !F::gt(dj, tol)) dim = j;
+            D[j] = dj;
+            const bool use = j < dim;
+            const R inv = use ? F::div(F::mk(1.0f), dj) : F::mk(0.0f);
 #pragma unroll
-        for (int i = j + 1; i < 5; ++i) {
-            R s = F::mk(Mf[uidx(i, j)]);
+            for (int i = j + 1; i < 5; ++i) {
+                R s = F::mk(Mf[uidx(i, j)]);
 #pragma unroll
-            for (int k = 0; k < j; ++k) s = F::sub(s, F::mul(F::mul(Lm[i][k], Lm[j][k]), D[k]));
-            Lm[i][j] = F::mul(s, inv);
+                for (int k = 0; k < j; ++k) s = F::sub(s, F::mul(F::mul(Lm[i][k], Lm[j][k]), D[k]));
+                Lm[i][j] = F::mul(s, inv);
+            }
         }
     }
-    R y[5];
+    __device__ __forceinline__ void solve(const float* bf, float x[5]) const {
+        R y[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        R s = F::mk(bf[i]);
+        for (int i = 0; i < 5; ++i) {
+            R s = F::mk(bf[i]);
 #pragma unroll
-        for (int k = 0; k < i; ++k) s = F::sub(s, F::mul(Lm[i][k], y[k]));
-        y[i] = i < dim ? s : F::mk(0.0f);
+            for (int k = 0; k < i; ++k) s = F::sub(s, F::mul(Lm[i][k], y[k]));
+            y[i] = i < dim ? s : F::mk(0.0f);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) y[i] = i < dim ? F::div(y[i], D[i]) : F::mk(0.0f);
+        R xs[5];
+#pragma unroll
+        for (int i = 4; i >= 0; --i) {
+            R s = y[i];
+#pragma unroll
+            for (int k = i + 1; k < 5; ++k) s = F::sub(s, F::mul(Lm[k][i], xs[k]));
+            xs[i] = i < dim ? s : F::mk(0.0f);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) x[i] = F::tof(xs[i]);
     }
-#pragma unroll
-    for (int i = 0; i < 5; ++i) y[i] = i < dim ? F::div(y[i], D[i]) : F::mk(0.0f);
-    R xs[5];
-#pragma unroll
-    for (int i = 4; i >= 0; --i) {
-        R s = y[i];
-#pragma unroll
-        for (int k = i + 1; k < 5; ++k) s = F::sub(s, F::mul(Lm[k][i], xs[k]));
-        xs[i] = i < dim ? s : F::mk(0.0f);
-    }
-#pragma unroll
-    for (int i = 0; i < 5; ++i) x[i] = F::tof(xs[i]);
-    return dim;
+};
+
+template <int FIT>
+__device__ __forceinline__ int fit_solve(const float* Mf, const float* bf, int m, float x[5]) {
+    Ldlt<FIT> f;
+    f.factor(Mf, m);
+    f.solve(bf, x);
+    return f.dim;
 }
 
 // Eq. 42 at the origin: (A (I^2+1) + B (H^2+1) - C H I) / (H^2 + I^2 + 1)^(3/2).

@@ -1,6 +1,275 @@
-// vof_curvature_bwd.cu -- vector-Jacobian product of the curvature step with
-// respect to the fill field (placeholder until the adjoint kernel lands).
+// vof_curvature_bwd.cu -- vector-Jacobian product of the curvature step
+// (Sec. 4.2, Appendix B) with respect to the fill field:
+//   g_phi = d(sum_k g_kappa[k] kappa[k]) / d phi,
+// with the interface set (the list and the 0 < phi < 1 flags of the stencil)
+// held fixed.
+//
+// Per interface cell (one thread), the forward step is recomputed and reversed:
+//   kappa = s N / (1 + H^2 + I^2)^(3/2), N = A (I^2+1) + B (H^2+1) - C H I (Eq. 42)
+//     -> pbar = dkappa/d(A,B,C,H,I) * g_kappa
+//   M p = b (leading block, Appendix B)  ->  bbar = M^-1 pbar (same LDL^T factors),
+//     Mbar = -bbar p^T
+//   M = sum Q Q^T, b = sum z Q  ->  Qbar_i = bbar (z_i - p.Q_i) - p (bbar.Q_i),
+//     zbar_i = bbar.Q_i; Q = (x^2, y^2, xy, x, y) -> xbar_i, ybar_i
+//   x_i = e_i.b_x, y_i = e_i.b_y, z_i = e_i.n + d0_i - d0_0 (Eq. 36)
+//   d0_i = d0(phi_i, n): dd0/dphi = 1/A_i, dd0/dn = c_i (cut-polygon area and
+//     centroid, implicit function theorem on Eq. 1)
+//   b_x = b_y x n, b_y = u/|u|, u = n x r (Sec. 4.2)
+//   n = -g/|g|, g = sum w_i e_i phi_i (Eq. 38)
+// The 27 partial derivatives of each cell go to the workspace; a second kernel
+// sums, for every field cell j, the entries of the (at most 27) interface cells
+// whose stencil contains j, in a fixed order -- deterministic, no atomics.
+// Only the foot-point variant (Eq. 36) is differentiated.
 #include "host_common.h"
+#include "vof_curvature.cuh"
+
+namespace plic {
+
+constexpr int CB_THREADS = 128;
+
+__device__ __forceinline__ void cross3(float ax, float ay, float az, float bx, float by, float bz,
+                                       float& cx, float& cy, float& cz) {
+    cx = ay * bz - az * by;
+    cy = az * bx - ax * bz;
+    cz = ax * by - ay * bx;
+}
+
+template <int METHOD, int FIT>
+__global__ void __launch_bounds__(CB_THREADS)
+k_vof_curvature_vjp(const float* __restrict__ phi, int nx, int ny,
+                    const int32_t* __restrict__ idx, int64_t n, const int64_t* __restrict__ d_n,
+                    const float* __restrict__ g_kappa, float* __restrict__ contrib, uint32_t flags) {
+    __shared__ float s_d0[26][CB_THREADS];
+    __shared__ float s_g[27][CB_THREADS];
+    int64_t lim = n;
+    if (d_n) {
+        const int64_t dn = *d_n;
+        lim = dn < n ? dn : n;
+    }
+    const int t = threadIdx.x;
+    const int64_t nxy = (int64_t)nx * ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + t; k < lim;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = __ldg(idx + k);
+        const float gk = __ldg(g_kappa + k);
+#pragma unroll 1
+        for (int i = 0; i < 27; ++i) s_g[i][t] = 0.0f;
+        // ---- forward: Parker-Youngs gradient and normal ----
+        float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const float* row = phi + c + dz * nxy + (int64_t)dy * nx;
+                const float a = __ldg(row - 1), b = __ldg(row), e = __ldg(row + 1);
+                const float wy = dy == 0 ? 2.0f : 1.0f, wz = dz == 0 ? 2.0f : 1.0f;
+                const float sum = a + 2.0f * b + e;
+                gx += wy * wz * (e - a);
+                gy += dy * wz * sum;
+                gz += dz * wy * sum;
+            }
+        const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
+        bool zero = !(gl > 0.0f) || gk == 0.0f;
+        float nx_ = 0, ny_ = 0, nz_ = 0, rx = 0.56270900f, ry = 0.32704452f, rz = 0.75921047f;
+        float ux = 0, uy = 0, uz = 0, ul = 1, byx = 0, byy = 0, byz = 0, bxx = 0, bxy = 0, bxz = 0;
+        float d00 = 0.0f;
+        float M[15], bv[5];
+#pragma unroll
+        for (int q = 0; q < 15; ++q) M[q] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) bv[q] = 0.0f;
+        int m = 0;
+        CellPlic<METHOD> pl;
+        if (!zero) {
+            const float inv = -1.0f / gl;
+            nx_ = gx * inv; ny_ = gy * inv; nz_ = gz * inv;
+            cross3(nx_, ny_, nz_, rx, ry, rz, ux, uy, uz);
+            float u2 = ux * ux + uy * uy + uz * uz;
+            if (!(u2 > 1e-12f)) {
+                rx = 0.32704452f; ry = 0.75921047f; rz = 0.56270900f;
+                cross3(nx_, ny_, nz_, rx, ry, rz, ux, uy, uz);
+                u2 = ux * ux + uy * uy + uz * uz;
+            }
+            ul = sqrtf(u2);
+            const float iu = 1.0f / ul;
+            byx = ux * iu; byy = uy * iu; byz = uz * iu;
+            cross3(byx, byy, byz, nx_, ny_, nz_, bxx, bxy, bxz);
+            pl.prepare(nx_, ny_, nz_);
+            d00 = pl.offset(__ldg(phi + c));
+#pragma unroll 1
+            for (int i = 1; i < 27; ++i) {
+                int ex, ey, ez;
+                e_of(i, ex, ey, ez);
+                const float v = __ldg(phi + c + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
+                if (!(v > 0.0f && v < 1.0f)) continue;
+                const float d0i = pl.offset(v);
+                s_d0[i - 1][t] = d0i;
+                const float x = ex * bxx + ey * bxy + ez * bxz;
+                const float y = ex * byx + ey * byy + ez * byz;
+                const float z = ex * nx_ + ey * ny_ + ez * nz_ + (d0i - d00);
+                const float Q[5] = {x * x, y * y, x * y, x, y};
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+#pragma unroll
+                    for (int b = a; b < 5; ++b) M[uidx(a, b)] = fmaf(Q[a], Q[b], M[uidx(a, b)]);
+                    bv[a] = fmaf(z, Q[a], bv[a]);
+                }
+                ++m;
+            }
+        }
+        Ldlt<FIT> fac;
+        float p[5] = {0, 0, 0, 0, 0};
+        if (!zero) {
+            fac.factor(M, m);
+            fac.solve(bv, p);
+            zero = fac.dim == 0;
+        }
+        if (!zero) {
+            // ---- Eq. 42 backward ----
+            const float s = (flags & PLIC_FLAG_KAPPA_PAPER_SIGN) ? 1.0f : -1.0f;
+            const float A = p[0], B = p[1], C = p[2], H = p[3], I = p[4];
+            const float w = 1.0f + H * H + I * I;
+            const float rw = rsqrtf(w);
+            const float iD = rw * rw * rw;                       // (1+H^2+I^2)^(-3/2)
+            const float N = A * (I * I + 1.0f) + B * (H * H + 1.0f) - C * H * I;
+            const float sg = s * gk * iD;
+            float pbar[5];
+            pbar[0] = sg * (I * I + 1.0f);
+            pbar[1] = sg * (H * H + 1.0f);
+            pbar[2] = -sg * H * I;
+            pbar[3] = sg * (2.0f * B * H - C * I - 3.0f * H * N / w);
+            pbar[4] = sg * (2.0f * A * I - C * H - 3.0f * I * N / w);
+            // ---- solve backward: bbar = M^-1 pbar (leading block) ----
+            float bb[5];
+            fac.solve(pbar, bb);
+            // ---- points backward ----
+            float bxbx = 0, bxby = 0, bxbz = 0, bybx = 0, byby = 0, bybz = 0;  // bbar_x, bbar_y
+            float nbx = 0, nby = 0, nbz = 0, d00b = 0;
+#pragma unroll 1
+            for (int i = 1; i < 27; ++i) {
+                int ex, ey, ez;
+                e_of(i, ex, ey, ez);
+                const float v = __ldg(phi + c + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
+                if (!(v > 0.0f && v < 1.0f)) continue;
+                const float d0i = s_d0[i - 1][t];
+                const float x = ex * bxx + ey * bxy + ez * bxz;
+                const float y = ex * byx + ey * byy + ez * byz;
+                const float z = ex * nx_ + ey * ny_ + ez * nz_ + (d0i - d00);
+                const float Q[5] = {x * x, y * y, x * y, x, y};
+                float pQ = 0.0f, bQ = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    pQ = fmaf(p[a], Q[a], pQ);
+                    bQ = fmaf(bb[a], Q[a], bQ);
+                }
+                const float res = z - pQ;
+                float Qb[5];
+#pragma unroll
+                for (int a = 0; a < 5; ++a) Qb[a] = bb[a] * res - p[a] * bQ;
+                const float xb = 2.0f * x * Qb[0] + y * Qb[2] + Qb[3];
+                const float yb = 2.0f * y * Qb[1] + x * Qb[2] + Qb[4];
+                const float zb = bQ;
+                bxbx += xb * ex; bxby += xb * ey; bxbz += xb * ez;
+                bybx += yb * ex; byby += yb * ey; bybz += yb * ez;
+                nbx += zb * ex; nby += zb * ey; nbz += zb * ez;
+                d00b -= zb;
+                // d0_i = d0(phi_i, n)
+                float Ai, cx, cy, cz;
+                if (cut_polygon<float>(nx_, ny_, nz_, d0i, Ai, cx, cy, cz)) {
+                    s_g[i][t] += zb / Ai;
+                    nbx += zb * cx; nby += zb * cy; nbz += zb * cz;
+                }
+            }
+            {
+                float A0, cx, cy, cz;
+                if (cut_polygon<float>(nx_, ny_, nz_, d00, A0, cx, cy, cz)) {
+                    s_g[0][t] += d00b / A0;
+                    nbx += d00b * cx; nby += d00b * cy; nbz += d00b * cz;
+                }
+            }
+            // ---- frame backward: b_x = b_y x n ----
+            float tx, ty, tz;
+            cross3(bxbx, bxby, bxbz, byx, byy, byz, tx, ty, tz);     // nbar += bxbar x b_y
+            nbx += tx; nby += ty; nbz += tz;
+            cross3(nx_, ny_, nz_, bxbx, bxby, bxbz, tx, ty, tz);     // bybar += n x bxbar
+            bybx += tx; byby += ty; bybz += tz;
+            // b_y = u/|u|, u = n x r
+            const float dp = byx * bybx + byy * byby + byz * bybz;
+            const float iu = 1.0f / ul;
+            const float ubx = (bybx - byx * dp) * iu, uby = (byby - byy * dp) * iu, ubz = (bybz - byz * dp) * iu;
+            cross3(rx, ry, rz, ubx, uby, ubz, tx, ty, tz);           // nbar += r x ubar
+            nbx += tx; nby += ty; nbz += tz;
+            // ---- normal backward: n = -g/|g| ----
+            const float nn = nx_ * nbx + ny_ * nby + nz_ * nbz;
+            const float ig = -1.0f / gl;
+            const float gbx = (nbx - nx_ * nn) * ig, gby = (nby - ny_ * nn) * ig, gbz = (nbz - nz_ * nn) * ig;
+            // ---- Parker-Youngs backward: g = sum w_i e_i phi_i ----
+#pragma unroll 1
+            for (int i = 1; i < 27; ++i) {
+                int ex, ey, ez;
+                e_of(i, ex, ey, ez);
+                const int e2 = ex * ex + ey * ey + ez * ez;
+                const float wi = e2 == 1 ? 4.0f : (e2 == 2 ? 2.0f : 1.0f);
+                s_g[i][t] += wi * (ex * gbx + ey * gby + ez * gbz);
+            }
+        }
+        float* out = contrib + k * 27;
+#pragma unroll 1
+        for (int i = 0; i < 27; ++i) out[i] = s_g[i][t];
+    }
+}
+
+__global__ void k_curv_slot_scatter(const int32_t* __restrict__ idx, int64_t n,
+                                    const int64_t* __restrict__ d_n, int32_t* __restrict__ slot) {
+    int64_t lim = n;
+    if (d_n) {
+        const int64_t dn = *d_n;
+        lim = dn < n ? dn : n;
+    }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lim;
+         k += (int64_t)gridDim.x * blockDim.x)
+        slot[idx[k]] = (int32_t)k;
+}
+
+// g_phi[j] = sum over the 27 offsets o of contrib[slot[j - e_o]][o] (when cell
+// j - e_o is in the field and in the list).  One warp per row, one lane per x.
+__global__ void __launch_bounds__(256)
+k_curv_gather(const int32_t* __restrict__ slot, const float* __restrict__ contrib, int nx, int ny,
+              int nz, float* __restrict__ g_phi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = (int64_t)ny * nz;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nxy = (int64_t)nx * ny;
+    for (int64_t r = warp0; r < rows; r += nwarps) {
+        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
+        for (int x = lane; x < nx; x += 32) {
+            const int64_t j = r * nx + x;
+            float acc = 0.0f;
+#pragma unroll
+            for (int o = 0; o < 27; ++o) {
+                int ex, ey, ez;
+                e_of(o, ex, ey, ez);
+                const int sx = x - ex, sy = y - ey, sz = z - ez;
+                if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz) continue;
+                const int32_t sl = __ldg(slot + (j - ex - (int64_t)ey * nx - (int64_t)ez * nxy));
+                if (sl >= 0) acc += __ldg(contrib + (int64_t)sl * 27 + o);
+            }
+            g_phi[j] = acc;
+        }
+    }
+}
+
+template <int METHOD>
+static const void* pick_vjp(int fit) {
+    switch (fit) {
+        case FIT_FP32: return reinterpret_cast<const void*>(&k_vof_curvature_vjp<METHOD, FIT_FP32>);
+        case FIT_DF32: return reinterpret_cast<const void*>(&k_vof_curvature_vjp<METHOD, FIT_DF32>);
+        default: return reinterpret_cast<const void*>(&k_vof_curvature_vjp<METHOD, FIT_FP64>);
+    }
+}
+
+}  // namespace plic
 
 extern "C" size_t plic_curv_bwd_workspace_bytes(int64_t cells, int64_t n_iface) {
     if (cells < 0 || n_iface < 0) return 0;
@@ -9,8 +278,53 @@ extern "C" size_t plic_curv_bwd_workspace_bytes(int64_t cells, int64_t n_iface) 
     return a + b;
 }
 
-extern "C" plic_status vof_curvature_backward(const float*, int, int, int, const int32_t*, int64_t,
-                                              const int64_t*, const float*, float*, plic_method,
-                                              uint32_t, void*, size_t, void*) {
-    return PLIC_ERR_UNSUPPORTED;
+extern "C" plic_status vof_curvature_backward(const float* phi, int nx, int ny, int nz,
+                                              const int32_t* idx, int64_t n_iface,
+                                              const int64_t* d_n_iface, const float* g_kappa,
+                                              float* g_phi, plic_method m, uint32_t flags,
+                                              void* workspace, size_t ws_bytes, void* stream) {
+    using namespace plic;
+    if (nx < 3 || ny < 3 || nz < 3 || n_iface < 0) return PLIC_ERR_ARG;
+    if ((int)m < 0 || (int)m > 4) return PLIC_ERR_ARG;
+    const uint32_t known = PLIC_FLAG_POINT_CENTROID | PLIC_FLAG_KAPPA_PAPER_SIGN |
+                           PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32;
+    if ((flags & ~known) || ((flags & PLIC_FLAG_FIT_FP32) && (flags & PLIC_FLAG_FIT_DF32)))
+        return PLIC_ERR_ARG;
+    if (flags & PLIC_FLAG_POINT_CENTROID) return PLIC_ERR_UNSUPPORTED;
+    const int64_t cells = (int64_t)nx * ny * nz;
+    if (cells > 2147483647LL) return PLIC_ERR_ARG;
+    if (!phi || !g_phi || (n_iface > 0 && (!idx || !g_kappa)) || !workspace) return PLIC_ERR_ARG;
+    if (ws_bytes < plic_curv_bwd_workspace_bytes(cells, n_iface)) return PLIC_ERR_ARG;
+    if (!aligned(phi, 4) || !aligned(g_phi, 4) || (idx && !aligned(idx, 4)) ||
+        (g_kappa && !aligned(g_kappa, 4)) || !aligned(workspace, 256) ||
+        (d_n_iface && !aligned(d_n_iface, 8)))
+        return PLIC_ERR_ALIGN;
+    cudaStream_t s = as_stream(stream);
+    char* ws = reinterpret_cast<char*>(workspace);
+    int32_t* slot = reinterpret_cast<int32_t*>(ws);
+    float* contrib = reinterpret_cast<float*>(ws + ((size_t)cells * sizeof(int32_t) + 255) / 256 * 256);
+    cudaError_t e = cudaMemsetAsync(slot, 0xff, (size_t)cells * sizeof(int32_t), s);
+    if (e != cudaSuccess) { set_last_error("vof_curvature_backward", e); return PLIC_ERR_CUDA; }
+    if (n_iface > 0) {
+        const int fit = (flags & PLIC_FLAG_FIT_DF32) ? FIT_DF32 : (flags & PLIC_FLAG_FIT_FP32) ? FIT_FP32 : FIT_FP64;
+        const void* k = nullptr;
+        switch (m) {
+            case PLIC_ANALYTIC: k = pick_vjp<M_ANALYTIC>(fit); break;
+            case PLIC_SZ_ORIG: k = pick_vjp<M_SZ_ORIG>(fit); break;
+            case PLIC_SZ_OPT: k = pick_vjp<M_SZ_OPT>(fit); break;
+            case PLIC_NEWTON: k = pick_vjp<M_NEWTON>(fit); break;
+            case PLIC_NESTED: k = pick_vjp<M_NESTED>(fit); break;
+        }
+        const int grid = stride_grid(k, CB_THREADS, n_iface);
+        void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&idx, (void*)&n_iface,
+                        (void*)&d_n_iface, (void*)&g_kappa, (void*)&contrib, (void*)&flags};
+        e = cudaLaunchKernel(k, dim3(grid), dim3(CB_THREADS), args, 0, s);
+        if (e != cudaSuccess) { set_last_error("vof_curvature_backward", e); return PLIC_ERR_CUDA; }
+        const int sg = stride_grid(reinterpret_cast<const void*>(&k_curv_slot_scatter), 256, n_iface);
+        k_curv_slot_scatter<<<sg, 256, 0, s>>>(idx, n_iface, d_n_iface, slot);
+    }
+    const int64_t rows = (int64_t)ny * nz;
+    const int gg = stride_grid(reinterpret_cast<const void*>(&k_curv_gather), 256, rows * 32);
+    k_curv_gather<<<gg, 256, 0, s>>>(slot, contrib, nx, ny, nz, g_phi);
+    return check_launch("vof_curvature_backward");
 }

@@ -1,0 +1,117 @@
+"""Adjoints on the GPU against the oracle: the curvature VJP against central
+finite differences of the FP64 oracle curvature, and the autograd wrappers.
+
+The curvature workload: a 128^3 field holding one ellipsoid (semi-axes 12, 18,
+24) with 1e-3 noise on the interface cells, clamped to [2e-4, 1 - 2e-4], and
+weights w ~ N(0,1) per curvature cell; the interface set is held fixed.  The
+FD step is 1e-4; entries where the FD itself has not converged (steps 1e-4 and
+5e-5 disagree by more than 1e-3 of the gradient scale) are left out, with
+their count printed.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2006_12838_gb300 import autograd as AG  # noqa: E402
+from paper_2006_12838_gb300 import plic, synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_12838_gb300 import build
+    build.build()
+    plic.load()
+    return torch.device("cuda:0")
+
+
+def _compare(g_gpu, g1, g2, label, tol_rel=1e-3):
+    scale = np.abs(g1).max()
+    ok = np.abs(g1 - g2) <= 1e-3 * scale          # FD converged here
+    err = np.abs(g_gpu - g1)
+    nz = np.abs(g1) > 0
+    glob = np.linalg.norm((g_gpu - g1)[ok]) / np.linalg.norm(g1[ok])
+    rel = err[ok & nz] / np.maximum(np.abs(g1[ok & nz]), 1e-2 * scale)
+    print("%s: entries %d (FD-unconverged %d), global rel %.3e, max rel %.3e, p99.9 %.3e" % (
+        label, nz.sum(), (~ok & nz).sum(), glob, rel.max(), np.percentile(rel, 99.9)))
+    assert glob <= tol_rel
+    assert np.percentile(rel, 99.9) <= 10 * tol_rel
+    # nothing outside the union of the stencils
+    assert np.all(g_gpu[~nz & (np.abs(g2) == 0)] == 0)
+
+
+@pytest.mark.parametrize("fit", [0, plic.FLAG_FIT_DF32])
+def test_curvature_vjp_against_fd(dev, orc, fit):
+    phi, _ = synth.adjoint_field(seed=4, edge=128)
+    p = phi.numpy()
+    idx = orc.interface_cells(p)
+    w = np.random.default_rng(4).standard_normal(idx.size)
+    g1 = orc.curvature_grad_fd(p, idx, w, 1e-4)
+    g2 = orc.curvature_grad_fd(p, idx, w, 5e-5)
+    phid = torch.tensor(p, device=dev)
+    it = torch.tensor(idx, device=dev)
+    wd = torch.tensor(w, dtype=torch.float32, device=dev)
+    g = plic.curvature_backward(phid, it, wd, flags=fit).cpu().numpy().astype(np.float64)
+    _compare(g, g1, g2, "ellipsoid 128^3 fit %d" % fit)
+
+
+@pytest.mark.parametrize("method", list(plic.METHODS))
+def test_curvature_vjp_methods_small(dev, orc, method):
+    phi = synth.fill_spheres((28, 30, 26), [(13.2, 14.9, 12.4, 8.7)]).numpy()
+    rng = np.random.default_rng(7)
+    iface = (phi > 0) & (phi < 1)
+    phi[iface] = np.clip(phi[iface] + 1e-3 * rng.standard_normal(iface.sum()), 0.01, 0.99)
+    idx = orc.interface_cells(phi)
+    w = rng.standard_normal(idx.size)
+    g1 = orc.curvature_grad_fd(phi, idx, w, 1e-4)
+    g2 = orc.curvature_grad_fd(phi, idx, w, 5e-5)
+    phid = torch.tensor(phi, device=dev)
+    g = plic.curvature_backward(phid, torch.tensor(idx, device=dev),
+                                torch.tensor(w, dtype=torch.float32, device=dev),
+                                method=method).cpu().numpy().astype(np.float64)
+    _compare(g, g1, g2, "sphere %s" % method)
+
+
+def test_curvature_vjp_device_count_and_determinism(dev):
+    phi, _ = synth.curvature_field(seed=3, edge=64, n_spheres=3, rmin=6, rmax=14, device=dev)
+    idx, cnt = plic.interface_compact(phi)
+    k = int(cnt.item())
+    w = torch.randn(idx.numel(), device=dev)
+    a = plic.curvature_backward(phi, idx, w, n_iface=idx.numel(), count=cnt)
+    b = plic.curvature_backward(phi, idx[:k].contiguous(), w[:k].contiguous())
+    c = plic.curvature_backward(phi, idx[:k].contiguous(), w[:k].contiguous())
+    assert torch.equal(a, b) and torch.equal(b, c)
+    with pytest.raises(plic.PlicError):
+        plic.curvature_backward(phi, idx[:k].contiguous(), w[:k].contiguous(),
+                                flags=plic.FLAG_POINT_CENTROID)
+
+
+def test_autograd_wrappers(dev, orc):
+    c = synth.plic_cells(20_000, seed=13)
+    n = c["n"]
+    V0 = np.clip(c["V0"], 0.02, 0.98)
+    t = [torch.tensor(a, dtype=torch.float64, device=dev, requires_grad=True) for a in (n[0], n[1], n[2], V0)]
+    d0 = AG.offset(*t, method="sz_opt", precision="fp64")
+    g = torch.randn_like(d0)
+    (d0 * g).sum().backward()
+    rV, rx, ry, rz = orc.offset_grad(n[0], n[1], n[2], d0.detach().cpu().numpy(), g.cpu().numpy())
+    for tt, r in zip(t, (rx, ry, rz, rV)):
+        np.testing.assert_allclose(tt.grad.cpu().numpy(), r, rtol=1e-9, atol=1e-12)
+    # volume(offset(V0)) = V0: the composed gradient w.r.t. V0 is the identity
+    t2 = [torch.tensor(a, dtype=torch.float64, device=dev, requires_grad=True) for a in (n[0], n[1], n[2], V0)]
+    V = AG.volume(t2[0], t2[1], t2[2], AG.offset(*t2, precision="fp64"))
+    V.sum().backward()
+    np.testing.assert_allclose(t2[3].grad.cpu().numpy(), 1.0, atol=1e-9)
+    np.testing.assert_allclose(t2[0].grad.cpu().numpy(), 0.0, atol=1e-9)
+    # curvature through autograd equals the direct backward call
+    phi, _ = synth.curvature_field(seed=3, edge=48, n_spheres=2, rmin=6, rmax=12, device=dev)
+    idx, cnt = plic.interface_compact(phi)
+    it = idx[:int(cnt.item())].contiguous()
+    ph = phi.clone().requires_grad_(True)
+    kap = AG.curvature(ph, it)
+    w = torch.randn_like(kap)
+    (kap * w).sum().backward()
+    assert torch.equal(ph.grad, plic.curvature_backward(phi, it, w))
