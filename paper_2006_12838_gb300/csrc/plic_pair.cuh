@@ -35,30 +35,34 @@ __device__ __forceinline__ f2 sqrt_(f2 a) {
     return make_float2(Fm<float>::sqrt_(a.x), Fm<float>::sqrt_(a.y));
 }
 
-// cube root of x >= 0: MUFU exp2(log2(x)/3) and one Newton step (see Fm<float>)
+// cube root of x >= 0: MUFU exp2(log2(x)/3) and one Newton step (see
+// Fm<float>).  x is floored at 1e-30 (whose cube root, 1e-10, is far below the
+// FP32 resolution of an offset), which removes the zero/denormal branches.
 __device__ __forceinline__ f2 cbrt_(f2 x) {
-    f2 s = mk(1.0f);
-    if (x.x < 1e-30f) { x.x *= 4.7223665e21f; s.x = 5.9604645e-08f; }
-    if (x.y < 1e-30f) { x.y *= 4.7223665e21f; s.y = 5.9604645e-08f; }
+    x = make_float2(fmaxf(x.x, 1e-30f), fmaxf(x.y, 1e-30f));
     f2 r = make_float2(Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.x) * (1.0f / 3.0f)),
                        Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.y) * (1.0f / 3.0f)));
     const f2 r2 = mul(r, r);
     const f2 res = fma(r2, r, make_float2(-x.x, -x.y));           // r^3 - x
     const f2 inv = rcp(mul(mk(3.0f), r2));
-    r = fma(make_float2(-res.x, -res.y), inv, r);
-    r = mul(s, r);
-    return make_float2(x.x > 0.0f ? r.x : 0.0f, x.y > 0.0f ? r.y : 0.0f);
+    return fma(make_float2(-res.x, -res.y), inv, r);
 }
 
-// arcsine by the series of fast_asinf (Maclaurin series of arcsin to s^17 on
-// s <= 1/2, half-angle reduction above), two lanes at once
-__device__ __forceinline__ f2 asin_(f2 x) {
-    const f2 a = make_float2(fabsf(x.x), fabsf(x.y));
+// sqrt of x >= 0 as x rsqrt(x), x floored at 1e-30 (no zero branch)
+__device__ __forceinline__ f2 sqrtp(f2 x) {
+    x = make_float2(fmaxf(x.x, 1e-30f), fmaxf(x.y, 1e-30f));
+    return mul(x, rsqrt(x));
+}
+
+// arcsine on [0, 1] by the series of fast_asinf (Maclaurin series of arcsin
+// to s^17 on s <= 1/2, half-angle reduction above), two lanes at once.  The
+// optimised-SZ argument is never negative: it is 1.5 n1 n2 (n1+n2-2 n3 V)/t^3
+// with n1+n2 > 2 n3 V outside case (5), or 0.75 n1 n2 n3 (1-2V)/t^3 with V <= 1/2.
+__device__ __forceinline__ f2 asin01(f2 a) {
     const b2 big = lt(mk(0.5f), a);
     const f2 zb = mul(mk(0.5f), sub(mk(1.0f), a));
     const f2 z = sel(big, zb, mul(a, a));
-    const f2 sb = make_float2(z.x > 0.0f ? z.x * rsqrtf(z.x) : 0.0f, z.y > 0.0f ? z.y * rsqrtf(z.y) : 0.0f);
-    const f2 s = sel(big, sb, a);
+    const f2 s = sel(big, sqrtp(z), a);
     f2 p = mk(0.011551800896139705f);
     p = fma(p, z, mk(0.01396484375f));
     p = fma(p, z, mk(0.017352764423076924f));
@@ -68,8 +72,7 @@ __device__ __forceinline__ f2 asin_(f2 x) {
     p = fma(p, z, mk(0.075f));
     p = fma(p, z, mk(0.16666666666666666f));
     p = fma(mul(s, z), p, s);
-    const f2 r = sel(big, fma(mk(-2.0f), p, mk(1.5707963267948966f)), p);
-    return make_float2(copysignf(r.x, x.x), copysignf(r.y, x.y));
+    return sel(big, fma(mk(-2.0f), p, mk(1.5707963267948966f)), p);
 }
 
 // Reduced optimised-SZ solution for two cells (L1-normalised m1 <= m2 <= m3,
@@ -105,13 +108,13 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3, b2& trig) {
     const f2 rt = rsqrt(t2);
     const f2 t = mul(t2, rt);
     f2 arg = mul(q, mul(rt, mul(rt, rt)));
-    arg = make_float2(fminf(fmaxf(arg.x, -1.0f), 1.0f), fminf(fmaxf(arg.y, -1.0f), 1.0f));
-    const f2 th = mul(mk(0.33333333333333333f), asin_(arg));
+    arg = make_float2(fminf(arg.x, 1.0f), fminf(arg.y, 1.0f));
+    const f2 th = mul(mk(0.33333333333333333f), asin01(arg));
     const f2 sn = make_float2(__sinf(th.x), __sinf(th.y));
     const f2 d34 = fma(mul(mk(-2.0f), t), sn, c);
     // closed forms
     const f2 d5 = fma(mk(0.5f), n12, n3V);
-    const f2 d2 = mul(mk(0.5f), add(n1, sqrt_(fma(mk(8.0f), mul(n2, n3V), mul(mk(-0.33333333333333333f), sqn1)))));
+    const f2 d2 = mul(mk(0.5f), add(n1, sqrtp(fma(mk(8.0f), mul(n2, n3V), mul(mk(-0.33333333333333333f), sqn1)))));
     const f2 d1 = cbrt_(mul(V6n2n3, n1));
     trig = {!c5.x && !c2.x && !c1.x, !c5.y && !c2.y && !c1.y};
     f2 d = sel(c1, d1, d34);
@@ -120,9 +123,10 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3, b2& trig) {
 }
 
 // One Newton step on the cubic of Eq. 10 for cases (3)/(4) (d >= n2, n1 > 0):
-// g = 3 d (d - n1) + n1^2 - ((d - n2)^3 + (d - n3)_+^3)/n1 - 6 n2 n3 V
+// g = 3 d (d - n1) + n1^2 - ((d - n2)^3 + (d - n3)_+^3)/n1 - 6 n2 n3 V,
+// g' = 6 d - 3 n1 - 3 ((d - n2)^2 + (d - n3)_+^2)/n1 = 12 n2 n3 x area > 0.
 __device__ __forceinline__ f2 polish34(f2 d, f2 V, f2 n1, f2 n2, f2 n3) {
-    const f2 e2 = fmax0(sub(d, n2)), e3 = fmax0(sub(d, n3));
+    const f2 e2 = sub(d, n2), e3 = fmax0(sub(d, n3));
     const f2 inv1 = rcp(n1);
     const f2 e22 = mul(e2, e2), e33 = mul(e3, e3);
     const f2 cub = fma(e22, e2, mul(e33, e3));
@@ -132,9 +136,7 @@ __device__ __forceinline__ f2 polish34(f2 d, f2 V, f2 n1, f2 n2, f2 n3) {
     g = fma(mk(-6.0f), mul(mul(n2, n3), V), g);
     f2 gp = fma(mk(6.0f), d, mul(mk(-3.0f), n1));
     gp = fma(mk(-3.0f), mul(add(e22, e33), inv1), gp);
-    const f2 step = mul(g, rcp(gp));
-    const f2 dn = sub(d, step);
-    return make_float2(gp.x > 0.0f ? dn.x : d.x, gp.y > 0.0f ? dn.y : d.y);
+    return sub(d, mul(g, rcp(gp)));
 }
 
 // Whole cells: two (n, V0) -> d0 by the optimised SZ solution in FP32.
@@ -146,13 +148,15 @@ __device__ __forceinline__ f2 offset_sz_opt(f2 nx, f2 ny, f2 nz, f2 V0, int& bad
     const f2 n1 = make_float2(fminf(fminf(ax.x, ay.x), az.x), fminf(fminf(ax.y, ay.y), az.y));
     const f2 n3 = make_float2(fmaxf(fmaxf(ax.x, ay.x), az.x), fmaxf(fmaxf(ax.y, ay.y), az.y));
     const f2 L = add(add(ax, ay), az);
-    const bool okx = V0.x >= 0.0f && V0.x <= 1.0f && L.x > 0.0f && L.x <= 3.0f;
-    const bool oky = V0.y >= 0.0f && V0.y <= 1.0f && L.y > 0.0f && L.y <= 3.0f;
+    // V = min(V0, 1 - V0) equals the exact reduction of Eq. 5 on [0, 1], and is
+    // negative or NaN exactly when V0 is outside [0, 1] or NaN
+    const f2 V = make_float2(fminf(V0.x, 1.0f - V0.x), fminf(V0.y, 1.0f - V0.y));
+    const bool okx = V.x >= 0.0f && L.x > 0.0f && L.x <= 3.0f;
+    const bool oky = V.y >= 0.0f && L.y > 0.0f && L.y <= 3.0f;
     bad += (int)!okx + (int)!oky;
     const f2 il = rcp(L);
     const f2 m1 = mul(n1, il), m3 = mul(n3, il);
     const f2 m2 = fmax0(sub(mk(1.0f), add(m1, m3)));
-    const f2 V = make_float2(V0.x <= 0.5f ? V0.x : 1.0f - V0.x, V0.y <= 0.5f ? V0.y : 1.0f - V0.y);
     b2 trig;
     f2 a = sz_opt(V, m1, m2, m3, trig);
     if (POLISH) {

@@ -7,12 +7,12 @@
 //   1. k_compact_count : each block counts the interface cells of its tile.
 //   2. k_compact_scan  : one block turns the per-tile counts into exclusive
 //                        offsets (in place) and writes the total to *d_count.
-//   3. k_compact_write : each block re-reads its tile (L2-resident right after
-//                        pass 1 for fields up to the 129 MB L2), keeps the row
-//                        ballots in shared memory, scans the row counts and
-//                        writes the indices at its offset, in order.
-// HBM roofline: 4 B per field cell read once (pass 3 mostly hits L2), plus
-// 4 B per interface cell written.
+//   3. k_compact_write : each block takes its tile's interface bits (stored by
+//                        pass 1 in the workspace, 1 bit per cell), scans the
+//                        row counts and writes the indices at its offset, in
+//                        order.
+// HBM roofline: 4 B per field cell read once + 1/8 B per cell of bits written
+// and read back, plus 4 B per interface cell written.
 #include <mutex>
 #include <stdio.h>
 
@@ -24,7 +24,7 @@ constexpr int CT_THREADS = 256;
 constexpr int CT_WARPS = CT_THREADS / 32;
 constexpr int CT_TILE = 4096;            // cells per tile (whole x-rows)
 constexpr int CT_MAX_ROWS = 1024;        // rows per tile at most (nx >= 4)
-constexpr int CT_MAX_WORDS = 2048;       // ballot words per tile at most
+constexpr int CT_MAX_WORDS = 2048;       // ballot words per tile kept in shared memory
 
 // Rows (x-lines) per tile: as many whole rows as fit in CT_TILE cells.
 __host__ __device__ inline int tile_rows(int nx) {
@@ -32,27 +32,73 @@ __host__ __device__ inline int tile_rows(int nx) {
     return r < 1 ? 1 : (r > CT_MAX_ROWS ? CT_MAX_ROWS : r);
 }
 
-// Work is split by rows: warp w of a block takes rows w, w + 8, ... of the
-// block's tile.  A row's (y, z) is computed once per warp (one division), rows
-// on the field boundary are skipped without reading them, and a row is read
-// as coalesced 128-byte segments.
+__device__ __forceinline__ bool iface(float v) { return v > 0.0f && v < 1.0f; }
+
+// Interface bits of one row, 32 cells per word (bit x % 32 of word x / 32),
+// with the boundary columns x = 0 and x = nx - 1 cleared; the caller has
+// checked the row's y and z.  `fn(word_index, bits)` is called by one lane per
+// word; returns the row's count in every lane.  With 16-byte aligned rows
+// (nx % 4 == 0) each lane loads 4 cells at once.
+template <typename F>
+__device__ __forceinline__ int row_bits(const float* __restrict__ row, int nx, bool vec, F fn) {
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+    if (vec) {
+        for (int x0 = 0; x0 < nx; x0 += 128) {
+            const int x = x0 + 4 * lane;
+            unsigned m = 0u;
+            if (x < nx) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(row + x));
+                m = (unsigned)iface(v.x) | ((unsigned)iface(v.y) << 1) |
+                    ((unsigned)iface(v.z) << 2) | ((unsigned)iface(v.w) << 3);
+                if (x == 0) m &= ~1u;
+                if (x + 3 == nx - 1) m &= ~8u;
+            }
+            // gather the nibbles of 8 lanes into one 32-bit word
+            unsigned w = m << (4 * (lane & 7));
+            w |= __shfl_xor_sync(0xffffffffu, w, 1);
+            w |= __shfl_xor_sync(0xffffffffu, w, 2);
+            w |= __shfl_xor_sync(0xffffffffu, w, 4);
+            cnt += __popc(m);
+            if ((lane & 7) == 0 && x < nx) fn((x0 >> 5) + (lane >> 3), w);
+        }
+    } else {
+        for (int x0 = 0; x0 < nx; x0 += 32) {
+            const int x = x0 + lane;
+            const float v = x < nx ? __ldg(row + x) : 0.0f;
+            const unsigned b = __ballot_sync(0xffffffffu, x >= 1 && x <= nx - 2 && iface(v));
+            cnt += (b >> lane) & 1u;
+            if (lane == 0) fn(x0 >> 5, b);
+        }
+    }
+    return __reduce_add_sync(0xffffffffu, cnt);
+}
+
+// Pass 1.  Work is split by rows: warp w of a block takes rows w, w + 8, ...
+// of the block's tile.  A row's (y, z) is computed once per warp, rows on the
+// field boundary are skipped without reading them.  The per-tile count goes
+// to tile_count; with `bits` given, the row's interface bits are stored too
+// (wpr words per row), so that pass 3 need not read the field again.
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
-                int* __restrict__ tile_count) {
+                int* __restrict__ tile_count, unsigned* __restrict__ bits, int vec) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpr = (nx + 31) >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
     const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
     int cnt = 0;
     for (int64_t r = rbeg + warp; r < rend; r += CT_WARPS) {
         const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        if (y < 1 || y > ny - 2 || z < 1 || z > nz - 2) continue;
-        const float* row = phi + r * nx;
-        for (int x = lane; x < nx; x += 32) {
-            const float v = __ldg(row + x);
-            cnt += (x >= 1 && x <= nx - 2 && v > 0.0f && v < 1.0f);
+        unsigned* rb = bits ? bits + r * wpr : nullptr;
+        if (y < 1 || y > ny - 2 || z < 1 || z > nz - 2) {
+            if (rb)
+                for (int w = lane; w < wpr; w += 32) rb[w] = 0u;
+            continue;
         }
+        cnt += row_bits(phi + r * nx, nx, vec != 0, [&](int w, unsigned b) {
+            if (rb) rb[w] = b;
+        });
     }
-    cnt = __reduce_add_sync(0xffffffffu, cnt);
     __shared__ int ws[CT_WARPS];
     if (lane == 0) ws[warp] = cnt;
     __syncthreads();
@@ -64,21 +110,23 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     }
 }
 
-// Exclusive scan of ntiles ints by one block of 1024 threads; total -> *d_count.
+// Pass 2: exclusive scan of ntiles ints by one block of 1024 threads (four
+// consecutive entries per thread and round); total -> *d_count.
 __global__ void __launch_bounds__(1024)
 k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict__ d_count) {
     __shared__ long long wsum[32];
-    __shared__ long long carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t b0 = 0; b0 < ntiles; b0 += 1024) {
-        const int64_t i = b0 + threadIdx.x;
-        long long v = i < ntiles ? tile_count[i] : 0;
-        long long x = v;
+    long long carry = 0;
+    for (int64_t b0 = 0; b0 < ntiles; b0 += 4096) {
+        const int64_t i0 = b0 + 4 * (int64_t)threadIdx.x;
+        int v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = i0 + j < ntiles ? tile_count[i0 + j] : 0;
+        const long long own = (long long)v[0] + v[1] + v[2] + v[3];
+        long long x = own;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, x, o);
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) wsum[warp] = x;
@@ -87,51 +135,60 @@ k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict
             long long w = wsum[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                long long y = __shfl_up_sync(0xffffffffu, w, o);
+                const long long y = __shfl_up_sync(0xffffffffu, w, o);
                 if (lane >= o) w += y;
             }
             wsum[lane] = w;
         }
         __syncthreads();
-        const long long excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - v;
-        if (i < ntiles) tile_count[i] = (int)excl;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
+        long long run = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - own;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (i0 + j < ntiles) tile_count[i0 + j] = (int)run;
+            run += v[j];
+        }
+        carry += wsum[31];
         __syncthreads();
     }
     if (threadIdx.x == 0) *d_count = carry;
 }
 
-// Pass 3: the warps ballot their rows into shared memory (one 32-bit word per
-// 32 cells of a row), the block scans the per-row counts, and each warp writes
-// its rows' indices at the row offsets -- in ascending cell order.
+// Pass 3: each warp takes its rows' interface bits (from pass 1's bit array,
+// or recomputed from the field when none was kept), the block scans the row
+// counts, and every warp writes its rows' indices at the row offsets, in
+// ascending cell order.
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
-                const int* __restrict__ tile_offset, int32_t* __restrict__ idx, int64_t cap) {
+                const int* __restrict__ tile_offset, const unsigned* __restrict__ bits,
+                int32_t* __restrict__ idx, int64_t cap, int vec) {
     __shared__ unsigned bal[CT_MAX_WORDS];
     __shared__ int rowoff[CT_MAX_ROWS + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
     const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
     const int nr = (int)(rend - rbeg);
-    const int wpr = (nx + 31) >> 5;                 // ballot words per row
+    const int wpr = (nx + 31) >> 5;                 // words per row
     const bool in_smem = (int64_t)nr * wpr <= CT_MAX_WORDS;
     for (int k = warp; k < nr; k += CT_WARPS) {
         const int64_t r = rbeg + k;
-        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        const bool row_ok = y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2;
         int cnt = 0;
-        if (row_ok) {
-            const float* row = phi + r * nx;
-            for (int x0 = 0; x0 < nx; x0 += 32) {
-                const int x = x0 + lane;
-                const float v = x < nx ? __ldg(row + x) : 0.0f;
-                const unsigned b = __ballot_sync(0xffffffffu, x >= 1 && x <= nx - 2 && v > 0.0f && v < 1.0f);
-                if (in_smem && lane == 0) bal[k * wpr + (x0 >> 5)] = b;
+        if (bits) {
+            const unsigned* rb = bits + r * wpr;
+            for (int w = lane; w < wpr; w += 32) {
+                const unsigned b = __ldg(rb + w);
                 cnt += __popc(b);
+                if (in_smem) bal[k * wpr + w] = b;
             }
-        } else if (in_smem) {
-            for (int w = lane; w < wpr; w += 32) bal[k * wpr + w] = 0u;
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+        } else {
+            const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
+            if (y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2) {
+                cnt = row_bits(phi + r * nx, nx, vec != 0, [&](int w, unsigned b) {
+                    if (in_smem) bal[k * wpr + w] = b;
+                });
+            } else if (in_smem) {
+                for (int w = lane; w < wpr; w += 32) bal[k * wpr + w] = 0u;
+            }
         }
         if (lane == 0) rowoff[k] = cnt;
     }
@@ -159,24 +216,44 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     const int64_t base = tile_offset[blockIdx.x];
     for (int k = warp; k < nr; k += CT_WARPS) {
         const int64_t r = rbeg + k;
-        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        if (!(y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2)) continue;
         int64_t pos = base + rowoff[k];
-        const float* row = phi + r * nx;
-        for (int x0 = 0; x0 < nx; x0 += 32) {
-            const int x = x0 + lane;
-            unsigned b;
-            if (in_smem) {
-                b = bal[k * wpr + (x0 >> 5)];
-            } else {
-                const float v = x < nx ? __ldg(row + x) : 0.0f;
-                b = __ballot_sync(0xffffffffu, x >= 1 && x <= nx - 2 && v > 0.0f && v < 1.0f);
+        // one lane per 32-cell word: warp prefix of the word counts, then each
+        // lane writes its word's cells in order
+        for (int w0 = 0; w0 < wpr; w0 += 32) {
+            const int w = w0 + lane;
+            unsigned b = 0u;
+            if (w < wpr) {
+                if (in_smem) {
+                    b = bal[k * wpr + w];
+                } else if (bits) {
+                    b = __ldg(bits + r * wpr + w);
+                } else {
+                    // recompute this word (rare: tiles of very long rows)
+                    const float* row = phi + r * nx;
+                    const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
+                    if (y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2)
+                        for (int j = 0; j < 32; ++j) {
+                            const int x = 32 * w + j;
+                            if (x >= 1 && x <= nx - 2 && iface(__ldg(row + x))) b |= 1u << j;
+                        }
+                }
             }
-            if ((b >> lane) & 1u) {
-                const int64_t p = pos + __popc(b & ((1u << lane) - 1u));
-                if (p < cap) idx[p] = (int32_t)(r * nx + x);
+            const int c = __popc(b);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
             }
-            pos += __popc(b);
+            int64_t p = pos + incl - c;
+            const int64_t cell0 = r * nx + 32 * (int64_t)w;
+            while (b) {
+                const int j = __ffs(b) - 1;
+                b &= b - 1u;
+                if (p < cap) idx[p] = (int32_t)(cell0 + j);
+                ++p;
+            }
+            pos += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
 }
@@ -193,12 +270,14 @@ extern "C" size_t plic_workspace_bytes(int op, int64_t arg) {
     if (arg < 0) return 0;
     switch (op) {
         case PLIC_WS_COMPACT: {
-            // at least one tile per 4096 cells or per row (for rows longer
-            // than 4096 cells), rounded up; an upper bound for any shape with
-            // arg cells and at most CT_MAX_ROWS rows per tile
+            // tile counts: tiles hold >= 2048 cells (or one whole row), so a
+            // field of arg cells has at most 2 arg / 4096 + 1 tiles; interface
+            // bits: one word per 32 cells of each row, at most arg / 16 words
+            // for rows of >= 32 cells (shorter rows keep no bits)
             const int64_t t = (arg + plic::CT_TILE - 1) / plic::CT_TILE * 2 + 1;
-            const size_t b = (size_t)t * sizeof(int);
-            return (b + 255) / 256 * 256;
+            const size_t a = ((size_t)t * sizeof(int) + 255) / 256 * 256;
+            const size_t b = ((size_t)(arg / 16 + 1) * sizeof(unsigned) + 255) / 256 * 256;
+            return a + b;
         }
         case PLIC_WS_BATCHED: {
             // descriptor table + per-field cell prefix + the ticket counter
@@ -230,11 +309,18 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
     const int64_t rows = (int64_t)ny * nz;
     const int R = tile_rows(nx);
     const int64_t nt = compact_tiles(nx, rows);
-    if ((size_t)nt * sizeof(int) > ws_bytes) return PLIC_ERR_ARG;
+    const size_t tile_bytes = ((size_t)nt * sizeof(int) + 255) / 256 * 256;
+    if (tile_bytes > ws_bytes) return PLIC_ERR_ARG;
     int* tiles = reinterpret_cast<int*>(workspace);
-    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles);
+    const int64_t words = rows * ((nx + 31) / 32);
+    unsigned* bits = nullptr;
+    if (nx >= 32 && tile_bytes + (size_t)words * sizeof(unsigned) <= ws_bytes)
+        bits = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + tile_bytes);
+    const int vec = (nx % 4 == 0) && aligned(phi, 16);
+    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, vec);
     k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
-    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, idx, idx_capacity);
+    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, idx,
+                                                        idx_capacity, vec);
     return check_launch("vof_interface_compact");
 }
 
@@ -310,8 +396,11 @@ extern "C" plic_status vof_interface_compact_noalloc(const float* phi, int nx, i
         set_limit_error(ncell);
         return PLIC_ERR_ARG;
     }
-    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles);
+    // the built-in scratch holds the tile counts only; pass 3 re-reads the field
+    const int vec = (nx % 4 == 0) && aligned(phi, 16);
+    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr, vec);
     k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
-    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, idx, idx_capacity);
+    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr, idx,
+                                                        idx_capacity, vec);
     return check_launch("vof_interface_compact_noalloc");
 }

@@ -3,10 +3,15 @@ finite differences of the FP64 oracle curvature, and the autograd wrappers.
 
 The curvature workload: a 128^3 field holding one ellipsoid (semi-axes 12, 18,
 24) with 1e-3 noise on the interface cells, clamped to [2e-4, 1 - 2e-4], and
-weights w ~ N(0,1) per curvature cell; the interface set is held fixed.  The
-FD step is 1e-4; entries where the FD itself has not converged (steps 1e-4 and
-5e-5 disagree by more than 1e-3 of the gradient scale) are left out, with
-their count printed.
+weights w ~ N(0,1) per curvature cell; the interface set is held fixed.
+
+Finite-difference step: the stated step of 1e-4 is in its asymptotic range
+only away from the clamp -- near fills of 2e-4 the offset d0 ~ V^(1/3) bends
+so fast that central differences with h = 1e-4 are off by ~5 % in norm on this
+field (h = 1e-5: 4e-4; h = 1e-6 and 1e-7 agree to 4e-6).  The oracle is FP64,
+so the gate uses h = 1e-6 and h = 1e-7 (entries where these two disagree by
+more than 1e-4 of the gradient scale are left out and counted); the h = 1e-4
+difference is printed beside it.
 """
 import numpy as np
 import pytest
@@ -28,15 +33,17 @@ def dev():
     return torch.device("cuda:0")
 
 
-def _compare(g_gpu, g1, g2, label, tol_rel=1e-3):
+def _compare(g_gpu, g1, g2, label, tol_rel=1e-3, g_coarse=None):
     scale = np.abs(g1).max()
-    ok = np.abs(g1 - g2) <= 1e-3 * scale          # FD converged here
+    ok = np.abs(g1 - g2) <= 1e-4 * scale          # FD converged here
     err = np.abs(g_gpu - g1)
     nz = np.abs(g1) > 0
     glob = np.linalg.norm((g_gpu - g1)[ok]) / np.linalg.norm(g1[ok])
     rel = err[ok & nz] / np.maximum(np.abs(g1[ok & nz]), 1e-2 * scale)
     print("%s: entries %d (FD-unconverged %d), global rel %.3e, max rel %.3e, p99.9 %.3e" % (
         label, nz.sum(), (~ok & nz).sum(), glob, rel.max(), np.percentile(rel, 99.9)))
+    if g_coarse is not None:
+        print("   vs FD h=1e-4: global rel %.3e" % (np.linalg.norm(g_gpu - g_coarse) / np.linalg.norm(g_coarse)))
     assert glob <= tol_rel
     assert np.percentile(rel, 99.9) <= 10 * tol_rel
     # nothing outside the union of the stencils
@@ -49,13 +56,14 @@ def test_curvature_vjp_against_fd(dev, orc, fit):
     p = phi.numpy()
     idx = orc.interface_cells(p)
     w = np.random.default_rng(4).standard_normal(idx.size)
-    g1 = orc.curvature_grad_fd(p, idx, w, 1e-4)
-    g2 = orc.curvature_grad_fd(p, idx, w, 5e-5)
+    g1 = orc.curvature_grad_fd(p, idx, w, 1e-6)
+    g2 = orc.curvature_grad_fd(p, idx, w, 1e-7)
+    gc = orc.curvature_grad_fd(p, idx, w, 1e-4)
     phid = torch.tensor(p, device=dev)
     it = torch.tensor(idx, device=dev)
     wd = torch.tensor(w, dtype=torch.float32, device=dev)
     g = plic.curvature_backward(phid, it, wd, flags=fit).cpu().numpy().astype(np.float64)
-    _compare(g, g1, g2, "ellipsoid 128^3 fit %d" % fit)
+    _compare(g, g1, g2, "ellipsoid 128^3 fit %d" % fit, g_coarse=gc)
 
 
 @pytest.mark.parametrize("method", list(plic.METHODS))
@@ -66,8 +74,8 @@ def test_curvature_vjp_methods_small(dev, orc, method):
     phi[iface] = np.clip(phi[iface] + 1e-3 * rng.standard_normal(iface.sum()), 0.01, 0.99)
     idx = orc.interface_cells(phi)
     w = rng.standard_normal(idx.size)
-    g1 = orc.curvature_grad_fd(phi, idx, w, 1e-4)
-    g2 = orc.curvature_grad_fd(phi, idx, w, 5e-5)
+    g1 = orc.curvature_grad_fd(phi, idx, w, 1e-6)
+    g2 = orc.curvature_grad_fd(phi, idx, w, 1e-7)
     phid = torch.tensor(phi, device=dev)
     g = plic.curvature_backward(phid, torch.tensor(idx, device=dev),
                                 torch.tensor(w, dtype=torch.float32, device=dev),
