@@ -71,11 +71,16 @@ enum {
     /* Curvature: return Eq. 42 as printed (negative for a convex fluid region
      * with the Parker-Youngs normal); default is -(Eq. 42). */
     PLIC_FLAG_KAPPA_PAPER_SIGN = 4u,
-    /* Curvature: solve the 5x5 normal equations in FP32 instead of FP64. */
+    /* Curvature fit precision (at most one of the three; default: adaptive,
+     * an FP32 LDL^T that is redone in FP64 for the cells whose normal matrix
+     * is ill-conditioned -- smallest pivot below 1e-2 of the largest).
+     * FIT_FP32: the 5x5 normal equations in FP32 only. */
     PLIC_FLAG_FIT_FP32 = 8u,
-    /* Curvature: solve the 5x5 normal equations in double-float (pairs of FP32
-     * numbers, about 48 significant bits) on the FP32 pipes. */
-    PLIC_FLAG_FIT_DF32 = 16u
+    /* FIT_DF32: in double-float (pairs of FP32 numbers, about 48 significant
+     * bits) on the FP32 pipes. */
+    PLIC_FLAG_FIT_DF32 = 16u,
+    /* FIT_FP64: in FP64 for every cell. */
+    PLIC_FLAG_FIT_FP64 = 32u
 };
 
 /* plic_volume -- forward problem ("inverse PLIC", Sec. 2.2, Eq. 10 with Eqs.
@@ -161,8 +166,8 @@ plic_status vof_interface_compact_noalloc(const float *phi, int nx, int ny, int 
  * cell idx[k]: 3^3 stencil -> Parker-Youngs normal (Eq. 38) -> local frame ->
  * PLIC offsets d0(phi_i, n) of the centre and of every interface neighbour
  * with the centre normal (Eq. 36), by solver m in FP32 with one Newton polish
- * -> least-squares paraboloid (Appendix B, FP64 solve unless a FIT flag says
- * otherwise) -> mean curvature (Eq. 42) into kappa[k].
+ * -> least-squares paraboloid (Appendix B; fit precision per the FIT flags,
+ * default adaptive FP32/FP64) -> mean curvature (Eq. 42) into kappa[k].
  * n_iface: number of list entries (host).  d_n_iface (device int64, nullable):
  * if given, only the first min(n_iface, *d_n_iface) entries are processed, so
  * the call can follow vof_interface_compact without a host round trip.

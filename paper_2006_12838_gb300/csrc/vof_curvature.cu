@@ -2,85 +2,124 @@
 // field (vof_curvature) and for many fields in one persistent launch
 // (vof_curvature_batched).
 //
-// One thread per interface cell.  Consecutive list entries are mostly x-
-// neighbours (the list is in ascending cell order), so a warp's 27-point
-// stencils overlap in 3 x 3 rows of ~34 consecutive floats: the gathers hit L1.
-// The work per cell is dominated by up to 27 PLIC solves (the paper's
-// observation that PLIC is the main cost) and the 5x5 solve.
+// Eight lanes per interface cell and one lane per 5x5 solve (see
+// vof_curvature_coop.cuh).  Consecutive list entries are mostly x-neighbours
+// (the list is in ascending cell order), so the stencils of a warp's cells
+// overlap in 3 x 3 rows of consecutive floats: the gathers hit L1.  The work
+// per cell is dominated by up to 27 PLIC solves (the paper's observation that
+// PLIC is the main cost) and the 5x5 solve.
 #include "host_common.h"
-#include "vof_curvature.cuh"
+#include "vof_curvature_coop.cuh"
 
 namespace plic {
 
+constexpr int CO_THREADS = 128;       // 4 warps per block
+constexpr int CO_WARPS = CO_THREADS / 32;
+
+// Single field: warp w of the grid takes batches of 32 list entries in a
+// grid-stride loop.
 template <int METHOD, int FIT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(CO_THREADS)
 k_vof_curvature(const float* __restrict__ phi, int nx, int ny, const int32_t* __restrict__ idx,
                 int64_t n, const int64_t* __restrict__ d_n, float* __restrict__ kappa,
                 uint32_t flags) {
+    __shared__ float smem[CO_WARPS][CO_BATCH * CO_VALS];
     int64_t lim = n;
     if (d_n) {
         const int64_t dn = *d_n;
         lim = dn < n ? dn : n;
     }
+    const int warp = threadIdx.x >> 5;
     const int64_t nxy = (int64_t)nx * ny;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lim;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const CurvOut o = curvature_cell<METHOD, FIT>(phi, (int64_t)__ldg(idx + k), nx, nxy, flags);
-        kappa[k] = o.kappa;
+    const int64_t gw = (int64_t)blockIdx.x * CO_WARPS + warp;
+    const int64_t nw = (int64_t)gridDim.x * CO_WARPS;
+    for (int64_t k0 = gw * CO_BATCH; k0 < lim; k0 += nw * CO_BATCH) {
+        auto fetch = [&](int slot) {
+            const int64_t k = k0 + slot;
+            CoCell c;
+            c.phi = phi; c.nx = nx; c.nxy = nxy;
+            c.valid = k < lim;
+            c.c = c.valid ? (int64_t)__ldg(idx + k) : 0;
+            c.out = kappa + k;
+            return c;
+        };
+        co_warp_batch<METHOD, FIT>(fetch, flags, smem[warp]);
     }
 }
 
-// Persistent batched kernel: blocks claim chunks of the concatenated interface
-// lists from a ticket counter and stop when the tickets pass the total.
+// Persistent batched kernel: each warp claims tickets of `chunk` cells (a
+// multiple of 32) of the concatenated interface lists from a device counter
+// and stops when the tickets pass the total; no warp waits for another.
 template <int METHOD, int FIT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(CO_THREADS)
 k_vof_curvature_batched(const vof_field* __restrict__ fields, const int64_t* __restrict__ prefix,
                         int n_fields, int64_t total, int chunk,
                         unsigned long long* __restrict__ ticket, uint32_t flags) {
-    __shared__ long long s_start;
+    __shared__ float smem[CO_WARPS][CO_BATCH * CO_VALS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
-        if (threadIdx.x == 0) s_start = (long long)atomicAdd(ticket, (unsigned long long)chunk);
-        __syncthreads();
-        const int64_t start = s_start;
-        __syncthreads();
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ticket, (unsigned long long)chunk);
+        const int64_t start = (int64_t)__shfl_sync(0xffffffffu, t, 0);
         if (start >= total) break;
         const int64_t end = start + chunk < total ? start + chunk : total;
-        for (int64_t g = start + threadIdx.x; g < end; g += blockDim.x) {
-            // field f with prefix[f] <= g < prefix[f+1]
-            int lo = 0, hi = n_fields - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(prefix + mid) <= g) lo = mid; else hi = mid - 1;
+        for (int64_t b0 = start; b0 < end; b0 += CO_BATCH) {
+            // lane l locates entry b0 + l: field (binary search on the prefix)
+            // and position in that field's list
+            const int64_t gi = b0 + lane;
+            int f = 0;
+            int64_t kk = 0;
+            if (gi < end) {
+                int lo = 0, hi = n_fields - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(prefix + mid) <= gi) lo = mid; else hi = mid - 1;
+                }
+                f = lo;
+                kk = gi - __ldg(prefix + lo);
             }
-            const vof_field& F = fields[lo];
-            const int64_t k = g - __ldg(prefix + lo);
-            const int64_t nxy = (int64_t)F.nx * F.ny;
-            const CurvOut o = curvature_cell<METHOD, FIT>(F.phi, (int64_t)__ldg(F.idx + k), F.nx, nxy, flags);
-            F.kappa[k] = o.kappa;
+            auto fetch = [&](int slot) {
+                const int fs = __shfl_sync(0xffffffffu, f, slot);
+                const long long ks = __shfl_sync(0xffffffffu, (long long)kk, slot);
+                const vof_field& F = fields[fs];
+                CoCell c;
+                c.phi = F.phi; c.nx = F.nx; c.nxy = (int64_t)F.nx * F.ny;
+                c.valid = b0 + slot < end;
+                c.c = c.valid ? (int64_t)__ldg(F.idx + ks) : 0;
+                c.out = F.kappa + ks;
+                return c;
+            };
+            co_warp_batch<METHOD, FIT>(fetch, flags, smem[warp]);
         }
     }
 }
 
+#define PLIC_FIT_TABLE(K, M) \
+    static const void* K##_tab[4] = { \
+        reinterpret_cast<const void*>(&K<M, FIT_FP64>), reinterpret_cast<const void*>(&K<M, FIT_FP32>), \
+        reinterpret_cast<const void*>(&K<M, FIT_DF32>), reinterpret_cast<const void*>(&K<M, FIT_AUTO>)};
+
 template <int METHOD>
 static const void* pick_single(int fit) {
-    switch (fit) {
-        case FIT_FP32: return reinterpret_cast<const void*>(&k_vof_curvature<METHOD, FIT_FP32>);
-        case FIT_DF32: return reinterpret_cast<const void*>(&k_vof_curvature<METHOD, FIT_DF32>);
-        default: return reinterpret_cast<const void*>(&k_vof_curvature<METHOD, FIT_FP64>);
-    }
+    PLIC_FIT_TABLE(k_vof_curvature, METHOD)
+    return k_vof_curvature_tab[fit];
 }
 
 template <int METHOD>
 static const void* pick_batched(int fit) {
-    switch (fit) {
-        case FIT_FP32: return reinterpret_cast<const void*>(&k_vof_curvature_batched<METHOD, FIT_FP32>);
-        case FIT_DF32: return reinterpret_cast<const void*>(&k_vof_curvature_batched<METHOD, FIT_DF32>);
-        default: return reinterpret_cast<const void*>(&k_vof_curvature_batched<METHOD, FIT_FP64>);
-    }
+    PLIC_FIT_TABLE(k_vof_curvature_batched, METHOD)
+    return k_vof_curvature_batched_tab[fit];
 }
 
+// Fit precision from the flags: one of FIT_FP32 / FIT_DF32 / FIT_FP64, or the
+// adaptive default; -1 when more than one is set.
 static int fit_mode(uint32_t flags) {
-    return (flags & PLIC_FLAG_FIT_DF32) ? FIT_DF32 : (flags & PLIC_FLAG_FIT_FP32) ? FIT_FP32 : FIT_FP64;
+    const uint32_t f = flags & (PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64);
+    if (f == 0) return FIT_AUTO;
+    if (f == PLIC_FLAG_FIT_FP32) return FIT_FP32;
+    if (f == PLIC_FLAG_FIT_DF32) return FIT_DF32;
+    if (f == PLIC_FLAG_FIT_FP64) return FIT_FP64;
+    return -1;
 }
 
 static const void* select(bool batched, plic_method m, int fit) {
@@ -95,7 +134,7 @@ static const void* select(bool batched, plic_method m, int fit) {
 }
 
 static const uint32_t kCurvFlags = PLIC_FLAG_POINT_CENTROID | PLIC_FLAG_KAPPA_PAPER_SIGN |
-                                   PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32;
+                                   PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64;
 
 }  // namespace plic
 
@@ -104,15 +143,15 @@ extern "C" plic_status vof_curvature(const float* phi, int nx, int ny, int nz, c
                                      plic_method m, uint32_t flags, void* stream) {
     using namespace plic;
     if (nx < 3 || ny < 3 || nz < 3 || n_iface < 0) return PLIC_ERR_ARG;
-    if ((int)m < 0 || (int)m > 4 || (flags & ~kCurvFlags)) return PLIC_ERR_ARG;
-    if ((flags & PLIC_FLAG_FIT_FP32) && (flags & PLIC_FLAG_FIT_DF32)) return PLIC_ERR_ARG;
+    if ((int)m < 0 || (int)m > 4 || (flags & ~kCurvFlags) || fit_mode(flags) < 0) return PLIC_ERR_ARG;
     if (n_iface == 0) return PLIC_OK;
     if (!phi || !idx || !kappa) return PLIC_ERR_ARG;
     if (!aligned(phi, 4) || !aligned(idx, 4) || !aligned(kappa, 4) || (d_n_iface && !aligned(d_n_iface, 8)))
         return PLIC_ERR_ALIGN;
     const void* k = select(false, m, fit_mode(flags));
-    const int threads = 128;
-    const int grid = stride_grid(k, threads, n_iface);
+    const int threads = CO_THREADS;
+    // one warp per 32 entries, at most one resident wave
+    const int grid = stride_grid(k, threads, (n_iface + CO_BATCH - 1) / CO_BATCH * 32);
     void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&idx, (void*)&n_iface,
                     (void*)&d_n_iface, (void*)&kappa, (void*)&flags};
     cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, as_stream(stream));
@@ -125,21 +164,22 @@ extern "C" plic_status vof_curvature_batched(const vof_field* fields, int n_fiel
                                              uint32_t flags, void* workspace, size_t ws_bytes,
                                              void* stream) {
     using namespace plic;
-    if (n_fields < 0 || (int)m < 0 || (int)m > 4 || (flags & ~kCurvFlags)) return PLIC_ERR_ARG;
-    if ((flags & PLIC_FLAG_FIT_FP32) && (flags & PLIC_FLAG_FIT_DF32)) return PLIC_ERR_ARG;
+    if (n_fields < 0 || (int)m < 0 || (int)m > 4 || (flags & ~kCurvFlags) || fit_mode(flags) < 0)
+        return PLIC_ERR_ARG;
     if (n_fields == 0) return PLIC_OK;
     if (!fields || !workspace) return PLIC_ERR_ARG;
     if (ws_bytes < plic_workspace_bytes(PLIC_WS_BATCHED, n_fields)) return PLIC_ERR_ARG;
     if (!aligned(workspace, 256)) return PLIC_ERR_ALIGN;
-    int threads = 128, chunk = 512, bps = 0;
+    int threads = CO_THREADS, chunk = 128, bps = 0;
     if (tuning) {
         threads = tuning->block_threads;
         chunk = tuning->cells_per_chunk;
         bps = tuning->blocks_per_sm;
         if (threads < 32 || threads > 1024 || (threads & 31) || chunk < 1 || bps < 0)
             return PLIC_ERR_ARG;
-        if (threads > 128) return PLIC_ERR_UNSUPPORTED;     // kernels are built for <= 128
+        if (threads != CO_THREADS) return PLIC_ERR_UNSUPPORTED;   // built for 4 warps per block
     }
+    chunk = (chunk + CO_BATCH - 1) / CO_BATCH * CO_BATCH;     // whole warp batches
     // host-side prefix of the list lengths and argument checks
     const size_t nf = (size_t)n_fields;
     int64_t* pre = (int64_t*)malloc((nf + 1) * sizeof(int64_t));
@@ -171,7 +211,7 @@ extern "C" plic_status vof_curvature_batched(const vof_field* fields, int n_fiel
     const int occ = blocks_per_sm(k, threads, 0);
     const int per_sm = bps > 0 ? (bps < occ ? bps : occ) : occ;
     int64_t grid = (int64_t)sm_count() * per_sm;
-    const int64_t need = (total + chunk - 1) / chunk;
+    const int64_t need = ((total + chunk - 1) / chunk + CO_WARPS - 1) / CO_WARPS;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     int n_f = n_fields;

@@ -22,7 +22,7 @@
 
 namespace plic {
 
-enum { FIT_FP64 = 0, FIT_FP32 = 1, FIT_DF32 = 2 };
+enum { FIT_FP64 = 0, FIT_FP32 = 1, FIT_DF32 = 2, FIT_AUTO = 3 };
 
 // D3Q27 directions e_0..e_26, packed as (ex+1) + 3 (ey+1) + 9 (ez+1).
 __constant__ unsigned char c_e27[27] = {

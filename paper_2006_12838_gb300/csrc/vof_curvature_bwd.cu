@@ -287,9 +287,9 @@ extern "C" plic_status vof_curvature_backward(const float* phi, int nx, int ny, 
     if (nx < 3 || ny < 3 || nz < 3 || n_iface < 0) return PLIC_ERR_ARG;
     if ((int)m < 0 || (int)m > 4) return PLIC_ERR_ARG;
     const uint32_t known = PLIC_FLAG_POINT_CENTROID | PLIC_FLAG_KAPPA_PAPER_SIGN |
-                           PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32;
-    if ((flags & ~known) || ((flags & PLIC_FLAG_FIT_FP32) && (flags & PLIC_FLAG_FIT_DF32)))
-        return PLIC_ERR_ARG;
+                           PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64;
+    const uint32_t fitf = flags & (PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64);
+    if ((flags & ~known) || (fitf & (fitf - 1u))) return PLIC_ERR_ARG;
     if (flags & PLIC_FLAG_POINT_CENTROID) return PLIC_ERR_UNSUPPORTED;
     const int64_t cells = (int64_t)nx * ny * nz;
     if (cells > 2147483647LL) return PLIC_ERR_ARG;
@@ -306,6 +306,7 @@ extern "C" plic_status vof_curvature_backward(const float* phi, int nx, int ny, 
     cudaError_t e = cudaMemsetAsync(slot, 0xff, (size_t)cells * sizeof(int32_t), s);
     if (e != cudaSuccess) { set_last_error("vof_curvature_backward", e); return PLIC_ERR_CUDA; }
     if (n_iface > 0) {
+        // the adaptive default differentiates with the FP64 factorisation
         const int fit = (flags & PLIC_FLAG_FIT_DF32) ? FIT_DF32 : (flags & PLIC_FLAG_FIT_FP32) ? FIT_FP32 : FIT_FP64;
         const void* k = nullptr;
         switch (m) {

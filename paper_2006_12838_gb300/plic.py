@@ -23,6 +23,7 @@ FLAG_POINT_CENTROID = 2
 FLAG_KAPPA_PAPER_SIGN = 4
 FLAG_FIT_FP32 = 8
 FLAG_FIT_DF32 = 16
+FLAG_FIT_FP64 = 32
 WS_COMPACT = 0
 WS_BATCHED = 2
 

@@ -78,15 +78,16 @@ def _check(kappa, kref, dim, tol, label):
 
 
 @pytest.mark.parametrize("method", list(plic.METHODS))
-def test_curvature_methods_fp64_fit(dev, orc, field, method):
+def test_curvature_methods_default_fit(dev, orc, field, method):
     p, idx = field
     kref, dim, _ = orc.curvature(p, idx)
     phid = torch.tensor(p, device=dev)
     k = plic.curvature(phid, torch.tensor(idx, device=dev), method=method).cpu().numpy()
-    _check(k.astype(np.float64), kref, dim, TOL, method + " fit64")
+    _check(k.astype(np.float64), kref, dim, TOL, method + " adaptive fit")
 
 
-@pytest.mark.parametrize("fit,tol", [(plic.FLAG_FIT_DF32, TOL), (plic.FLAG_FIT_FP32, 1e-2)])
+@pytest.mark.parametrize("fit,tol", [(plic.FLAG_FIT_DF32, TOL), (plic.FLAG_FIT_FP64, TOL),
+                                     (plic.FLAG_FIT_FP32, 1e-3)])
 def test_curvature_fit_precisions(dev, orc, field, fit, tol):
     p, idx = field
     kref, dim, _ = orc.curvature(p, idx)
