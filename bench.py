@@ -38,6 +38,8 @@ if ROOT not in sys.path:
 METRIC = "G PLIC solves/s & curvature cells/s vs roofline, FP32-polished vs FP64"
 UNIT = "G solves/s"
 CELLS = 1 << 28
+# curvature fit precisions: adaptive FP32/FP64 (default), FP64, double-float, FP32
+FITS = ((0, "auto"), (32, "fit64"), (16, "fitdf32"), (8, "fit32"))
 
 
 def peaks():
@@ -256,13 +258,13 @@ def section_curvature(dev, pk, steps):
     sec = timed(lambda: plic.interface_compact(phi, idx=idx, count=cnt2, workspace=ws), steps, 3, s)
     out["compact"] = {"ms": sec / steps * 1e3,
                       "hbm_gbs": (phi.numel() * 4 + k * 4) * steps / sec / 1e9}
-    for fit, name in ((0, "fit64"), (plic.FLAG_FIT_DF32, "fitdf32"), (plic.FLAG_FIT_FP32, "fit32")):
+    for fit, name in FITS:
         sec = timed(lambda: plic.curvature(phi, it, kappa=kap, flags=fit), steps, 3, s)
         out["curvature_sz_opt_" + name] = {"ms": sec / steps * 1e3,
                                             "m_cells_s": k * steps / sec / 1e6}
     for m in plic.METHODS:
         sec = timed(lambda: plic.curvature(phi, it, kappa=kap, method=m), steps, 2, s)
-        out["curvature_%s_fit64" % m] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+        out["curvature_%s_auto" % m] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
 
     def pipeline():
         plic.interface_compact(phi, idx=idx, count=cnt2, workspace=ws)
@@ -288,8 +290,13 @@ def section_batched(dev, pk, steps):
         cells += phi.numel()
     s = torch.cuda.current_stream()
     out = {"fields": len(args), "field_cells": cells, "interface_cells": tot}
-    for fit, name in ((0, "fit64"), (plic.FLAG_FIT_DF32, "fitdf32"), (plic.FLAG_FIT_FP32, "fit32")):
-        sec = timed(lambda: plic.curvature_batched(args, flags=fit), steps, 2, s)
+    from paper_2006_12838_gb300 import autotune
+    shape, times = autotune.tune(args, flags=0, force=True)
+    out["autotune"] = {"shape": list(shape), "candidates": len(times),
+                       "best_ms": min(times.values()) if times else None,
+                       "worst_ms": max(times.values()) if times else None}
+    for fit, name in FITS:
+        sec = timed(lambda: plic.curvature_batched(args, flags=fit, tuning=shape), steps, 2, s)
         out["batched_" + name] = {"ms": sec / steps * 1e3, "m_cells_s": tot * steps / sec / 1e6}
     return out
 
@@ -429,22 +436,18 @@ def main():
         return run_case(args)
 
     import torch
-    import torch.distributed as dist
     from paper_2006_12838_gb300 import build as B
+    from paper_2006_12838_gb300 import dist as D
     from paper_2006_12838_gb300 import plic
     from paper_2006_12838_gb300.pipeline import HostOffsetPipeline
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    rank, world, local = D.rank_info()
     torch.cuda.set_device(local)
+    D.init("nccl")
     dev = torch.device("cuda", local)
     if rank == 0:
         B.build()
-    if world > 1:
-        dist.barrier()
+    D.barrier()
     B.build()
     plic.load()
     pk = peaks()
@@ -469,8 +472,7 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    D.barrier()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -481,14 +483,10 @@ def main():
         b.record(s)
         torch.cuda.synchronize()
         time.sleep(0.3)
-    sec = a.elapsed_time(b) / 1e3
-    if world > 1:
-        tt = torch.tensor([sec], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        sec = float(tt.item())
-        dist.barrier()
+    sec = D.max_over_ranks(a.elapsed_time(b) / 1e3, dev)
+    D.barrier()
     kern_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
-    value = CELLS * world * args.steps / sec / 1e9
+    value = D.weak_scaling_value(CELLS, world, args.steps, sec) / 1e9
     # accuracy of the timed result: round trip on a sample of the output
     rt = (Vrt - t32[3]).abs()
     rt_max = float(rt.max().item())
@@ -511,7 +509,7 @@ def main():
             pipe.run(*hn, hd, hV)
         b.record(s)
         torch.cuda.synchronize()
-        esec = time.perf_counter() - t0
+        esec = D.max_over_ranks(time.perf_counter() - t0, dev)
         e2e = {"value": CELLS * world * esteps / esec / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 16 * CELLS, "d2h_bytes_per_step": 8 * CELLS,
                "steps": esteps, "chunk_cells": 1 << 24,
@@ -565,6 +563,7 @@ def main():
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
 
 

@@ -146,7 +146,7 @@ plic_status vof_interface_compact(const float *phi, int nx, int ny, int nz, int3
  * real-time step loop, a callback that must not synchronise the device), or a
  * foreign-language host without a device allocator.  The paper has no
  * counterpart; this is a deployment variant.
- * Its scratch (one int per tile of 4096 cells) is a fixed array inside the
+ * Its scratch (one int per tile of at least 8192 cells) is a fixed array inside the
  * library, held by every GPU that loads the library until the process exits,
  * so fields are limited to PLIC_NOALLOC_MAX_CELLS cells; larger fields return
  * PLIC_ERR_ARG with an explanation in plic_last_error().  The call allocates
@@ -157,7 +157,7 @@ plic_status vof_interface_compact(const float *phi, int nx, int ny, int nz, int3
  * streams, other host threads) race and must be serialised by the caller.
  * The scratch needs no clearing between calls.  Other arguments and the
  * output are as for vof_interface_compact. */
-#define PLIC_NOALLOC_MAX_CELLS 268435456LL  /* 2^28 cells: 65536 tiles, 256 KiB */
+#define PLIC_NOALLOC_MAX_CELLS 268435456LL  /* 2^28 cells: at most 32769 tiles, 128 KiB */
 plic_status vof_interface_compact_noalloc(const float *phi, int nx, int ny, int nz,
                                           int32_t *idx, int64_t idx_capacity,
                                           int64_t *d_count, void *stream);

@@ -22,8 +22,8 @@ import torch
 from . import build as _build
 from . import plic
 
-CANDIDATES = [(bt, ch, bps) for bt in (64, 96, 128) for ch in (32, 128, 512, 2048)
-              for bps in (0, 2, 4)]
+CANDIDATES = [(128, ch, bps) for ch in (32, 64, 128, 256, 512, 1024, 4096)
+              for bps in (0, 1, 2, 3)]
 _lock = threading.Lock()
 
 

@@ -3,7 +3,7 @@
 //
 // Three launches, no atomics and no inter-block waiting, so the list is in
 // ascending cell order and identical run to run.  A tile is a run of whole
-// x-rows (about 4096 cells):
+// x-rows (about 16384 cells):
 //   1. k_compact_count : each block counts the interface cells of its tile.
 //   2. k_compact_scan  : one block turns the per-tile counts into exclusive
 //                        offsets (in place) and writes the total to *d_count.
@@ -22,8 +22,8 @@ namespace plic {
 
 constexpr int CT_THREADS = 256;
 constexpr int CT_WARPS = CT_THREADS / 32;
-constexpr int CT_TILE = 4096;            // cells per tile (whole x-rows)
-constexpr int CT_MAX_ROWS = 1024;        // rows per tile at most (nx >= 4)
+constexpr int CT_TILE = 16384;           // cells per tile (whole x-rows)
+constexpr int CT_MAX_ROWS = 4096;        // rows per tile at most (tiles >= 8192 cells for nx >= 3)
 constexpr int CT_MAX_WORDS = 2048;       // ballot words per tile kept in shared memory
 
 // Rows (x-lines) per tile: as many whole rows as fit in CT_TILE cells.
@@ -270,8 +270,8 @@ extern "C" size_t plic_workspace_bytes(int op, int64_t arg) {
     if (arg < 0) return 0;
     switch (op) {
         case PLIC_WS_COMPACT: {
-            // tile counts: tiles hold >= 2048 cells (or one whole row), so a
-            // field of arg cells has at most 2 arg / 4096 + 1 tiles; interface
+            // tile counts: tiles hold >= CT_TILE/2 cells (or one whole row), so a
+            // field of arg cells has at most 2 arg / CT_TILE + 1 tiles; interface
             // bits: one word per 32 cells of each row, at most arg / 16 words
             // for rows of >= 32 cells (shorter rows keep no bits)
             const int64_t t = (arg + plic::CT_TILE - 1) / plic::CT_TILE * 2 + 1;
@@ -327,7 +327,7 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
 // ---------------------------------------------------------------------------
 // Allocation-free variant.  The per-tile scratch of the three passes lives in
 // a file-scope device array instead of a caller-provided workspace.  Every
-// GPU that loads the library holds these 256 KiB until the process exits.
+// GPU that loads the library holds these 128 KiB until the process exits.
 // ---------------------------------------------------------------------------
 namespace plic {
 

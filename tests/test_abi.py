@@ -49,8 +49,8 @@ def test_status_strings_and_version(lib):
 
 
 def test_workspace_sizes(lib):
-    # one int per tile (tiles of whole rows, >= 2048 cells each), rounded up to 256 bytes
-    assert lib.plic_workspace_bytes(plic.WS_COMPACT, 256 ** 3) == ((2 * 4096 + 1) * 4 + 255) // 256 * 256 + ((256 ** 3 // 16 + 1) * 4 + 255) // 256 * 256
+    # one int per tile (tiles of whole rows, >= 8192 cells each) + 1 bit per cell, 256-byte rounded
+    assert lib.plic_workspace_bytes(plic.WS_COMPACT, 256 ** 3) == ((2 * 1024 + 1) * 4 + 255) // 256 * 256 + ((256 ** 3 // 16 + 1) * 4 + 255) // 256 * 256
     assert lib.plic_workspace_bytes(plic.WS_COMPACT, 1) == 512
     assert lib.plic_workspace_bytes(plic.WS_BATCHED, 64) >= 64 * (ctypes.sizeof(plic.VofField) + 8)
     assert lib.plic_workspace_bytes(77, 10) == 0

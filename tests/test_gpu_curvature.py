@@ -136,7 +136,7 @@ def test_batched_matches_single(dev, orc):
         kap = torch.empty(max(k, 1), device=dev)
         args.append((phid, it, k, kap))
         singles.append(plic.curvature(phid, it).cpu().numpy() if k else np.zeros(0, np.float32))
-    for tuning in (None, (128, 64, 1), (64, 7, 2), (96, 1000, 0)):
+    for tuning in (None, (128, 64, 1), (128, 7, 2), (128, 1000, 0)):
         plic.curvature_batched(args, tuning=tuning)
         for (phid, it, k, kap), s in zip(args, singles):
             np.testing.assert_allclose(kap[:k].cpu().numpy(), s, rtol=1e-6, atol=1e-7)
