@@ -51,12 +51,22 @@ def peaks():
         return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-def kernel_source_hash():
+# Sources of each profiled kernel's translation unit: a change to any of them
+# makes the stored ncu traffic figure stale.
+KERNEL_SOURCES = {
+    "plic_offset_sz_opt_fp32p": ("plic_offset.cu", "plic_pair.cuh", "plic_solvers.cuh",
+                                 "plic_math.cuh", "host_common.h"),
+}
+
+
+def kernel_source_hash(kernel_key):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2006_12838_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES[kernel_key]:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
+    with open(os.path.join(ROOT, "include", "plic.h"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -68,7 +78,7 @@ def profile_traffic(kernel_key):
         with open(path) as f:
             t = json.load(f)
         e = t[kernel_key]
-        if e.get("src_hash") != kernel_source_hash():
+        if e.get("src_hash") != kernel_source_hash(kernel_key):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -274,6 +284,30 @@ def section_curvature(dev, pk, steps):
     return out
 
 
+def section_curvature_adjoint(dev, pk, steps):
+    """Curvature VJP on the adjoint workload (128^3, one noisy ellipsoid):
+    forward curvature, backward (per-cell VJP + deterministic gather)."""
+    import torch
+    from paper_2006_12838_gb300 import plic, synth
+    phi, w = synth.adjoint_field(seed=4, device=dev)
+    idx, cnt = plic.interface_compact(phi)
+    k = int(cnt.item())
+    it = idx[:k].contiguous()
+    g = (torch.from_numpy(np.ascontiguousarray(w[:k])).to(dev, torch.float32) if w.size >= k
+         else torch.ones(k, device=dev))
+    gphi = torch.empty_like(phi)
+    ws = torch.empty(max(plic.curv_bwd_workspace_bytes(phi.numel(), k), 1), dtype=torch.uint8,
+                     device=dev)
+    kap = torch.empty(k, device=dev)
+    s = torch.cuda.current_stream()
+    out = {"field": "128^3 f32 ellipsoid semi-axes (12,18,24) + 1e-3 noise", "interface_cells": k}
+    sec = timed(lambda: plic.curvature(phi, it, kappa=kap), steps, 3, s)
+    out["forward"] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+    sec = timed(lambda: plic.curvature_backward(phi, it, g, g_phi=gphi, workspace=ws), steps, 3, s)
+    out["backward"] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+    return out
+
+
 def section_batched(dev, pk, steps):
     import torch
     from paper_2006_12838_gb300 import plic, synth
@@ -298,6 +332,39 @@ def section_batched(dev, pk, steps):
     for fit, name in FITS:
         sec = timed(lambda: plic.curvature_batched(args, flags=fit, tuning=shape), steps, 2, s)
         out["batched_" + name] = {"ms": sec / steps * 1e3, "m_cells_s": tot * steps / sec / 1e6}
+    return out
+
+
+def section_paper(dev, pk, steps, normals=1 << 26, normals64=1 << 20, L=256):
+    """The paper's GPU harness (Sec. 2.5): one thread per normal, L fill levels
+    in series, round-trip error summed; time per PLIC evaluation with and
+    without the blank run subtracted, and E_avg (Eqs. 27-28)."""
+    import torch
+    from paper_2006_12838_gb300 import plic, synth
+    s = torch.cuda.current_stream()
+    out = {"normals": normals, "levels": L, "normals_fp64": normals64,
+           "normal_set": "(1,0,0), (1,1,0)/sqrt2, 1/8 random x-y plane, rest random 3D"}
+    n = synth.paper_normals(normals, seed=7)
+    for dt, tag, cnt in ((torch.float32, "fp32", normals), (torch.float64, "fp64", normals64)):
+        t = [torch.tensor(n[j][:cnt], dtype=dt, device=dev) for j in range(3)]
+        acc = torch.zeros(1, dtype=torch.float64, device=dev)
+        evals = cnt * L
+
+        def run(m, prec, blank):
+            acc.zero_()
+            plic.paper_benchmark(*t, L=L, method=m, precision=prec, blank=blank, err_sum=acc)
+        precs = ("fp32p", "fp32") if tag == "fp32" else ("fp64",)
+        sec = timed(lambda: run("sz_opt", precs[0], True), steps, 1, s)
+        blank_ps = sec / steps / evals * 1e12
+        out["blank_%s_ps" % tag] = blank_ps
+        for m in plic.METHODS:
+            for prec in precs:
+                sec = timed(lambda: run(m, prec, False), steps if m != "nested" else 1, 1, s)
+                ps = sec / (steps if m != "nested" else 1) / evals * 1e12
+                out["%s_%s" % (m, prec)] = {"ps_per_plic": ps, "ps_minus_blank": ps - blank_ps,
+                                           "g_plic_s": 1e3 / ps,
+                                           "E_avg": acc.item() / evals}
+        del t
     return out
 
 
@@ -551,7 +618,9 @@ def main():
             torch.cuda.empty_cache()
             sec_out.update(section_fp64(dev, pk, 2 if args.quick else 3, CELLS))
             sec_out["curvature_256"] = section_curvature(dev, pk, steps)
+            sec_out["curvature_adjoint_128"] = section_curvature_adjoint(dev, pk, steps)
             sec_out["batched_64_fields"] = section_batched(dev, pk, steps)
+            sec_out["paper_harness"] = section_paper(dev, pk, 2)
         except Exception as ex:
             sec_out["error"] = repr(ex)[:300]
         line["sections"] = sec_out

@@ -17,7 +17,8 @@
  *   invalid argument returns PLIC_ERR_ARG (or PLIC_ERR_ALIGN) and launches
  *   nothing.  A launch failure returns PLIC_ERR_CUDA; the CUDA error text is
  *   available from plic_last_error() on the calling thread.
- * - FP32 precisions take float arrays, PLIC_FP64 takes double arrays.
+ * - FP32 precisions take float arrays, PLIC_FP64 and PLIC_FP64_REFINED take
+ *   double arrays.
  * - Fill fields are float, laid out x-fastest: phi[x + nx*(y + ny*z)].
  *   Interface-cell lists hold int32 linear indices into that layout.
  * - No entry point throws, blocks on the device, or keeps global state other
@@ -57,7 +58,11 @@ typedef enum {
 typedef enum {
     PLIC_FP32 = 0,           /* float in/out, fast-math solver                      */
     PLIC_FP32_POLISHED = 1,  /* float in/out, solver + one Newton step on Eq. 10    */
-    PLIC_FP64 = 2            /* double in/out, the solver in double                 */
+    PLIC_FP64 = 2,           /* double in/out, the solver in double                 */
+    PLIC_FP64_REFINED = 3    /* double in/out, the FP32 solver (polished) on the
+                                inputs rounded to float, then two FP64 Newton steps
+                                on Eq. 10: FP64 accuracy with the trigonometry on
+                                the FP32 pipes (plic_offset only)                   */
 } plic_precision;
 
 enum {
@@ -221,6 +226,20 @@ typedef struct {
 plic_status vof_curvature_batched(const vof_field *fields, int n_fields,
                                   const vof_tuning *tuning, plic_method m, uint32_t flags,
                                   void *workspace, size_t ws_bytes, void *stream);
+
+/* plic_paper_benchmark -- the accuracy/throughput harness of Sec. 2.5: each
+ * of the n_normals unit normals (nx, ny, nz: device arrays) is solved for the
+ * L equally spaced fill levels V0_j = j/(L-1), j = 0..L-1, in series, and the
+ * round-trip errors E = |V0(n, d0(V0_j, n)) - V0_j| (Eqs. 27-28) are summed into
+ * *d_err_sum (device double, accumulated: zero it first); E_avg is the sum
+ * over n_normals * L.  blank != 0 runs the paper's "blank run": d0 = V0_j - 1/2
+ * instead of the solve, same loads, forward volume and sums.  Precisions
+ * PLIC_FP32, PLIC_FP32_POLISHED (float normals) and PLIC_FP64 (double).  Kawano's
+ * SZ returns NaN for axis-aligned normals at V0 in {0, 1}, so its sum is NaN
+ * when such a normal is present, as the paper reports. */
+plic_status plic_paper_benchmark(const void *nx, const void *ny, const void *nz,
+                                 int64_t n_normals, int L, plic_method m, plic_precision p,
+                                 int blank, double *d_err_sum, void *stream);
 
 /* Workspace kinds for plic_workspace_bytes(). */
 enum {

@@ -110,6 +110,31 @@ k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict_
     count_invalid(bad, invalid);
 }
 
+// PLIC_FP64_REFINED: double in/out, FP32 solve + two FP64 Newton steps.
+template <int METHOD>
+__global__ void __launch_bounds__(256)
+k_plic_offset_refined(const double* __restrict__ nx, const double* __restrict__ ny,
+                      const double* __restrict__ nz, const double* __restrict__ V0,
+                      double* __restrict__ d0, int64_t n, int vec_ok,
+                      unsigned long long* invalid) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    const int64_t nvec = vec_ok ? n / 2 : 0;
+    for (int64_t i = tid; i < nvec; i += stride) {
+        const double2 a = __ldcs(reinterpret_cast<const double2*>(nx) + i);
+        const double2 b = __ldcs(reinterpret_cast<const double2*>(ny) + i);
+        const double2 c = __ldcs(reinterpret_cast<const double2*>(nz) + i);
+        const double2 v = __ldcs(reinterpret_cast<const double2*>(V0) + i);
+        const double r0 = offset_cell_refined<METHOD>(a.x, b.x, c.x, v.x, bad);
+        const double r1 = offset_cell_refined<METHOD>(a.y, b.y, c.y, v.y, bad);
+        __stcs(reinterpret_cast<double2*>(d0) + i, make_double2(r0, r1));
+    }
+    for (int64_t i = nvec * 2 + tid; i < n; i += stride)
+        d0[i] = offset_cell_refined<METHOD>(nx[i], ny[i], nz[i], V0[i], bad);
+    count_invalid(bad, invalid);
+}
+
 typedef void (*offset_kernel_t)(const void*, const void*, const void*, const void*, void*,
                                 int64_t, int, unsigned long long*);
 
@@ -120,6 +145,7 @@ static const void* kptr() {
 
 template <int METHOD>
 static const void* pick(plic_precision p, bool faithful) {
+    if (p == PLIC_FP64_REFINED) return reinterpret_cast<const void*>(&k_plic_offset_refined<METHOD>);
     if (p == PLIC_FP64)
         return faithful ? kptr<METHOD, double, false, true>() : kptr<METHOD, double, false, false>();
     if (p == PLIC_FP32_POLISHED)
@@ -135,11 +161,13 @@ extern "C" plic_status plic_offset(const void* nx, const void* ny, const void* n
                                    void* stream) {
     using namespace plic;
     if (n < 0) return PLIC_ERR_ARG;
-    if ((int)m < 0 || (int)m > 4 || (int)p < 0 || (int)p > 2) return PLIC_ERR_ARG;
+    if ((int)m < 0 || (int)m > 4 || (int)p < 0 || (int)p > 3) return PLIC_ERR_ARG;
     if (flags & ~(uint32_t)PLIC_FLAG_FAITHFUL) return PLIC_ERR_ARG;
+    if (p == PLIC_FP64_REFINED && (flags & PLIC_FLAG_FAITHFUL)) return PLIC_ERR_UNSUPPORTED;
     if (n == 0) return PLIC_OK;
     if (!nx || !ny || !nz || !V0 || !d0) return PLIC_ERR_ARG;
-    const size_t es = p == PLIC_FP64 ? 8 : 4;
+    const bool dbl = p == PLIC_FP64 || p == PLIC_FP64_REFINED;
+    const size_t es = dbl ? 8 : 4;
     if (!aligned(nx, es) || !aligned(ny, es) || !aligned(nz, es) || !aligned(V0, es) ||
         !aligned(d0, es) || (d_invalid_count && !aligned(d_invalid_count, 8)))
         return PLIC_ERR_ALIGN;
@@ -151,7 +179,7 @@ extern "C" plic_status plic_offset(const void* nx, const void* ny, const void* n
         case PLIC_ANALYTIC: k = pick<M_ANALYTIC>(p, faithful); break;
         case PLIC_SZ_ORIG: k = pick<M_SZ_ORIG>(p, faithful); break;
         case PLIC_SZ_OPT:
-            if (p != PLIC_FP64 && !faithful)
+            if (!dbl && !faithful)
                 k = p == PLIC_FP32_POLISHED ? reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<true>)
                                             : reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<false>);
             else
@@ -161,7 +189,7 @@ extern "C" plic_status plic_offset(const void* nx, const void* ny, const void* n
         case PLIC_NESTED: k = pick<M_NESTED>(p, faithful); break;
     }
     const int threads = 256;
-    const int W = p == PLIC_FP64 ? 2 : 4;
+    const int W = dbl ? 2 : 4;
     const int64_t work = vec_ok ? (n + W - 1) / W : n;
     const int grid = stride_grid(k, threads, work);
     unsigned long long* inv = reinterpret_cast<unsigned long long*>(d_invalid_count);

@@ -434,6 +434,31 @@ __device__ __forceinline__ T offset_cell(T nx, T ny, T nz, T V0, int& bad) {
 }
 
 // ----------------------------------------------------------------------------
+// FP64 result from an FP32 solve: the method's FP32 solver on the inputs
+// rounded to float, then two Newton steps of polish() on the double problem.
+// The FP32 root is within ~1e-7 of the double root, so the first step lands
+// at ~1e-14 and the second at rounding level; the FP64 pipe runs ~50
+// operations per cell instead of a double-precision trigonometric solve.
+// ----------------------------------------------------------------------------
+template <int METHOD>
+__device__ __forceinline__ double offset_cell_refined(double nx, double ny, double nz, double V0,
+                                                      int& bad) {
+    const float g = offset_cell<METHOD, float, true, false>((float)nx, (float)ny, (float)nz,
+                                                            (float)V0, bad);
+    double n1, n2, n3;
+    reduce_normal<double, false>(nx, ny, nz, n1, n2, n3);
+    const double L = n1 + n2 + n3;
+    const bool ok = (V0 >= 0.0) && (V0 <= 1.0) && (L > 0.0) && (L <= 3.0);
+    if (!ok || g != g) return ok ? (double)g : (double)NAN;
+    const double h = 0.5 * L;
+    const double V = V0 <= 0.5 ? V0 : 1.0 - V0;
+    double d = fmin(fmax(h - fabs((double)g), 0.0), h);
+    d = polish<double>(d, V, n1, n2, n3);
+    d = polish<double>(d, V, n1, n2, n3);
+    return copysign(h - d, V0 - 0.5);
+}
+
+// ----------------------------------------------------------------------------
 // Forward problem, Eq. 10 (cases written without cancellation), for
 // 0 <= d <= L/2 with n1 <= n2 <= n3, n3 > 0.  Case (5) requires
 // n1 + n2 <= d <= n3 (the form min(n1+n2, n3) <= d of Eq. 10 would also admit

@@ -198,7 +198,7 @@ struct CellPlic {
     __device__ __forceinline__ void prepare(float nx, float ny, float nz) {
         reduce_normal<float, false>(nx, ny, nz, n1, n2, n3);
         L = fabsf(nx) + fabsf(ny) + fabsf(nz);
-        if (METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT) {
+        if (METHOD == M_SZ_ORIG) {
             m1 = n1 / L;
             m3 = n3 / L;
             m2 = fmaxf(1.0f - (m1 + m3), 0.0f);
@@ -207,9 +207,8 @@ struct CellPlic {
     // d0(V0, n) in FP32 with one Newton polish (PLIC_FP32_POLISHED); V0 in (0, 1).
     __device__ __forceinline__ float offset(float V0) const {
         const float V = V0 <= 0.5f ? V0 : 1.0f - V0;
-        if (METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT) {
-            float a = METHOD == M_SZ_ORIG ? solve_sz_orig<float, false>(V, m1, m2, m3)
-                                          : solve_sz_opt<float, false>(V, m1, m2, m3);
+        if (METHOD == M_SZ_ORIG) {
+            float a = solve_sz_orig<float, false>(V, m1, m2, m3);
             a = polish<float>(a, V, m1, m2, m3);
             return L * copysignf(0.5f - a, V0 - 0.5f);
         }
@@ -218,6 +217,73 @@ struct CellPlic {
                                        : solve_nested<float, false>(V, n1, n2, n3);
         d = polish<float>(d, V, n1, n2, n3);
         return copysignf(0.5f * (n1 + n2 + n3) - d, V0 - 0.5f);
+    }
+};
+
+// The optimised SZ solution (Sec. 2.4) with everything that depends on the
+// normal alone computed once per curvature cell (all neighbour solves of a
+// cell use the centre normal, Eq. 36).  Per solve there remain: the reduced
+// volume, four threshold tests on V, the closed forms of cases (5), (2), (1)
+// (the last as cbrt(6 m1 m2 m3) * cbrt(V)), the trigonometric root of cases
+// (3)/(4) with the cancellation-free arcsine argument written as
+// (n1+n2 - 2 m3 V) s3 or (1 - 2V) s4, and the FP32 Newton polish of the
+// trigonometric root.  Same cases and formulas as solve_sz_opt_default; the
+// thresholds are the product-form tests divided through once.
+template <>
+struct CellPlic<M_SZ_OPT> {
+    float L, m1, m2, m3, n12;
+    float V5, V1, V2, V3;
+    float s3, t3, s4, t4, k2a, k2b, cb1, inv1, k6;
+    __device__ __forceinline__ void prepare(float nx, float ny, float nz) {
+        const float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
+        L = ax + ay + az;
+        const float il = 1.0f / L;
+        m1 = fminf(fminf(ax, ay), az) * il;
+        m3 = fmaxf(fmaxf(ax, ay), az) * il;
+        m2 = fmaxf(1.0f - (m1 + m3), 0.0f);
+        n12 = m1 + m2;
+        const float m1m2 = m1 * m2, sq1 = m1 * m1;
+        const float k23 = 6.0f * m2 * m3;
+        V5 = 0.5f * n12 / m3;                                    // case (5): V >= V5
+        V1 = k23 > 0.0f ? sq1 / k23 : 0.0f;                      // case (1): V < V1
+        V2 = k23 > 0.0f ? (sq1 - 3.0f * m2 * (m1 - m2)) / k23 : 0.0f;  // case (2): V < V2
+        const float num3 = m3 * m3 * (3.0f * n12 - m3) + sq1 * (m1 - 3.0f * m3) + m2 * m2 * (m2 - 3.0f * m3);
+        V3 = (m3 < n12 && m1m2 > 0.0f) ? num3 / (k23 * m1) : 3.4e38f;  // case (3): V < V3
+        const float t32 = 2.0f * m1m2;
+        const float r3 = t32 > 0.0f ? rsqrtf(t32) : 0.0f;
+        t3 = t32 * r3;
+        s3 = 1.5f * m1m2 * r3 * r3 * r3;
+        const float d32 = m3 - m2;
+        const float t42 = 0.25f * (m1 * (2.0f * (m2 + m3) - m1) - d32 * d32);
+        const float r4 = t42 > 0.0f ? rsqrtf(t42) : 0.0f;
+        t4 = t42 * r4;
+        s4 = 0.75f * m1m2 * m3 * r4 * r4 * r4;
+        k2a = 8.0f * m2 * m3;
+        k2b = sq1 * (1.0f / 3.0f);
+        cb1 = Fm<float>::cbrt_(k23 * m1);
+        inv1 = m1 > 0.0f ? 1.0f / m1 : 0.0f;
+        k6 = k23;
+    }
+    __device__ __forceinline__ float offset(float V0) const {
+        const float V = fminf(V0, 1.0f - V0);
+        const bool c5 = V >= V5, c1 = V < V1, c2 = !c1 && V < V2, c3 = V < V3;
+        const float d5 = fmaf(m3, V, 0.5f * n12);
+        const float d2 = 0.5f * (m1 + Fm<float>::sqrt_(fmaxf(fmaf(k2a, V, -k2b), 1e-30f)));
+        const float d1 = cb1 * Fm<float>::cbrt_(V);
+        const float x = c3 ? fmaf(-2.0f * m3, V, n12) : fmaf(-2.0f, V, 1.0f);
+        const float arg = fminf(x * (c3 ? s3 : s4), 1.0f);
+        const float t = c3 ? t3 : t4, c = c3 ? n12 : 0.5f;
+        float d = fmaf(-2.0f * t, __sinf((1.0f / 3.0f) * fast_asinf(arg)), c);
+        // polish of the trigonometric root (cases 3/4: d >= m2, m1 > 0)
+        const float e2 = d - m2, e3 = fmaxf(d - m3, 0.0f);
+        const float e22 = e2 * e2, e33 = e3 * e3;
+        const float g = fmaf(3.0f * d, d - m1, m1 * m1) - fmaf(e22, e2, e33 * e3) * inv1 - k6 * V;
+        const float gp = fmaf(6.0f, d, -3.0f * m1) - 3.0f * (e22 + e33) * inv1;
+        d = d - __fdividef(g, gp);
+        d = c1 ? d1 : d;
+        d = c2 ? d2 : d;
+        d = c5 ? d5 : d;
+        return L * copysignf(0.5f - d, V0 - 0.5f);
     }
 };
 

@@ -17,7 +17,7 @@ import torch
 from . import build as _build
 
 METHODS = {"analytic": 0, "sz_orig": 1, "sz_opt": 2, "newton": 3, "nested": 4}
-PRECISIONS = {"fp32": 0, "fp32p": 1, "fp64": 2}
+PRECISIONS = {"fp32": 0, "fp32p": 1, "fp64": 2, "fp64r": 3}
 FLAG_FAITHFUL = 1
 FLAG_POINT_CENTROID = 2
 FLAG_KAPPA_PAPER_SIGN = 4
@@ -73,6 +73,7 @@ def load():
             "vof_curvature": [P, I32, I32, I32, P, I64, P, P, I32, U32, P],
             "vof_curvature_backward": [P, I32, I32, I32, P, I64, P, P, P, I32, U32, P, SZ, P],
             "vof_curvature_batched": [P, I32, P, I32, U32, P, SZ, P],
+            "plic_paper_benchmark": [P, P, P, I64, I32, I32, I32, I32, P, P],
         }
         for name, args in sigs.items():
             f = getattr(L, name, None)
@@ -131,7 +132,7 @@ def _prec(dtype, precision):
     if precision is None:
         return 2 if dtype == torch.float64 else 1
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    want = torch.float64 if p == 2 else torch.float32
+    want = torch.float64 if p >= 2 else torch.float32
     if dtype != want:
         raise PlicError("precision %s needs %s tensors" % (precision, want))
     return p
@@ -277,3 +278,18 @@ def curvature_batched(fields, method="sz_opt", flags=0, tuning=None, workspace=N
                                         None if tun is None else ctypes.cast(ctypes.pointer(tun), ctypes.c_void_p),
                                         m, flags, _ptr(workspace), workspace.numel(),
                                         _stream(fields[0][0], stream)), "vof_curvature_batched")
+
+
+def paper_benchmark(nx, ny, nz, L=256, method="sz_opt", precision=None, blank=False, err_sum=None,
+                    stream=None):
+    """Sec. 2.5 harness: sum over normals and L fill levels of the round-trip
+    error; returns the device accumulator (double, one element)."""
+    _cuda(nx, ny, nz, dtype=nx.dtype)
+    p = _prec(nx.dtype, precision)
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    if err_sum is None:
+        err_sum = torch.zeros(1, dtype=torch.float64, device=nx.device)
+    _check(load().plic_paper_benchmark(_ptr(nx), _ptr(ny), _ptr(nz), nx.numel(), int(L), m, p,
+                                       1 if blank else 0, _ptr(err_sum), _stream(nx, stream)),
+           "plic_paper_benchmark")
+    return err_sum

@@ -44,9 +44,9 @@ def _report(tag, err, n, V0, ref, d0, k=5):
 
 
 @pytest.mark.parametrize("method", list(plic.METHODS))
-@pytest.mark.parametrize("precision", ["fp32p", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32p", "fp64", "fp64r"])
 def test_vertex_cells(dev, orc, method, precision):
-    dtype = torch.float64 if precision == "fp64" else torch.float32
+    dtype = torch.float64 if precision.startswith("fp64") else torch.float32
     n, V0, vm = _inputs(orc, 1 << 20, 12, dtype, 0.5)
     ref = orc.offset(n[0], n[1], n[2], V0)
     t = [torch.tensor(a, dtype=dtype, device=dev) for a in (n[0], n[1], n[2], V0)]
@@ -57,7 +57,7 @@ def test_vertex_cells(dev, orc, method, precision):
     Vb = plic.volume(t[0], t[1], t[2], d0t).cpu().numpy().astype(np.float64)
     rt = np.abs(Vb - V0)
     print("   round trip max %.3e" % rt.max())
-    tol = 1e-12 if precision == "fp64" else 2e-6
+    tol = 1e-12 if precision.startswith("fp64") else 2e-6
     assert err.max() <= tol
     if precision == "fp32p":
         assert rt.max() <= 1e-6
