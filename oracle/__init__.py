@@ -18,6 +18,10 @@ Functions and the passages they follow:
 * :func:`curvature_grad_fd` -- central differences of sum_k w_k kappa_k.
 * :func:`lsq_paraboloid`, :func:`paraboloid_kappa`, :func:`py_normal` -- the
   individual curvature steps, exposed for the pins.
+* :func:`cm_normal`, :func:`normals` -- the centre-of-mass normal of Appendix B
+  and batched PY/CM normals.
+* :func:`sphere_volume`, :func:`sphere_offset` -- the plane-sphere problem of
+  Sec. 3 (spherical cap; inverse by bisection).
 
 Every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, brute force, high-precision re-evaluation and invariants.
@@ -40,6 +44,8 @@ _lib = None
 
 POINT_CENTROID = 2
 KAPPA_PAPER_SIGN = 4
+NORMAL_CM = 64
+NEIGHBOR_NORMAL = 128
 
 
 def build(force: bool = False) -> str:
@@ -81,7 +87,16 @@ def _load():
         lib.oracle_paraboloid_kappa.restype = D
         lib.oracle_paraboloid_kappa.argtypes = [P]
         lib.oracle_curvature_cell.restype = D
-        lib.oracle_curvature_cell.argtypes = [P, P, U, P, P]
+        lib.oracle_curvature_cell.argtypes = [P, P, P, U, P, P]
+        lib.oracle_cm_normal.restype = I32
+        lib.oracle_cm_normal.argtypes = [P, P]
+        lib.oracle_normal_batch.argtypes = [P, I32, I32, I32, P, I64, U, P, P, P]
+        lib.oracle_sphere_volume.restype = D
+        lib.oracle_sphere_volume.argtypes = [D]
+        lib.oracle_sphere_offset.restype = D
+        lib.oracle_sphere_offset.argtypes = [D]
+        lib.oracle_sphere_volume_batch.argtypes = [P, P, I64]
+        lib.oracle_sphere_offset_batch.argtypes = [P, P, I64]
         lib.oracle_curvature_batch.argtypes = [P, I32, I32, I32, P, I64, U, P, P, P]
         lib.oracle_curvature_grad_fd.argtypes = [P, I32, I32, I32, P, I64, P, D, U, P]
         _lib = lib
@@ -179,17 +194,63 @@ def paraboloid_kappa(x5) -> float:
     return float(_load().oracle_paraboloid_kappa(_ptr(x5)))
 
 
-def curvature_cell(phi27, flags: int = 0, iface27=None):
-    """Curvature of one stencil; returns (kappa, fit_dim, n_points)."""
+def curvature_cell(phi27, flags: int = 0, iface27=None, nn=None):
+    """Curvature of one stencil; returns (kappa, fit_dim, n_points).
+
+    ``nn`` (27 x 3, optional, used with NEIGHBOR_NORMAL): the normal of each
+    neighbour's PLIC plane; zero rows mean the centre normal."""
     s = _f64(phi27).ravel()
     dim = ctypes.c_int(0)
     npt = ctypes.c_int(0)
     mask = None
     if iface27 is not None:
         mask = np.ascontiguousarray(np.asarray(iface27, dtype=np.int32).ravel())
+    nn81 = None if nn is None else _f64(nn).ravel()
     k = _load().oracle_curvature_cell(_ptr(s), None if mask is None else _ptr(mask),
+                                      None if nn81 is None else _ptr(nn81),
                                       flags, ctypes.byref(dim), ctypes.byref(npt))
     return float(k), dim.value, npt.value
+
+
+def cm_normal(phi27):
+    """Centre-of-mass normal (Appendix B, unit weights); None if undefined."""
+    s = _f64(phi27).ravel()
+    assert s.size == 27
+    n = np.empty(3, np.float64)
+    ok = _load().oracle_cm_normal(_ptr(s), _ptr(n))
+    return n if ok else None
+
+
+def normals(phi, idx, flags: int = 0):
+    """PY (or CM with NORMAL_CM) normals of the listed cells, shape (3, k)."""
+    phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float32))
+    nz, ny, nx = phi.shape
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    out = np.empty((3, idx.size), np.float64)
+    _load().oracle_normal_batch(_ptr(phi), nx, ny, nz, _ptr(idx), idx.size, flags,
+                                _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
+    return out
+
+
+def sphere_radius() -> float:
+    """Radius of the unit-volume ball of Sec. 3."""
+    return (3.0 / (4.0 * np.pi)) ** (1.0 / 3.0)
+
+
+def sphere_volume(d0):
+    """Sec. 3: volume of the unit-volume ball below a plane at distance d0."""
+    d0 = _f64(d0).ravel()
+    out = np.empty(d0.shape, np.float64)
+    _load().oracle_sphere_volume_batch(_ptr(d0), _ptr(out), d0.size)
+    return out
+
+
+def sphere_offset(V0):
+    """Sec. 3: the inverse of :func:`sphere_volume` by bisection, FP64."""
+    V0 = _f64(V0).ravel()
+    out = np.empty(V0.shape, np.float64)
+    _load().oracle_sphere_offset_batch(_ptr(V0), _ptr(out), V0.size)
+    return out
 
 
 def interface_cells(phi) -> np.ndarray:

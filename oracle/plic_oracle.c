@@ -26,6 +26,10 @@
  *                        partial pivoting, mean curvature (Eq. 42).
  *   - oracle_curvature_grad_fd  central finite differences of sum_i w_i kappa_i
  *                        with respect to the fill field.
+ *   - oracle_cm_normal   the centre-of-mass normal of Appendix B (unit weights).
+ *   - oracle_sphere_volume / oracle_sphere_offset  the plane-sphere problem of
+ *                        Sec. 3: spherical-cap volume of the unit-volume ball
+ *                        and its inverse by bisection.
  *
  * Readings of the paper that this file fixes (where it is silent or garbled):
  *   - case (5) holds for n1+n2 <= d <= n3; written as min(n1+n2,n3) <= d the
@@ -39,6 +43,11 @@
  *     leading parameters in the order (A, B, C, H, I) are fitted; the others stay 0.
  *   - only cells whose 26 neighbours are all inside the field are curvature
  *     cells; the interface set is 0 < phi < 1 on the stored values.
+ *   - neighbour-normal variant (Sec. 4.2 mentions it; the paper gives no
+ *     formula): neighbour i contributes the point e_i + d0(phi_i, n_i) n_i
+ *     relative to the centre's d0(phi_0, n) n, with n_i its own normal; this is
+ *     Eq. 36 when n_i = n.  A neighbour whose own 3^3 stencil leaves the field,
+ *     or whose normal is undefined, uses the centre normal.
  */
 #include <math.h>
 #include <stdint.h>
@@ -313,6 +322,20 @@ ORC_EXPORT int oracle_py_normal(const double *phi27, double n[3])
     return 1;
 }
 
+/* Appendix B, centre-of-mass normal: n = -sum e_i phi_i / |.| (all weights 1).
+ * Returns 0 when the sum vanishes. */
+ORC_EXPORT int oracle_cm_normal(const double *phi27, double n[3])
+{
+    double g[3] = {0, 0, 0}, len;
+    int i, k;
+    for (i = 1; i < 27; ++i)
+        for (k = 0; k < 3; ++k) g[k] += E27[i][k] * phi27[i];
+    len = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (!(len > 0.0)) { n[0] = n[1] = n[2] = 0.0; return 0; }
+    for (k = 0; k < 3; ++k) n[k] = -g[k] / len;
+    return 1;
+}
+
 /* Gaussian elimination with partial pivoting on a k x k system (row-major
  * a[5][5], right-hand side b[5]); solution in x.  Returns the determinant. */
 static double gauss_solve(int k, const double ain[5][5], const double *bin, double *x)
@@ -395,30 +418,37 @@ ORC_EXPORT double oracle_paraboloid_kappa(const double *x5)
 
 #define ORC_POINT_CENTROID 2u
 #define ORC_KAPPA_PAPER_SIGN 4u
+#define ORC_NORMAL_CM 64u
+#define ORC_NEIGHBOR_NORMAL 128u
 
 /* Sec. 4.2: curvature of one interface cell from its 3^3 fill stencil in D3Q27
- * order.  Steps: Parker-Youngs normal (Eq. 38); frame b_z = n,
- * b_y = (b_z x r)/|.|, b_x = b_y x b_z with the fixed r of Sec. 4.2 (rotated
- * cyclically in the event that it is parallel to n); PLIC-corrected points
- * of the interface neighbours (Eq. 36), all with the centre normal;
- * least-squares paraboloid; Eq. 42.
- * Point mode (default): foot of the PLIC plane along n, as in Eq. 36.
+ * order.  Steps: Parker-Youngs normal (Eq. 38; the centre-of-mass normal of
+ * Appendix B with ORC_NORMAL_CM); frame b_z = n, b_y = (b_z x r)/|.|,
+ * b_x = b_y x b_z with the fixed r of Sec. 4.2 (rotated cyclically in the
+ * event that it is parallel to n); PLIC-corrected points of the interface
+ * neighbours (Eq. 36); least-squares paraboloid; Eq. 42.
+ * Point mode (default): foot of the PLIC plane along the normal, as in Eq. 36.
  * ORC_POINT_CENTROID: centroid of each neighbour's cut polygon instead.
+ * Normals of the neighbour planes: the centre normal (Eq. 36), or, with
+ * ORC_NEIGHBOR_NORMAL and nn81 != NULL, nn81[3i..3i+2] for neighbour i where
+ * that entry is non-zero (the centre normal where it is zero).
  * iface27 (nullable) fixes which neighbours count as interface cells; when it
  * is NULL the test 0 < phi_i < 1 is applied to phi27 itself.
  * Writes the fit dimension and the number of neighbour points; returns kappa
  * (-(Eq. 42) unless ORC_KAPPA_PAPER_SIGN). */
-ORC_EXPORT double oracle_curvature_cell(const double *phi27, const int *iface27, unsigned flags,
+ORC_EXPORT double oracle_curvature_cell(const double *phi27, const int *iface27,
+                                        const double *nn81, unsigned flags,
                                         int *dim_out, int *npts_out)
 {
     static const double R[3] = {0.56270900, 0.32704452, 0.75921047};
     double n[3], by[3], bx[3], r[3], len, d00, c0[3] = {0, 0, 0}, x5[5];
     double px[26], py[26], pz[26];
-    int i, k, m = 0, dim;
+    int i, k, m = 0, dim, ok;
 
     if (dim_out) *dim_out = 0;
     if (npts_out) *npts_out = 0;
-    if (!oracle_py_normal(phi27, n)) return 0.0;
+    ok = (flags & ORC_NORMAL_CM) ? oracle_cm_normal(phi27, n) : oracle_py_normal(phi27, n);
+    if (!ok) return 0.0;
     r[0] = R[0]; r[1] = R[1]; r[2] = R[2];
     for (k = 0; k < 2; ++k) {
         by[0] = n[1] * r[2] - n[2] * r[1];
@@ -439,23 +469,25 @@ ORC_EXPORT double oracle_curvature_cell(const double *phi27, const int *iface27,
         oracle_area_centroid(n[0], n[1], n[2], d00, &a, c0);
     }
     for (i = 1; i < 27; ++i) {
-        double v = phi27[i], d0i, q[3];
+        double v = phi27[i], d0i, q[3], ni[3];
         int is_iface = iface27 ? iface27[i] : (v > 0.0 && v < 1.0);
         if (!is_iface) continue;
-        d0i = oracle_offset(n[0], n[1], n[2], v);
+        for (k = 0; k < 3; ++k) ni[k] = n[k];
+        if ((flags & ORC_NEIGHBOR_NORMAL) && nn81 &&
+            (nn81[3 * i] != 0.0 || nn81[3 * i + 1] != 0.0 || nn81[3 * i + 2] != 0.0))
+            for (k = 0; k < 3; ++k) ni[k] = nn81[3 * i + k];
+        d0i = oracle_offset(ni[0], ni[1], ni[2], v);
         if (flags & ORC_POINT_CENTROID) {
             double a, ci[3];
-            oracle_area_centroid(n[0], n[1], n[2], d0i, &a, ci);
+            oracle_area_centroid(ni[0], ni[1], ni[2], d0i, &a, ci);
             for (k = 0; k < 3; ++k) q[k] = E27[i][k] + ci[k] - c0[k];
-            px[m] = q[0] * bx[0] + q[1] * bx[1] + q[2] * bx[2];
-            py[m] = q[0] * by[0] + q[1] * by[1] + q[2] * by[2];
-            pz[m] = q[0] * n[0] + q[1] * n[1] + q[2] * n[2];
         } else {
-            for (k = 0; k < 3; ++k) q[k] = E27[i][k];
-            px[m] = q[0] * bx[0] + q[1] * bx[1] + q[2] * bx[2];
-            py[m] = q[0] * by[0] + q[1] * by[1] + q[2] * by[2];
-            pz[m] = q[0] * n[0] + q[1] * n[1] + q[2] * n[2] + d0i - d00;
+            /* foot points d0 n of the two planes (Eq. 36 for ni = n) */
+            for (k = 0; k < 3; ++k) q[k] = E27[i][k] + d0i * ni[k] - d00 * n[k];
         }
+        px[m] = q[0] * bx[0] + q[1] * bx[1] + q[2] * bx[2];
+        py[m] = q[0] * by[0] + q[1] * by[1] + q[2] * by[2];
+        pz[m] = q[0] * n[0] + q[1] * n[1] + q[2] * n[2];
         ++m;
     }
     dim = oracle_lsq_paraboloid(m, px, py, pz, x5);
@@ -476,21 +508,64 @@ static void gather27(const float *phi, int nx, int ny, int64_t c, double *out)
     }
 }
 
+/* Neighbour normals for ORC_NEIGHBOR_NORMAL: for each interface neighbour i
+ * of cell c whose own 26 neighbours lie inside the field, its PY (or CM)
+ * normal; zero (centre normal) otherwise. */
+static void neighbour_normals(const float *phi, int nx, int ny, int nz, int64_t c,
+                              const double *s27, unsigned flags, double *nn81)
+{
+    int64_t x = c % nx, y = (c / nx) % ny, z = c / ((int64_t)nx * ny);
+    int i, k;
+    for (i = 0; i < 81; ++i) nn81[i] = 0.0;
+    for (i = 1; i < 27; ++i) {
+        int64_t xi = x + E27[i][0], yi = y + E27[i][1], zi = z + E27[i][2];
+        double t[27], ni[3];
+        int ok;
+        if (!(s27[i] > 0.0 && s27[i] < 1.0)) continue;
+        if (xi < 1 || yi < 1 || zi < 1 || xi > nx - 2 || yi > ny - 2 || zi > nz - 2) continue;
+        gather27(phi, nx, ny, xi + (int64_t)nx * (yi + (int64_t)ny * zi), t);
+        ok = (flags & ORC_NORMAL_CM) ? oracle_cm_normal(t, ni) : oracle_py_normal(t, ni);
+        if (ok)
+            for (k = 0; k < 3; ++k) nn81[3 * i + k] = ni[k];
+    }
+}
+
 /* Curvature for a list of interface cells (linear indices x + nx*(y + ny*z)). */
 ORC_EXPORT void oracle_curvature_batch(const float *phi, int nx, int ny, int nz,
                                        const int32_t *idx, int64_t n_iface, unsigned flags,
                                        double *kappa, int32_t *dim, int32_t *npts)
 {
     int64_t k;
-    (void)nz;
 #pragma omp parallel for schedule(dynamic, 64)
     for (k = 0; k < n_iface; ++k) {
-        double s[27];
+        double s[27], nn[81];
         int dm, np;
         gather27(phi, nx, ny, idx[k], s);
-        kappa[k] = oracle_curvature_cell(s, NULL, flags, &dm, &np);
+        if (flags & ORC_NEIGHBOR_NORMAL) neighbour_normals(phi, nx, ny, nz, idx[k], s, flags, nn);
+        kappa[k] = oracle_curvature_cell(s, NULL, (flags & ORC_NEIGHBOR_NORMAL) ? nn : NULL, flags,
+                                         &dm, &np);
         if (dim) dim[k] = dm;
         if (npts) npts[k] = np;
+    }
+}
+
+/* Normals (PY, or CM with ORC_NORMAL_CM) of a list of interface cells; zero
+ * where undefined. */
+ORC_EXPORT void oracle_normal_batch(const float *phi, int nx, int ny, int nz,
+                                    const int32_t *idx, int64_t n_iface, unsigned flags,
+                                    double *nx_out, double *ny_out, double *nz_out)
+{
+    int64_t k;
+    (void)nz;
+#pragma omp parallel for schedule(static)
+    for (k = 0; k < n_iface; ++k) {
+        double s[27], n[3];
+        gather27(phi, nx, ny, idx[k], s);
+        if (flags & ORC_NORMAL_CM) oracle_cm_normal(s, n);
+        else oracle_py_normal(s, n);
+        nx_out[k] = n[0];
+        ny_out[k] = n[1];
+        nz_out[k] = n[2];
     }
 }
 
@@ -517,9 +592,9 @@ ORC_EXPORT void oracle_curvature_grad_fd(const float *phi, int nx, int ny, int n
         for (j = 0; j < 27; ++j) {
             double keep = s[j], kp, km;
             s[j] = keep + h;
-            kp = oracle_curvature_cell(s, mask, flags, NULL, NULL);
+            kp = oracle_curvature_cell(s, mask, NULL, flags, NULL, NULL);
             s[j] = keep - h;
-            km = oracle_curvature_cell(s, mask, flags, NULL, NULL);
+            km = oracle_curvature_cell(s, mask, NULL, flags, NULL, NULL);
             s[j] = keep;
             contrib[27 * k + j] = w[k] * (kp - km) / (2.0 * h);
         }
@@ -533,4 +608,64 @@ ORC_EXPORT void oracle_curvature_grad_fd(const float *phi, int nx, int ny, int n
     }
     free(contrib);
     (void)nz;
+}
+
+/* ---------------------------------------------------------------------------
+ * Sec. 3: plane-sphere intersection.  The ball has unit volume, so its radius
+ * is r = (3/(4 pi))^(1/3).  V0(d0) is the volume of the part of the ball on
+ * the side n.x <= d0 of a plane at signed distance d0 from the centre: a
+ * spherical cap of height h = r + d0, V0 = pi h^2 (3r - h)/3
+ * = pi/3 (r + d0)^2 (2r - d0); 0 for d0 <= -r and 1 for d0 >= r.  The
+ * normal's direction does not matter.
+ * ------------------------------------------------------------------------- */
+static double sphere_radius(void) { return cbrt(3.0 / (4.0 * 3.14159265358979323846)); }
+
+ORC_EXPORT double oracle_sphere_volume(double d0)
+{
+    double r = sphere_radius(), h;
+    if (isnan(d0)) return NAN;
+    if (d0 <= -r) return 0.0;
+    if (d0 >= r) return 1.0;
+    h = r + d0;
+    return 3.14159265358979323846 / 3.0 * h * h * (3.0 * r - h);
+}
+
+/* The inverse: d0 in [-r, r] with V0(d0) = V0, by bisection down to adjacent
+ * doubles (V0 increases strictly on [-r, r]).  By the symmetry
+ * V0(-d0) = 1 - V0(d0) the search runs for W = min(V0, 1 - V0) on [-r, 0]
+ * and the sign is restored, so the residual stays relative to W. */
+ORC_EXPORT double oracle_sphere_offset(double V0)
+{
+    double r = sphere_radius(), W, lo, hi, d;
+    int it;
+    if (isnan(V0) || V0 < 0.0 || V0 > 1.0) return NAN;
+    W = V0 <= 0.5 ? V0 : 1.0 - V0;
+    lo = -r;
+    hi = 0.0;
+    if (W == 0.0) {
+        d = -r;
+    } else {
+        for (it = 0; it < 2200; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (oracle_sphere_volume(mid) < W) lo = mid;
+            else hi = mid;
+        }
+        d = (W - oracle_sphere_volume(lo) <= oracle_sphere_volume(hi) - W) ? lo : hi;
+    }
+    return V0 <= 0.5 ? d : -d;
+}
+
+ORC_EXPORT void oracle_sphere_volume_batch(const double *d0, double *V0, int64_t n)
+{
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i) V0[i] = oracle_sphere_volume(d0[i]);
+}
+
+ORC_EXPORT void oracle_sphere_offset_batch(const double *V0, double *d0, int64_t n)
+{
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i) d0[i] = oracle_sphere_offset(V0[i]);
 }
