@@ -276,11 +276,46 @@ def section_curvature(dev, pk, steps):
         sec = timed(lambda: plic.curvature(phi, it, kappa=kap, method=m), steps, 2, s)
         out["curvature_%s_auto" % m] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
 
+    for flags, name in ((plic.FLAG_NORMAL_CM, "cm_normal"),
+                        (plic.FLAG_NEIGHBOR_NORMAL, "neighbor_normals"),
+                        (plic.FLAG_NEIGHBOR_NORMAL | plic.FLAG_NORMAL_CM, "neighbor_normals_cm")):
+        sec = timed(lambda: plic.curvature(phi, it, kappa=kap, flags=flags), steps, 2, s)
+        out["curvature_sz_opt_" + name] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+    nrm = torch.empty((3, k), device=dev)
+    for flags, name in ((0, "py"), (plic.FLAG_NORMAL_CM, "cm")):
+        sec = timed(lambda: plic.normals(phi, it, out=nrm, flags=flags), steps, 3, s)
+        out["normals_" + name] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+    sec = timed(lambda: plic.laplace_pressure(phi, it, 0.0728, dp=kap), steps, 3, s)
+    out["laplace_pressure"] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+
     def pipeline():
         plic.interface_compact(phi, idx=idx, count=cnt2, workspace=ws)
         plic.curvature(phi, idx, n_iface=k, count=cnt2, kappa=kap)
     sec = timed(pipeline, steps, 3, s)
     out["compact_plus_curvature"] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+    return out
+
+
+def section_sphere(dev, pk, steps, cells=1 << 28):
+    """Plane-sphere inverse and forward (Sec. 3): 8 B/cell FP32, 16 B/cell FP64."""
+    import torch
+    from paper_2006_12838_gb300 import plic
+    s = torch.cuda.current_stream()
+    out = {}
+    g = torch.Generator(device=dev)
+    g.manual_seed(86)
+    for dt, tag, n, bpc in ((torch.float32, "fp32", cells, 8.0), (torch.float64, "fp64", cells // 2, 16.0)):
+        V0 = torch.rand(n, device=dev, dtype=dt, generator=g)
+        d0 = torch.empty_like(V0)
+        V1 = torch.empty_like(V0)
+        for name, fn in (("offset", lambda: plic.sphere_offset(V0, out=d0)),
+                         ("volume", lambda: plic.sphere_volume(d0, out=V1))):
+            sec = timed(fn, steps, 2, s)
+            gbs = bpc * n * steps / sec / 1e9
+            out["sphere_%s_%s" % (name, tag)] = {"g_cells_s": n * steps / sec / 1e9,
+                                                 "ms": sec / steps * 1e3, "hbm_gbs": gbs,
+                                                 "hbm_frac": frac(gbs, pk["hbm_gbs"]), "cells": n}
+        del V0, d0, V1
     return out
 
 
@@ -344,9 +379,12 @@ def section_paper(dev, pk, steps, normals=1 << 26, normals64=1 << 20, L=256):
     s = torch.cuda.current_stream()
     out = {"normals": normals, "levels": L, "normals_fp64": normals64,
            "normal_set": "(1,0,0), (1,1,0)/sqrt2, 1/8 random x-y plane, rest random 3D"}
-    n = synth.paper_normals(normals, seed=7)
     for dt, tag, cnt in ((torch.float32, "fp32", normals), (torch.float64, "fp64", normals64)):
-        t = [torch.tensor(n[j][:cnt], dtype=dt, device=dev) for j in range(3)]
+        # the normal set is built for each size, so both keep the paper's mix
+        # (1/8 of the normals in the x-y plane, the rest 3D)
+        n = synth.paper_normals(cnt, seed=7)
+        t = [torch.tensor(n[j], dtype=dt, device=dev) for j in range(3)]
+        del n
         acc = torch.zeros(1, dtype=torch.float64, device=dev)
         evals = cnt * L
 
@@ -617,6 +655,7 @@ def main():
             del t32, d0, Vrt
             torch.cuda.empty_cache()
             sec_out.update(section_fp64(dev, pk, 2 if args.quick else 3, CELLS))
+            sec_out["sphere"] = section_sphere(dev, pk, steps)
             sec_out["curvature_256"] = section_curvature(dev, pk, steps)
             sec_out["curvature_adjoint_128"] = section_curvature_adjoint(dev, pk, steps)
             sec_out["batched_64_fields"] = section_batched(dev, pk, steps)

@@ -85,7 +85,19 @@ enum {
      * bits) on the FP32 pipes. */
     PLIC_FLAG_FIT_DF32 = 16u,
     /* FIT_FP64: in FP64 for every cell. */
-    PLIC_FLAG_FIT_FP64 = 32u
+    PLIC_FLAG_FIT_FP64 = 32u,
+    /* Normals (vof_normal, vof_curvature, vof_curvature_backward): the
+     * centre-of-mass normal of Appendix B (all 26 weights 1) instead of the
+     * Parker-Youngs normal of Eq. 38. */
+    PLIC_FLAG_NORMAL_CM = 64u,
+    /* vof_curvature only: the neighbour-normal variant of Sec. 4.2.  Each
+     * interface neighbour i is placed with its own normal n_i (from its own
+     * 3^3 stencil): point e_i + d0(phi_i, n_i) n_i relative to the centre's
+     * d0(phi_0, n) n (with POINT_CENTROID: e_i + c(n_i) - c(n)); this is Eq. 36
+     * when n_i = n.  A neighbour whose stencil leaves the field, or whose normal
+     * is undefined, uses the centre normal.  Not available in the batched and
+     * backward calls (PLIC_ERR_UNSUPPORTED). */
+    PLIC_FLAG_NEIGHBOR_NORMAL = 128u
 };
 
 /* plic_volume -- forward problem ("inverse PLIC", Sec. 2.2, Eq. 10 with Eqs.
@@ -185,6 +197,26 @@ plic_status vof_curvature(const float *phi, int nx, int ny, int nz, const int32_
                           int64_t n_iface, const int64_t *d_n_iface, float *kappa,
                           plic_method m, uint32_t flags, void *stream);
 
+/* vof_normal -- interface normals of the listed cells (Appendix B): the
+ * Parker-Youngs normal n = -sum w_i e_i phi_i / |.| (Eq. 38), or with
+ * PLIC_FLAG_NORMAL_CM the centre-of-mass normal (unit weights), written as
+ * three float arrays n_x[k], n_y[k], n_z[k] (structure of arrays, caller-owned
+ * device memory, n_iface entries each).  A zero weighted sum gives (0, 0, 0).
+ * n_iface / d_n_iface as for vof_curvature; every listed cell must have its
+ * 26 neighbours inside the field.  Errors: PLIC_ERR_ARG (sizes, null
+ * pointers, flags other than NORMAL_CM), PLIC_ERR_ALIGN, PLIC_ERR_CUDA. */
+plic_status vof_normal(const float *phi, int nx, int ny, int nz, const int32_t *idx,
+                       int64_t n_iface, const int64_t *d_n_iface, float *n_x, float *n_y,
+                       float *n_z, uint32_t flags, void *stream);
+
+/* vof_laplace_pressure -- the Young-Laplace pressure jump of Sec. 4.1,
+ * dp[k] = 2 sigma kappa[k], with kappa computed exactly as vof_curvature does
+ * (same arguments, flags and solver) and the factor applied in the kernel's
+ * epilogue (no second pass over the list). */
+plic_status vof_laplace_pressure(const float *phi, int nx, int ny, int nz, const int32_t *idx,
+                                 int64_t n_iface, const int64_t *d_n_iface, float sigma,
+                                 float *dp, plic_method m, uint32_t flags, void *stream);
+
 /* vof_curvature_backward -- vector-Jacobian product of vof_curvature with
  * respect to the fill field: g_phi = d(sum_k g_kappa[k] kappa[k]) / d phi,
  * with the interface set (idx and the neighbour flags 0 < phi < 1) held fixed.
@@ -240,6 +272,26 @@ plic_status vof_curvature_batched(const vof_field *fields, int n_fields,
 plic_status plic_paper_benchmark(const void *nx, const void *ny, const void *nz,
                                  int64_t n_normals, int L, plic_method m, plic_precision p,
                                  int blank, double *d_err_sum, void *stream);
+
+/* plic_sphere_volume / plic_sphere_offset -- the plane-sphere problem of
+ * Sec. 3.  The cell is the ball of unit volume, radius r = (3/(4 pi))^(1/3);
+ * d0 is the signed distance of the plane from the centre (the normal's
+ * direction does not matter) and V0 the volume on the side n.x <= d0, the
+ * spherical cap V0 = pi/3 (r + d0)^2 (2r - d0).
+ *   plic_sphere_volume: d0[n] -> V0[n]; d0 outside [-r, r] gives 0 or 1,
+ *                       NaN gives NaN.
+ *   plic_sphere_offset: V0[n] -> d0[n] in [-r, r]; V0 outside [0, 1] or NaN
+ *                       gives NaN.
+ * Arrays: caller-owned device memory, float (PLIC_FP32, PLIC_FP32_POLISHED)
+ * or double (PLIC_FP64, PLIC_FP64_REFINED); the FP32 inverse always ends with
+ * Newton steps, so the two FP32 precisions (and the two FP64 ones) are the
+ * same computation.  16-byte aligned arrays take the vector path.  Errors:
+ * PLIC_ERR_ARG (n < 0, null pointer, bad precision), PLIC_ERR_ALIGN (element
+ * misalignment), PLIC_ERR_CUDA (launch failure).  Asynchronous on stream. */
+plic_status plic_sphere_volume(const void *d0, void *V0, int64_t n, plic_precision p,
+                               void *stream);
+plic_status plic_sphere_offset(const void *V0, void *d0, int64_t n, plic_precision p,
+                               void *stream);
 
 /* Workspace kinds for plic_workspace_bytes(). */
 enum {

@@ -434,27 +434,50 @@ __device__ __forceinline__ T offset_cell(T nx, T ny, T nz, T V0, int& bad) {
 }
 
 // ----------------------------------------------------------------------------
-// FP64 result from an FP32 solve: the method's FP32 solver on the inputs
-// rounded to float, then two Newton steps of polish() on the double problem.
-// The FP32 root is within ~1e-7 of the double root, so the first step lands
-// at ~1e-14 and the second at rounding level; the FP64 pipe runs ~50
-// operations per cell instead of a double-precision trigonometric solve.
+// FP64 result from an FP32 solve.  The symmetry reduction (Eqs. 2-8) is done
+// in FP64, so the reduced volume V = min(V0, 1 - V0) keeps its full relative
+// precision (V0 = 1 - 1e-9 rounded to float first would give V = 0); the
+// method's FP32 solver then runs on the reduced problem rounded to float, and
+// two Newton steps of polish() finish it on the FP64 problem.  The FP32 root is
+// within ~1e-7 relative of the FP64 root, so the first step lands at ~1e-14
+// and the second at rounding level; the FP64 pipe runs ~50 operations per
+// cell instead of a double-precision trigonometric solve.
 // ----------------------------------------------------------------------------
 template <int METHOD>
 __device__ __forceinline__ double offset_cell_refined(double nx, double ny, double nz, double V0,
                                                       int& bad) {
-    const float g = offset_cell<METHOD, float, true, false>((float)nx, (float)ny, (float)nz,
-                                                            (float)V0, bad);
     double n1, n2, n3;
     reduce_normal<double, false>(nx, ny, nz, n1, n2, n3);
-    const double L = n1 + n2 + n3;
+    const double L = fabs(nx) + fabs(ny) + fabs(nz);
     const bool ok = (V0 >= 0.0) && (V0 <= 1.0) && (L > 0.0) && (L <= 3.0);
-    if (!ok || g != g) return ok ? (double)g : (double)NAN;
+    if (!ok) {
+        bad += 1;
+        return (double)NAN;
+    }
+    const double V = reduce_volume<double, false>(V0);
+    const float Vf = (float)V;
+    double d;
+    if (METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT) {
+        const double il = 1.0 / L;
+        const float m1 = (float)(n1 * il), m3 = (float)(n3 * il);
+        const float m2 = Fm<float>::fdim_(1.0f, m1 + m3);
+        float a = METHOD == M_SZ_ORIG ? solve_sz_orig<float, false>(Vf, m1, m2, m3)
+                                      : solve_sz_opt<float, false>(Vf, m1, m2, m3);
+        a = polish<float>(a, Vf, m1, m2, m3);
+        d = (double)a * L;
+    } else {
+        const float f1 = (float)n1, f2 = (float)n2, f3 = (float)n3;
+        float e = METHOD == M_ANALYTIC ? solve_analytic<float, false>(Vf, f1, f2, f3)
+                : METHOD == M_NEWTON   ? solve_newton<float, false>(Vf, f1, f2, f3)
+                                       : solve_nested<float, false>(Vf, f1, f2, f3);
+        e = polish<float>(e, Vf, f1, f2, f3);
+        d = (double)e;
+    }
+    if (d != d) return d;                         // Kawano's NaN (axis normal, V0 in {0, 1})
     const double h = 0.5 * L;
-    const double V = V0 <= 0.5 ? V0 : 1.0 - V0;
-    double d = fmin(fmax(h - fabs((double)g), 0.0), h);
-    d = polish<double>(d, V, n1, n2, n3);
-    d = polish<double>(d, V, n1, n2, n3);
+    d = fmin(fmax(d, 0.0), h);
+    d = fmin(fmax(polish<double>(d, V, n1, n2, n3), 0.0), h);
+    d = fmin(fmax(polish<double>(d, V, n1, n2, n3), 0.0), h);
     return copysign(h - d, V0 - 0.5);
 }
 

@@ -22,7 +22,7 @@ template <int METHOD, int FIT>
 __global__ void __launch_bounds__(CO_THREADS)
 k_vof_curvature(const float* __restrict__ phi, int nx, int ny, const int32_t* __restrict__ idx,
                 int64_t n, const int64_t* __restrict__ d_n, float* __restrict__ kappa,
-                uint32_t flags) {
+                uint32_t flags, float scale) {
     __shared__ float smem[CO_WARPS][CO_BATCH * CO_VALS];
     int64_t lim = n;
     if (d_n) {
@@ -43,7 +43,7 @@ k_vof_curvature(const float* __restrict__ phi, int nx, int ny, const int32_t* __
             c.out = kappa + k;
             return c;
         };
-        co_warp_batch<METHOD, FIT>(fetch, flags, smem[warp]);
+        co_warp_batch<METHOD, FIT>(fetch, flags, scale, smem[warp]);
     }
 }
 
@@ -89,7 +89,7 @@ k_vof_curvature_batched(const vof_field* __restrict__ fields, const int64_t* __r
                 c.out = F.kappa + ks;
                 return c;
             };
-            co_warp_batch<METHOD, FIT>(fetch, flags, smem[warp]);
+            co_warp_batch<METHOD, FIT>(fetch, flags, 1.0f, smem[warp]);
         }
     }
 }
@@ -134,29 +134,50 @@ static const void* select(bool batched, plic_method m, int fit) {
 }
 
 static const uint32_t kCurvFlags = PLIC_FLAG_POINT_CENTROID | PLIC_FLAG_KAPPA_PAPER_SIGN |
-                                   PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64;
+                                   PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64 |
+                                   PLIC_FLAG_NORMAL_CM | PLIC_FLAG_NEIGHBOR_NORMAL;
+
+// vof_curvature and vof_laplace_pressure: out[k] = scale * kappa[k]
+static plic_status curvature_entry(const float* phi, int nx, int ny, int nz, const int32_t* idx,
+                                   int64_t n_iface, const int64_t* d_n_iface, float* out,
+                                   plic_method m, uint32_t flags, float scale, void* stream,
+                                   const char* who) {
+    if (nx < 3 || ny < 3 || nz < 3 || n_iface < 0) return PLIC_ERR_ARG;
+    if ((int)m < 0 || (int)m > 4 || (flags & ~kCurvFlags) || fit_mode(flags) < 0) return PLIC_ERR_ARG;
+    if (n_iface == 0) return PLIC_OK;
+    if (!phi || !idx || !out) return PLIC_ERR_ARG;
+    if (!aligned(phi, 4) || !aligned(idx, 4) || !aligned(out, 4) || (d_n_iface && !aligned(d_n_iface, 8)))
+        return PLIC_ERR_ALIGN;
+    if (flags & PLIC_FLAG_NEIGHBOR_NORMAL)
+        return launch_curvature_nn(phi, nx, ny, nz, idx, n_iface, d_n_iface, out, m, flags,
+                                   fit_mode(flags), scale, stream, who);
+    const void* k = select(false, m, fit_mode(flags));
+    const int threads = CO_THREADS;
+    // one warp per 32 entries, at most one resident wave
+    const int grid = stride_grid(k, threads, (n_iface + CO_BATCH - 1) / CO_BATCH * 32);
+    void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&idx, (void*)&n_iface,
+                    (void*)&d_n_iface, (void*)&out, (void*)&flags, (void*)&scale};
+    cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, as_stream(stream));
+    if (e != cudaSuccess) { set_last_error(who, e); return PLIC_ERR_CUDA; }
+    return PLIC_OK;
+}
 
 }  // namespace plic
 
 extern "C" plic_status vof_curvature(const float* phi, int nx, int ny, int nz, const int32_t* idx,
                                      int64_t n_iface, const int64_t* d_n_iface, float* kappa,
                                      plic_method m, uint32_t flags, void* stream) {
-    using namespace plic;
-    if (nx < 3 || ny < 3 || nz < 3 || n_iface < 0) return PLIC_ERR_ARG;
-    if ((int)m < 0 || (int)m > 4 || (flags & ~kCurvFlags) || fit_mode(flags) < 0) return PLIC_ERR_ARG;
-    if (n_iface == 0) return PLIC_OK;
-    if (!phi || !idx || !kappa) return PLIC_ERR_ARG;
-    if (!aligned(phi, 4) || !aligned(idx, 4) || !aligned(kappa, 4) || (d_n_iface && !aligned(d_n_iface, 8)))
-        return PLIC_ERR_ALIGN;
-    const void* k = select(false, m, fit_mode(flags));
-    const int threads = CO_THREADS;
-    // one warp per 32 entries, at most one resident wave
-    const int grid = stride_grid(k, threads, (n_iface + CO_BATCH - 1) / CO_BATCH * 32);
-    void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&idx, (void*)&n_iface,
-                    (void*)&d_n_iface, (void*)&kappa, (void*)&flags};
-    cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, as_stream(stream));
-    if (e != cudaSuccess) { set_last_error("vof_curvature", e); return PLIC_ERR_CUDA; }
-    return PLIC_OK;
+    return plic::curvature_entry(phi, nx, ny, nz, idx, n_iface, d_n_iface, kappa, m, flags, 1.0f,
+                                 stream, "vof_curvature");
+}
+
+extern "C" plic_status vof_laplace_pressure(const float* phi, int nx, int ny, int nz,
+                                            const int32_t* idx, int64_t n_iface,
+                                            const int64_t* d_n_iface, float sigma, float* dp,
+                                            plic_method m, uint32_t flags, void* stream) {
+    if (!(sigma == sigma)) return PLIC_ERR_ARG;
+    return plic::curvature_entry(phi, nx, ny, nz, idx, n_iface, d_n_iface, dp, m, flags,
+                                 2.0f * sigma, stream, "vof_laplace_pressure");
 }
 
 extern "C" plic_status vof_curvature_batched(const vof_field* fields, int n_fields,
@@ -166,6 +187,7 @@ extern "C" plic_status vof_curvature_batched(const vof_field* fields, int n_fiel
     using namespace plic;
     if (n_fields < 0 || (int)m < 0 || (int)m > 4 || (flags & ~kCurvFlags) || fit_mode(flags) < 0)
         return PLIC_ERR_ARG;
+    if (flags & PLIC_FLAG_NEIGHBOR_NORMAL) return PLIC_ERR_UNSUPPORTED;
     if (n_fields == 0) return PLIC_OK;
     if (!fields || !workspace) return PLIC_ERR_ARG;
     if (ws_bytes < plic_workspace_bytes(PLIC_WS_BATCHED, n_fields)) return PLIC_ERR_ARG;

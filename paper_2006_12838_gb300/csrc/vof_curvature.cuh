@@ -287,101 +287,40 @@ struct CellPlic<M_SZ_OPT> {
     }
 };
 
-struct CurvOut {
-    float kappa;
-    int dim, npts;
-};
-
-// Curvature of one interface cell.  `c` is its linear index; the caller
-// guarantees that all 26 neighbours are inside the field.
-template <int METHOD, int FIT>
-__device__ __forceinline__ CurvOut curvature_cell(const float* __restrict__ phi, int64_t c,
-                                                  int nx, int64_t nxy, uint32_t flags) {
-    CurvOut out{0.0f, 0, 0};
-    // 1-2: stencil and Parker-Youngs gradient (separable [1 2 1] weights)
+// Normal of the 3^3 stencil around cell c (Appendix B): Parker-Youngs
+// weights 4/2/1 (Eq. 38), or all 1 for the centre-of-mass normal.  Row by
+// row: the weights of the x-difference of row (dy, dz) are w(dy) w(dz) with
+// w(0) = 2, w(+-1) = 1; the row sums for the y and z components weigh the
+// middle entry 2 (all 1 for CM).  Returns false for a zero weighted sum.
+__device__ __forceinline__ bool stencil_normal(const float* __restrict__ phi, int64_t c, int nx,
+                                               int64_t nxy, bool cm, float& nx_, float& ny_,
+                                               float& nz_) {
     float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+    const float w0 = cm ? 1.0f : 2.0f;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             const float* row = phi + c + dz * nxy + (int64_t)dy * nx;
             const float a = __ldg(row - 1), b = __ldg(row), e = __ldg(row + 1);
-            const float wy = dy == 0 ? 2.0f : 1.0f, wz = dz == 0 ? 2.0f : 1.0f;
-            const float sum = a + 2.0f * b + e;
-            gx += wy * wz * (e - a);
-            gy += dy * wz * sum;
-            gz += dz * wy * sum;
+            const float wy = dy == 0 ? w0 : 1.0f, wz = dz == 0 ? w0 : 1.0f;
+            const float sum = fmaf(w0, b, a + e);
+            gx = fmaf(wy * wz, e - a, gx);
+            gy = fmaf((float)dy * wz, sum, gy);
+            gz = fmaf((float)dz * wy, sum, gz);
         }
-    // dy, dz weights for gy: [1 2 1] over x and z; for gz: over x and y
     const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
-    if (!(gl > 0.0f)) return out;
+    if (!(gl > 0.0f)) { nx_ = ny_ = nz_ = 0.0f; return false; }
     const float inv = -1.0f / gl;
-    const float nx_ = gx * inv, ny_ = gy * inv, nz_ = gz * inv;
-    // 3: frame
-    float rx = 0.56270900f, ry = 0.32704452f, rz = 0.75921047f;
-    float byx = ny_ * rz - nz_ * ry, byy = nz_ * rx - nx_ * rz, byz = nx_ * ry - ny_ * rx;
-    float bl = byx * byx + byy * byy + byz * byz;
-    if (!(bl > 1e-12f)) {
-        rx = 0.32704452f; ry = 0.75921047f; rz = 0.56270900f;
-        byx = ny_ * rz - nz_ * ry; byy = nz_ * rx - nx_ * rz; byz = nx_ * ry - ny_ * rx;
-        bl = byx * byx + byy * byy + byz * byz;
-    }
-    const float ib = rsqrtf(bl);
-    byx *= ib; byy *= ib; byz *= ib;
-    const float bxx = byy * nz_ - byz * ny_, bxy = byz * nx_ - byx * nz_, bxz = byx * ny_ - byy * nx_;
-    // 4: PLIC offsets with the centre normal
-    CellPlic<METHOD> pl;
-    pl.prepare(nx_, ny_, nz_);
-    const float phi0 = __ldg(phi + c);
-    const float d00 = pl.offset(phi0);
-    const bool centroid = (flags & PLIC_FLAG_POINT_CENTROID) != 0;
-    float c0x = 0.0f, c0y = 0.0f, c0z = 0.0f;
-    if (centroid) {
-        float A;
-        cut_polygon<float>(nx_, ny_, nz_, d00, A, c0x, c0y, c0z);
-    }
-    // 5: normal equations
-    float M[15], bv[5];
-#pragma unroll
-    for (int k = 0; k < 15; ++k) M[k] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) bv[k] = 0.0f;
-    int m = 0;
-#pragma unroll 1
-    for (int i = 1; i < 27; ++i) {
-        int ex, ey, ez;
-        e_of(i, ex, ey, ez);
-        const float v = __ldg(phi + c + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
-        if (!(v > 0.0f && v < 1.0f)) continue;
-        const float d0i = pl.offset(v);
-        float qx = (float)ex, qy = (float)ey, qz = (float)ez, z;
-        if (centroid) {
-            float A, cx, cy, cz;
-            cut_polygon<float>(nx_, ny_, nz_, d0i, A, cx, cy, cz);
-            qx += cx - c0x; qy += cy - c0y; qz += cz - c0z;
-            z = qx * nx_ + qy * ny_ + qz * nz_;
-        } else {
-            z = qx * nx_ + qy * ny_ + qz * nz_ + (d0i - d00);
-        }
-        const float x = qx * bxx + qy * bxy + qz * bxz;
-        const float y = qx * byx + qy * byy + qz * byz;
-        const float Q[5] = {x * x, y * y, x * y, x, y};
-#pragma unroll
-        for (int a = 0; a < 5; ++a) {
-#pragma unroll
-            for (int b = a; b < 5; ++b) M[uidx(a, b)] = fmaf(Q[a], Q[b], M[uidx(a, b)]);
-            bv[a] = fmaf(z, Q[a], bv[a]);
-        }
-        ++m;
-    }
-    out.npts = m;
-    // 6-7: solve and Eq. 42
-    float xs[5];
-    out.dim = fit_solve<FIT>(M, bv, m, xs);
-    if (out.dim == 0) return out;
-    const float k = paraboloid_kappa(xs);
-    out.kappa = (flags & PLIC_FLAG_KAPPA_PAPER_SIGN) ? k : -k;
-    return out;
+    nx_ = gx * inv; ny_ = gy * inv; nz_ = gz * inv;
+    return true;
 }
+
+// The neighbour-normal variant (PLIC_FLAG_NEIGHBOR_NORMAL), one thread per
+// list entry; defined in vof_curvature_nn.cu.  out[k] = scale * kappa[k].
+plic_status launch_curvature_nn(const float* phi, int nx, int ny, int nz, const int32_t* idx,
+                                int64_t n_iface, const int64_t* d_n_iface, float* out,
+                                plic_method m, uint32_t flags, int fit, float scale,
+                                void* stream, const char* who);
 
 }  // namespace plic

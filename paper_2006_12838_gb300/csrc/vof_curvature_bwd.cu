@@ -47,6 +47,7 @@ k_vof_curvature_vjp(const float* __restrict__ phi, int nx, int ny,
         lim = dn < n ? dn : n;
     }
     const int t = threadIdx.x;
+    const bool cm = (flags & PLIC_FLAG_NORMAL_CM) != 0;
     const int64_t nxy = (int64_t)nx * ny;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + t; k < lim;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -62,8 +63,8 @@ k_vof_curvature_vjp(const float* __restrict__ phi, int nx, int ny,
             for (int dy = -1; dy <= 1; ++dy) {
                 const float* row = phi + c + dz * nxy + (int64_t)dy * nx;
                 const float a = __ldg(row - 1), b = __ldg(row), e = __ldg(row + 1);
-                const float wy = dy == 0 ? 2.0f : 1.0f, wz = dz == 0 ? 2.0f : 1.0f;
-                const float sum = a + 2.0f * b + e;
+                const float wy = (dy == 0 && !cm) ? 2.0f : 1.0f, wz = (dz == 0 && !cm) ? 2.0f : 1.0f;
+                const float sum = a + (cm ? 1.0f : 2.0f) * b + e;
                 gx += wy * wz * (e - a);
                 gy += dy * wz * sum;
                 gz += dz * wy * sum;
@@ -209,7 +210,7 @@ k_vof_curvature_vjp(const float* __restrict__ phi, int nx, int ny,
                 int ex, ey, ez;
                 e_of(i, ex, ey, ez);
                 const int e2 = ex * ex + ey * ey + ez * ez;
-                const float wi = e2 == 1 ? 4.0f : (e2 == 2 ? 2.0f : 1.0f);
+                const float wi = cm ? 1.0f : (e2 == 1 ? 4.0f : (e2 == 2 ? 2.0f : 1.0f));
                 s_g[i][t] += wi * (ex * gbx + ey * gby + ez * gbz);
             }
         }
@@ -287,10 +288,11 @@ extern "C" plic_status vof_curvature_backward(const float* phi, int nx, int ny, 
     if (nx < 3 || ny < 3 || nz < 3 || n_iface < 0) return PLIC_ERR_ARG;
     if ((int)m < 0 || (int)m > 4) return PLIC_ERR_ARG;
     const uint32_t known = PLIC_FLAG_POINT_CENTROID | PLIC_FLAG_KAPPA_PAPER_SIGN |
-                           PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64;
+                           PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64 |
+                           PLIC_FLAG_NORMAL_CM | PLIC_FLAG_NEIGHBOR_NORMAL;
     const uint32_t fitf = flags & (PLIC_FLAG_FIT_FP32 | PLIC_FLAG_FIT_DF32 | PLIC_FLAG_FIT_FP64);
     if ((flags & ~known) || (fitf & (fitf - 1u))) return PLIC_ERR_ARG;
-    if (flags & PLIC_FLAG_POINT_CENTROID) return PLIC_ERR_UNSUPPORTED;
+    if (flags & (PLIC_FLAG_POINT_CENTROID | PLIC_FLAG_NEIGHBOR_NORMAL)) return PLIC_ERR_UNSUPPORTED;
     const int64_t cells = (int64_t)nx * ny * nz;
     if (cells > 2147483647LL) return PLIC_ERR_ARG;
     if (!phi || !g_phi || (n_iface > 0 && (!idx || !g_kappa)) || !workspace) return PLIC_ERR_ARG;

@@ -100,7 +100,9 @@ template <int METHOD>
 __device__ __forceinline__ void co_group_cell(const CoCell& cell, int g, uint32_t flags,
                                               float* rec) {
     const bool on = cell.valid;
-    // 1. stencil entries i = g, g+8, g+16, g+24 (i < 27) and the PY partial sums
+    const bool cm = (flags & PLIC_FLAG_NORMAL_CM) != 0;
+    // 1. stencil entries i = g, g+8, g+16, g+24 (i < 27) and the PY (or CM)
+    //    partial sums
     float gx = 0.0f, gy = 0.0f, gz = 0.0f;
     unsigned mask = 0u;
     float phi0 = 0.0f;
@@ -112,7 +114,7 @@ __device__ __forceinline__ void co_group_cell(const CoCell& cell, int g, uint32_
             e_of(i, ex, ey, ez);
             const float v = __ldg(cell.phi + cell.c + ex + (int64_t)ey * cell.nx + (int64_t)ez * cell.nxy);
             const int e2 = ex * ex + ey * ey + ez * ez;
-            const float w = e2 == 1 ? 4.0f : (e2 == 2 ? 2.0f : 1.0f);
+            const float w = cm ? 1.0f : (e2 == 1 ? 4.0f : (e2 == 2 ? 2.0f : 1.0f));
             gx = fmaf(w * ex, v, gx);
             gy = fmaf(w * ey, v, gy);
             gz = fmaf(w * ez, v, gz);
@@ -248,9 +250,11 @@ __device__ __forceinline__ float co_solve(const float* rec, uint32_t flags) {
 
 // One warp batch: `fetch(slot)` gives the CoCell of batch slot 0..31 (with
 // valid == false past the end).  `smem` holds CO_BATCH * CO_VALS floats for
-// this warp.
+// this warp.  The stored value is scale * kappa (scale = 1 for the curvature
+// itself, 2 sigma for the Young-Laplace pressure).
 template <int METHOD, int FIT, typename Fetch>
-__device__ __forceinline__ void co_warp_batch(Fetch fetch, uint32_t flags, float* smem) {
+__device__ __forceinline__ void co_warp_batch(Fetch fetch, uint32_t flags, float scale,
+                                              float* smem) {
     const int lane = threadIdx.x & 31;
     const int g = lane & 7, grp = lane >> 3;
 #pragma unroll 1
@@ -261,7 +265,7 @@ __device__ __forceinline__ void co_warp_batch(Fetch fetch, uint32_t flags, float
     }
     __syncwarp();
     const CoCell mine = fetch(lane);
-    if (mine.valid) *mine.out = co_solve<FIT>(smem + lane * CO_VALS, flags);
+    if (mine.valid) *mine.out = scale * co_solve<FIT>(smem + lane * CO_VALS, flags);
     __syncwarp();
 }
 

@@ -24,6 +24,8 @@ FLAG_KAPPA_PAPER_SIGN = 4
 FLAG_FIT_FP32 = 8
 FLAG_FIT_DF32 = 16
 FLAG_FIT_FP64 = 32
+FLAG_NORMAL_CM = 64
+FLAG_NEIGHBOR_NORMAL = 128
 WS_COMPACT = 0
 WS_BATCHED = 2
 
@@ -71,9 +73,13 @@ def load():
             "vof_interface_compact": [P, I32, I32, I32, P, I64, P, P, SZ, P],
             "vof_interface_compact_noalloc": [P, I32, I32, I32, P, I64, P, P],
             "vof_curvature": [P, I32, I32, I32, P, I64, P, P, I32, U32, P],
+            "vof_laplace_pressure": [P, I32, I32, I32, P, I64, P, ctypes.c_float, P, I32, U32, P],
+            "vof_normal": [P, I32, I32, I32, P, I64, P, P, P, P, U32, P],
             "vof_curvature_backward": [P, I32, I32, I32, P, I64, P, P, P, I32, U32, P, SZ, P],
             "vof_curvature_batched": [P, I32, P, I32, U32, P, SZ, P],
             "plic_paper_benchmark": [P, P, P, I64, I32, I32, I32, I32, P, P],
+            "plic_sphere_volume": [P, P, I64, I32, P],
+            "plic_sphere_offset": [P, P, I64, I32, P],
         }
         for name, args in sigs.items():
             f = getattr(L, name, None)
@@ -234,6 +240,38 @@ def curvature(phi, idx, n_iface=None, count=None, kappa=None, method="sz_opt", f
     return kappa[:n] if n_iface is not None or kappa.numel() != n else kappa
 
 
+def laplace_pressure(phi, idx, sigma, n_iface=None, count=None, dp=None, method="sz_opt",
+                     flags=0, stream=None):
+    """Young-Laplace pressure jump dp = 2 sigma kappa per interface cell (Sec. 4.1)."""
+    _cuda(phi, dtype=torch.float32)
+    _cuda(phi, idx, dtype=None)
+    nz, ny, nx = phi.shape
+    n = idx.numel() if n_iface is None else int(n_iface)
+    if dp is None:
+        dp = torch.empty(max(n, 1), dtype=torch.float32, device=phi.device)
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    _check(load().vof_laplace_pressure(_ptr(phi), nx, ny, nz, _ptr(idx), n, _ptr(count),
+                                       float(sigma), _ptr(dp), m, flags, _stream(phi, stream)),
+           "vof_laplace_pressure")
+    return dp[:n] if n_iface is not None or dp.numel() != n else dp
+
+
+def normals(phi, idx, n_iface=None, count=None, out=None, flags=0, stream=None):
+    """Interface normals (Appendix B: Parker-Youngs, or CM with FLAG_NORMAL_CM),
+    returned as a (3, n) float tensor (rows n_x, n_y, n_z)."""
+    _cuda(phi, dtype=torch.float32)
+    _cuda(phi, idx, dtype=None)
+    nz, ny, nx = phi.shape
+    n = idx.numel() if n_iface is None else int(n_iface)
+    if out is None:
+        out = torch.empty((3, max(n, 1)), dtype=torch.float32, device=phi.device)
+    _cuda(phi, out, dtype=None)
+    _check(load().vof_normal(_ptr(phi), nx, ny, nz, _ptr(idx), n, _ptr(count), _ptr(out[0]),
+                             _ptr(out[1]), _ptr(out[2]), flags, _stream(phi, stream)),
+           "vof_normal")
+    return out[:, :n]
+
+
 def curvature_backward(phi, idx, g_kappa, n_iface=None, count=None, g_phi=None,
                        method="sz_opt", flags=0, workspace=None, stream=None):
     """g_phi = d(sum g_kappa * kappa)/d phi (dense, same shape as phi)."""
@@ -293,3 +331,25 @@ def paper_benchmark(nx, ny, nz, L=256, method="sz_opt", precision=None, blank=Fa
                                        1 if blank else 0, _ptr(err_sum), _stream(nx, stream)),
            "plic_paper_benchmark")
     return err_sum
+
+
+def sphere_volume(d0, precision=None, out=None, stream=None):
+    """Sec. 3: cap volume of the unit-volume ball below a plane at distance d0."""
+    _cuda(d0, out, dtype=d0.dtype)
+    p = _prec(d0.dtype, precision)
+    if out is None:
+        out = torch.empty_like(d0)
+    _check(load().plic_sphere_volume(_ptr(d0), _ptr(out), d0.numel(), p, _stream(d0, stream)),
+           "plic_sphere_volume")
+    return out
+
+
+def sphere_offset(V0, precision=None, out=None, stream=None):
+    """Sec. 3: plane distance d0 that cuts volume V0 off the unit-volume ball."""
+    _cuda(V0, out, dtype=V0.dtype)
+    p = _prec(V0.dtype, precision)
+    if out is None:
+        out = torch.empty_like(V0)
+    _check(load().plic_sphere_offset(_ptr(V0), _ptr(out), V0.numel(), p, _stream(V0, stream)),
+           "plic_sphere_offset")
+    return out

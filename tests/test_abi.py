@@ -90,6 +90,18 @@ def test_host_side_argument_checks(lib):
     f = (plic.VofField * 1)()
     assert lib.vof_curvature_batched(ctypes.cast(f, P), 1, ctypes.cast(ctypes.pointer(tun), P), 2, 0,
                                      ok, 1 << 20, None) == ERR_ARG
+    # plane-sphere: bad n, precision, null, misaligned; empty is a no-op
+    assert lib.plic_sphere_offset(ok, ok, -1, 0, None) == ERR_ARG
+    assert lib.plic_sphere_offset(ok, ok, 10, 4, None) == ERR_ARG
+    assert lib.plic_sphere_volume(None, ok, 10, 0, None) == ERR_ARG
+    assert lib.plic_sphere_volume(ok, P(258), 10, 0, None) == ERR_ALIGN
+    assert lib.plic_sphere_offset(P(260), ok, 10, 2, None) == ERR_ALIGN
+    assert lib.plic_sphere_offset(None, None, 0, 0, None) == 0
+    # paper harness: L < 2, bad precision, null accumulator
+    assert lib.plic_paper_benchmark(ok, ok, ok, 10, 1, 2, 1, 0, ok, None) == ERR_ARG
+    assert lib.plic_paper_benchmark(ok, ok, ok, 10, 256, 2, 3, 0, ok, None) == ERR_ARG
+    assert lib.plic_paper_benchmark(ok, ok, ok, 10, 256, 2, 1, 0, None, None) == ERR_ARG
+    assert lib.plic_paper_benchmark(ok, ok, ok, 10, 256, 2, 1, 0, P(260), None) == ERR_ALIGN
 
 
 def test_binding_refuses_cpu_tensors(lib):

@@ -1,0 +1,145 @@
+"""GPU parity of the curvature-step variants against the oracle.
+
+- vof_normal: Parker-Youngs (Eq. 38) and centre-of-mass (Appendix B) normals,
+  |n - n_ref| <= 2e-6 per component.
+- Normal accuracy on exactly sub-sampled spheres (Appendix B cites ~4 degrees
+  for CM and ~1 degree for PY): the mean angle to the exact radial direction
+  is reported, and PY must beat CM.
+- vof_curvature with the CM normal and with the neighbour-normal variant
+  (Sec. 4.2), both point modes: |kappa - kappa_ref| <= 1e-4 max(|kappa_ref|,
+  1/64) on cells with a full fit (as the default curvature).
+- vof_laplace_pressure = 2 sigma kappa, bit for bit.
+- The curvature adjoint with the CM normal against oracle finite differences.
+- Unsupported combinations return PLIC_ERR_UNSUPPORTED.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2006_12838_gb300 import plic, synth  # noqa: E402
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_12838_gb300 import build
+    build.build()
+    plic.load()
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def field(orc):
+    phi, _ = synth.curvature_field(seed=3, edge=96, n_spheres=5, rmin=6, rmax=20)
+    p = phi.numpy()
+    return p, orc.interface_cells(p)
+
+
+def _rel(kappa, kref, dim, label, tol=TOL):
+    full = dim == 5
+    rel = np.abs(kappa - kref) / np.maximum(np.abs(kref), 1 / 64)
+    print("%s: cells %d, reduced-fit %d, max rel %.3e, p99.9 %.3e" % (
+        label, kappa.size, (~full).sum(), rel[full].max(), np.percentile(rel[full], 99.9)))
+    assert rel[full].max() <= tol, label
+
+
+@pytest.mark.parametrize("flags", [0, 64])
+def test_normals_match_oracle(dev, orc, field, flags):
+    p, idx = field
+    phid = torch.tensor(p, device=dev)
+    it = torch.tensor(idx, device=dev)
+    n = plic.normals(phid, it, flags=flags).cpu().numpy().astype(np.float64)
+    ref = orc.normals(p, idx, flags)
+    err = np.abs(n - ref).max()
+    print("normal flags %d: max |dn| %.3e" % (flags, err))
+    assert err <= 2e-6
+
+
+def test_normal_accuracy_on_spheres(dev, orc):
+    res = {}
+    for R in (6.0, 10.0, 20.0):
+        e = int(2 * R + 8)
+        c = (e / 2 + 0.21, e / 2 - 0.37, e / 2 + 0.11)
+        p = synth.fill_spheres((e, e, e), [(c[0], c[1], c[2], R)]).numpy()
+        idx = orc.interface_cells(p)
+        x, y, z = idx % e, (idx // e) % e, idx // (e * e)
+        # cell centres at integer coordinates; exact normal: outward radial
+        r = np.stack([x - c[0], y - c[1], z - c[2]]).astype(np.float64)
+        r /= np.linalg.norm(r, axis=0)
+        phid = torch.tensor(p, device=dev)
+        it = torch.tensor(idx, device=dev)
+        for flags, name in ((0, "PY"), (64, "CM")):
+            n = plic.normals(phid, it, flags=flags).cpu().numpy().astype(np.float64)
+            ang = np.degrees(np.arccos(np.clip((n * r).sum(0), -1, 1)))
+            res[(R, name)] = ang.mean()
+        print("R=%g mean angle error: PY %.2f deg, CM %.2f deg" % (R, res[(R, "PY")], res[(R, "CM")]))
+        assert res[(R, "PY")] < res[(R, "CM")]
+
+
+@pytest.mark.parametrize("flags", [64, 64 | 2, 128, 128 | 2, 128 | 64, 128 | 32, 128 | 8])
+def test_curvature_variants(dev, orc, field, flags):
+    p, idx = field
+    phid = torch.tensor(p, device=dev)
+    it = torch.tensor(idx, device=dev)
+    oflags = flags & (2 | 64 | 128)
+    kref, dim, _ = orc.curvature(p, idx, oflags)
+    k = plic.curvature(phid, it, flags=flags).cpu().numpy().astype(np.float64)
+    tol = 1e-3 if flags & 8 else TOL
+    _rel(k, kref, dim, "variant flags %d" % flags, tol)
+
+
+@pytest.mark.parametrize("method", list(plic.METHODS))
+def test_neighbour_normal_methods(dev, orc, field, method):
+    p, idx = field
+    phid = torch.tensor(p, device=dev)
+    it = torch.tensor(idx, device=dev)
+    kref, dim, _ = orc.curvature(p, idx, 128)
+    k = plic.curvature(phid, it, method=method, flags=128).cpu().numpy().astype(np.float64)
+    _rel(k, kref, dim, "neighbour normals %s" % method)
+
+
+def test_laplace_pressure_is_two_sigma_kappa(dev, field):
+    p, idx = field
+    phid = torch.tensor(p, device=dev)
+    it = torch.tensor(idx, device=dev)
+    for flags in (0, 128):
+        k = plic.curvature(phid, it, flags=flags)
+        for sigma in (1e-3, 0.0728, 3.0):
+            dp = plic.laplace_pressure(phid, it, sigma, flags=flags)
+            want = k * torch.tensor(2 * sigma, dtype=torch.float32, device=dev)
+            assert torch.equal(dp, want)
+
+
+def test_adjoint_with_cm_normal(dev, orc):
+    phi = synth.fill_spheres((28, 30, 26), [(13.2, 14.9, 12.4, 8.7)]).numpy()
+    rng = np.random.default_rng(91)
+    iface = (phi > 0) & (phi < 1)
+    phi[iface] = np.clip(phi[iface] + 1e-3 * rng.standard_normal(iface.sum()), 0.01, 0.99)
+    idx = orc.interface_cells(phi)
+    w = rng.standard_normal(idx.size)
+    g_ref = orc.curvature_grad_fd(phi, idx, w, 1e-6, 64)
+    phid = torch.tensor(phi, device=dev)
+    g = plic.curvature_backward(phid, torch.tensor(idx, device=dev),
+                                torch.tensor(w, dtype=torch.float32, device=dev),
+                                flags=64 | 32).cpu().numpy().astype(np.float64)
+    scale = np.abs(g_ref).max()
+    err = np.abs(g - g_ref)
+    print("CM adjoint: global rel %.3e, p99.9 %.3e" % (err.max() / scale,
+                                                      np.percentile(err, 99.9) / scale))
+    assert err.max() <= 1e-3 * scale
+
+
+def test_unsupported_combinations(dev, field):
+    p, idx = field
+    phid = torch.tensor(p, device=dev)
+    it = torch.tensor(idx, device=dev)
+    with pytest.raises(plic.PlicError):
+        plic.curvature_backward(phid, it, torch.ones(idx.size, device=dev), flags=128)
+    kap = torch.empty(idx.size, device=dev)
+    with pytest.raises(plic.PlicError):
+        plic.curvature_batched([(phid, it, idx.size, kap)], flags=128)
