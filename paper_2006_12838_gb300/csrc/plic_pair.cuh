@@ -36,10 +36,11 @@ __device__ __forceinline__ f2 sqrt_(f2 a) {
 }
 
 // cube root of x >= 0: MUFU exp2(log2(x)/3) and one Newton step (see
-// Fm<float>).  x is floored at 1e-30 (whose cube root, 1e-10, is far below the
-// FP32 resolution of an offset), which removes the zero/denormal branches.
+// Fm<float>).  1e-30 is added to x (its cube root, 1e-10, is far below the
+// FP32 resolution of an offset), which removes the zero/denormal branches;
+// the add runs on the paired FMA pipe where a max would take the ALU pipe.
 __device__ __forceinline__ f2 cbrt_(f2 x) {
-    x = make_float2(fmaxf(x.x, 1e-30f), fmaxf(x.y, 1e-30f));
+    x = add(x, mk(1e-30f));
     f2 r = make_float2(Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.x) * (1.0f / 3.0f)),
                        Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.y) * (1.0f / 3.0f)));
     const f2 r2 = mul(r, r);
@@ -48,9 +49,13 @@ __device__ __forceinline__ f2 cbrt_(f2 x) {
     return fma(make_float2(-res.x, -res.y), inv, r);
 }
 
-// sqrt of x >= 0 as x rsqrt(x), x floored at 1e-30 (no zero branch)
+// sqrt of x >= 0 as x rsqrt(x) with 1e-30 added (no zero branch).  Both
+// callers pass arguments that are >= 0 wherever the result is used: the
+// arcsine's 1/2 (1 - a) with a <= 1, and the case-(2) radicand
+// 8 n2 n3 V - n1^2/3, which is >= n1^2 in case (2) and exactly 8 n2 n3 V >= 0
+// for n1 = 0.
 __device__ __forceinline__ f2 sqrtp(f2 x) {
-    x = make_float2(fmaxf(x.x, 1e-30f), fmaxf(x.y, 1e-30f));
+    x = add(x, mk(1e-30f));
     return mul(x, rsqrt(x));
 }
 
@@ -75,19 +80,33 @@ __device__ __forceinline__ f2 asin01(f2 a) {
     return sel(big, fma(mk(-2.0f), p, mk(1.5707963267948966f)), p);
 }
 
+// One Newton step on the cubic of Eq. 10 for cases (3)/(4) (d >= n2, n1 > 0):
+// g = 3 d (d - n1) + n1^2 - ((d - n2)^3 + (d - n3)_+^3)/n1 - 6 n2 n3 V,
+// g' = 6 d - 3 n1 - 3 ((d - n2)^2 + (d - n3)_+^2)/n1 = 12 n2 n3 x area > 0.
+__device__ __forceinline__ f2 polish34(f2 d, f2 V, f2 n1, f2 n2, f2 n3) {
+    const f2 e2 = sub(d, n2), e3 = fmax0(sub(d, n3));
+    const f2 inv1 = rcp(n1);
+    const f2 e22 = mul(e2, e2), e33 = mul(e3, e3);
+    const f2 cub = fma(e22, e2, mul(e33, e3));
+    const f2 dd = sub(d, n1);
+    f2 g = fma(mk(3.0f), mul(d, dd), mul(n1, n1));
+    g = fma(make_float2(-cub.x, -cub.y), inv1, g);
+    g = fma(mk(-6.0f), mul(mul(n2, n3), V), g);
+    f2 gp = fma(mk(6.0f), d, mul(mk(-3.0f), n1));
+    gp = fma(mk(-3.0f), mul(add(e22, e33), inv1), gp);
+    return sub(d, mul(g, rcp(gp)));
+}
+
 // Reduced optimised-SZ solution for two cells (L1-normalised m1 <= m2 <= m3,
-// reduced volume V); returns the reduced offsets and whether the trigonometric
-// root was taken.
-__device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3, b2& trig) {
+// reduced volume V).  The trigonometric root of cases (3)/(4) is formed (and,
+// with POLISH, given its Newton step) first; the closed forms of cases (2),
+// (1) and (5) then replace it, each select right after its test, so that no
+// case flag stays live across the long trigonometric chain.
+template <bool POLISH>
+__device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3) {
     const f2 n12 = add(n1, n2), n3V = mul(n3, V);
     const f2 n3V2 = add(n3V, n3V);
     const f2 V6n2n3 = mul(mul(mk(6.0f), n2), n3V), sqn1 = mul(n1, n1);
-    const b2 c5 = le(n12, n3V2);
-    const b2 c1 = lt(V6n2n3, sqn1);
-    // case (2) upper test 3 n2 (2 n3 V + n1 - n2) < n1^2
-    const f2 t2a = mul(mul(mk(3.0f), n2), add(n3V2, sub(n1, n2)));
-    const b2 c2u = lt(t2a, sqn1);
-    const b2 c2 = {!c1.x && c2u.x, !c1.y && c2u.y};
     const f2 n1n2 = mul(n1, n2);
     // case (3) vs (4): 6 n1 n2 n3 V < n3^2 (3 n12 - n3) + n1^2 (n1 - 3 n3) + n2^2 (n2 - 3 n3)
     f2 num3 = mul(mul(n3, n3), fma(mk(3.0f), n12, make_float2(-n3.x, -n3.y)));
@@ -111,32 +130,18 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3, b2& trig) {
     arg = make_float2(fminf(arg.x, 1.0f), fminf(arg.y, 1.0f));
     const f2 th = mul(mk(0.33333333333333333f), asin01(arg));
     const f2 sn = make_float2(__sinf(th.x), __sinf(th.y));
-    const f2 d34 = fma(mul(mk(-2.0f), t), sn, c);
-    // closed forms
-    const f2 d5 = fma(mk(0.5f), n12, n3V);
+    f2 d = fma(mul(mk(-2.0f), t), sn, c);
+    if (POLISH) d = polish34(d, V, n1, n2, n3);
+    // case (2) where 3 n2 (2 n3 V + n1 - n2) < n1^2, unless case (1) holds
+    const f2 t2a = mul(mul(mk(3.0f), n2), add(n3V2, sub(n1, n2)));
     const f2 d2 = mul(mk(0.5f), add(n1, sqrtp(fma(mk(8.0f), mul(n2, n3V), mul(mk(-0.33333333333333333f), sqn1)))));
+    d = sel(lt(t2a, sqn1), d2, d);
+    // case (1) where 6 n2 n3 V < n1^2
     const f2 d1 = cbrt_(mul(V6n2n3, n1));
-    trig = {!c5.x && !c2.x && !c1.x, !c5.y && !c2.y && !c1.y};
-    f2 d = sel(c1, d1, d34);
-    d = sel(c2, d2, d);
-    return sel(c5, d5, d);
-}
-
-// One Newton step on the cubic of Eq. 10 for cases (3)/(4) (d >= n2, n1 > 0):
-// g = 3 d (d - n1) + n1^2 - ((d - n2)^3 + (d - n3)_+^3)/n1 - 6 n2 n3 V,
-// g' = 6 d - 3 n1 - 3 ((d - n2)^2 + (d - n3)_+^2)/n1 = 12 n2 n3 x area > 0.
-__device__ __forceinline__ f2 polish34(f2 d, f2 V, f2 n1, f2 n2, f2 n3) {
-    const f2 e2 = sub(d, n2), e3 = fmax0(sub(d, n3));
-    const f2 inv1 = rcp(n1);
-    const f2 e22 = mul(e2, e2), e33 = mul(e3, e3);
-    const f2 cub = fma(e22, e2, mul(e33, e3));
-    const f2 dd = sub(d, n1);
-    f2 g = fma(mk(3.0f), mul(d, dd), mul(n1, n1));
-    g = fma(make_float2(-cub.x, -cub.y), inv1, g);
-    g = fma(mk(-6.0f), mul(mul(n2, n3), V), g);
-    f2 gp = fma(mk(6.0f), d, mul(mk(-3.0f), n1));
-    gp = fma(mk(-3.0f), mul(add(e22, e33), inv1), gp);
-    return sub(d, mul(g, rcp(gp)));
+    d = sel(lt(V6n2n3, sqn1), d1, d);
+    // case (5) where n1 + n2 <= 2 n3 V
+    const f2 d5 = fma(mk(0.5f), n12, n3V);
+    return sel(le(n12, n3V2), d5, d);
 }
 
 // Whole cells: two (n, V0) -> d0 by the optimised SZ solution in FP32.
@@ -150,19 +155,15 @@ __device__ __forceinline__ f2 offset_sz_opt(f2 nx, f2 ny, f2 nz, f2 V0, int& bad
     const f2 L = add(add(ax, ay), az);
     // V = min(V0, 1 - V0) equals the exact reduction of Eq. 5 on [0, 1], and is
     // negative or NaN exactly when V0 is outside [0, 1] or NaN
-    const f2 V = make_float2(fminf(V0.x, 1.0f - V0.x), fminf(V0.y, 1.0f - V0.y));
+    const f2 W = sub(mk(1.0f), V0);
+    const f2 V = make_float2(fminf(V0.x, W.x), fminf(V0.y, W.y));
     const bool okx = V.x >= 0.0f && L.x > 0.0f && L.x <= 3.0f;
     const bool oky = V.y >= 0.0f && L.y > 0.0f && L.y <= 3.0f;
     bad += (int)!okx + (int)!oky;
     const f2 il = rcp(L);
     const f2 m1 = mul(n1, il), m3 = mul(n3, il);
     const f2 m2 = fmax0(sub(mk(1.0f), add(m1, m3)));
-    b2 trig;
-    f2 a = sz_opt(V, m1, m2, m3, trig);
-    if (POLISH) {
-        const f2 ap = polish34(a, V, m1, m2, m3);
-        a = sel(trig, ap, a);
-    }
+    const f2 a = sz_opt<POLISH>(V, m1, m2, m3);
     const f2 h = sub(mk(0.5f), a);
     f2 r = mul(L, make_float2(copysignf(h.x, V0.x - 0.5f), copysignf(h.y, V0.y - 0.5f)));
     if (!okx) r.x = __int_as_float(0x7fffffff);

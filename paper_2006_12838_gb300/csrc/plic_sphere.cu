@@ -9,8 +9,9 @@
 // because pi r^3 = 3/4.  The inverse is solved per cell without
 // trigonometric functions: u0 = s p(s), s = sqrt(W), a degree-4 least-squares
 // polynomial (|u0 - u| < 2.2e-4 on [0, 1/2]), then two Newton steps on
-// u^2 (3 - u) = 4W in FP32 (|u - u*| < 1e-7).  FP64 continues from the FP32
-// root with two Newton steps whose residual is evaluated in FP64 and whose
+// u^2 (3 - u) = 4W in FP32 with the MUFU reciprocal (|u - u*| < 1e-7).  FP64
+// continues from the FP32 root with two Newton steps whose residual is
+// evaluated in FP64 and whose
 // derivative is the FP32 reciprocal: each step multiplies the error by about
 // 1e-7, so the result is within a few ulp.  The paper's closed form (an arc
 // tangent and a sine) is the reference the oracle is pinned to; this kernel
@@ -19,6 +20,7 @@
 // Data: one array in, one out (SoA streams of float or double), 16-byte
 // vectors in a one-wave grid-stride loop; 8 (FP32) or 16 (FP64) bytes per cell.
 #include "host_common.h"
+#include "plic_math.cuh"
 
 namespace plic {
 namespace sphere {
@@ -35,7 +37,7 @@ __device__ __forceinline__ float cap_u_f32(float W) {
     for (int it = 0; it < 2; ++it) {
         const float f = fmaf(u * u, 3.0f - u, -W4);
         const float fp = 3.0f * u * (2.0f - u);
-        u = fp > 0.0f ? u - f * __frcp_rn(fp) : u;
+        u = fp > 0.0f ? u - f * Fm<float>::rcp_(fp) : u;
     }
     return u;
 }
@@ -58,7 +60,7 @@ template <> __device__ __forceinline__ double offset_cell<double>(double V0) {
     for (int it = 0; it < 2; ++it) {
         const double f = fma(u * u, 3.0 - u, -W4);
         const float fp = (float)(3.0 * u * (2.0 - u));
-        u = fp > 0.0f ? u - f * (double)__frcp_rn(fp) : u;
+        u = fp > 0.0f ? u - f * (double)Fm<float>::rcp_(fp) : u;
     }
     const double d = fma(R, u, -R);
     const double out = V0 <= 0.5 ? d : -d;

@@ -74,11 +74,41 @@ __device__ __forceinline__ int row_bits(const float* __restrict__ row, int nx, b
     return __reduce_add_sync(0xffffffffu, cnt);
 }
 
+// Vector path helpers: the 4-bit interface mask of the float4 at column x of
+// a row (boundary columns cleared), and the gather of the nibbles of 8 lanes
+// into the row's 32-bit word (x0 / 32 + lane / 8), stored by `fn`.
+__device__ __forceinline__ unsigned nib4(float4 v, int x, int nx) {
+    unsigned m = (unsigned)iface(v.x) | ((unsigned)iface(v.y) << 1) |
+                 ((unsigned)iface(v.z) << 2) | ((unsigned)iface(v.w) << 3);
+    if (x == 0) m &= ~1u;
+    if (x + 3 == nx - 1) m &= ~8u;
+    return x < nx ? m : 0u;
+}
+
+template <typename F>
+__device__ __forceinline__ void emit_nibbles(unsigned m, int x0, int nx, F fn) {
+    const int lane = threadIdx.x & 31;
+    unsigned w = m << (4 * (lane & 7));
+    w |= __shfl_xor_sync(0xffffffffu, w, 1);
+    w |= __shfl_xor_sync(0xffffffffu, w, 2);
+    w |= __shfl_xor_sync(0xffffffffu, w, 4);
+    if ((lane & 7) == 0 && x0 + 4 * lane < nx) fn((x0 >> 5) + (lane >> 3), w);
+}
+
+__device__ __forceinline__ float4 ld_row4(const float* __restrict__ row, bool ok, int x, int nx) {
+    return (ok && x < nx) ? __ldg(reinterpret_cast<const float4*>(row + x))
+                          : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
 // Pass 1.  Work is split by rows: warp w of a block takes rows w, w + 8, ...
 // of the block's tile.  A row's (y, z) is computed once per warp, rows on the
 // field boundary are skipped without reading them.  The per-tile count goes
 // to tile_count; with `bits` given, the row's interface bits are stored too
-// (wpr words per row), so that pass 3 need not read the field again.
+// (wpr words per row), so that pass 3 need not read the field again.  In the
+// vector path a warp takes two rows at a time and issues the four 16-byte
+// loads per lane of 256 columns of both rows before using any of them, so
+// every lane keeps 64 bytes in flight (the pass is bound by load latency, not
+// by the compare work).
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
                 int* __restrict__ tile_count, unsigned* __restrict__ bits, int vec) {
@@ -86,18 +116,45 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     const int wpr = (nx + 31) >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
     const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
-    int cnt = 0;
-    for (int64_t r = rbeg + warp; r < rend; r += CT_WARPS) {
+    auto interior = [&](int64_t r) {
         const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        unsigned* rb = bits ? bits + r * wpr : nullptr;
-        if (y < 1 || y > ny - 2 || z < 1 || z > nz - 2) {
-            if (rb)
-                for (int w = lane; w < wpr; w += 32) rb[w] = 0u;
-            continue;
+        return y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2;
+    };
+    int cnt = 0;
+    if (vec) {
+        for (int64_t ra = rbeg + warp; ra < rend; ra += 2 * CT_WARPS) {
+            const int64_t rb = ra + CT_WARPS;
+            const bool oka = interior(ra), hasb = rb < rend, okb = hasb && interior(rb);
+            const float* rowa = phi + ra * nx;
+            const float* rowb = phi + (hasb ? rb : ra) * nx;
+            unsigned* ba = bits ? bits + ra * wpr : nullptr;
+            unsigned* bb = (bits && hasb) ? bits + rb * wpr : nullptr;
+            for (int x0 = 0; x0 < nx; x0 += 256) {
+                const int xa = x0 + 4 * lane, xb = xa + 128;
+                const float4 a0 = ld_row4(rowa, oka, xa, nx), a1 = ld_row4(rowa, oka, xb, nx);
+                const float4 b0 = ld_row4(rowb, okb, xa, nx), b1 = ld_row4(rowb, okb, xb, nx);
+                const unsigned ma0 = oka ? nib4(a0, xa, nx) : 0u, ma1 = oka ? nib4(a1, xb, nx) : 0u;
+                const unsigned mb0 = okb ? nib4(b0, xa, nx) : 0u, mb1 = okb ? nib4(b1, xb, nx) : 0u;
+                cnt += __popc(ma0) + __popc(ma1) + __popc(mb0) + __popc(mb1);
+                emit_nibbles(ma0, x0, nx, [&](int w, unsigned b) { if (ba) ba[w] = b; });
+                emit_nibbles(ma1, x0 + 128, nx, [&](int w, unsigned b) { if (ba) ba[w] = b; });
+                emit_nibbles(mb0, x0, nx, [&](int w, unsigned b) { if (bb) bb[w] = b; });
+                emit_nibbles(mb1, x0 + 128, nx, [&](int w, unsigned b) { if (bb) bb[w] = b; });
+            }
         }
-        cnt += row_bits(phi + r * nx, nx, vec != 0, [&](int w, unsigned b) {
-            if (rb) rb[w] = b;
-        });
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+    } else {
+        for (int64_t r = rbeg + warp; r < rend; r += CT_WARPS) {
+            unsigned* rb = bits ? bits + r * wpr : nullptr;
+            if (!interior(r)) {
+                if (rb)
+                    for (int w = lane; w < wpr; w += 32) rb[w] = 0u;
+                continue;
+            }
+            cnt += row_bits(phi + r * nx, nx, false, [&](int w, unsigned b) {
+                if (rb) rb[w] = b;
+            });
+        }
     }
     __shared__ int ws[CT_WARPS];
     if (lane == 0) ws[warp] = cnt;

@@ -16,13 +16,14 @@ namespace plic {
 constexpr int CO_THREADS = 128;       // 4 warps per block
 constexpr int CO_WARPS = CO_THREADS / 32;
 
-// Single field: warp w of the grid takes batches of 32 list entries in a
-// grid-stride loop.
+// Single field: warp w of the grid takes batches of `batch` list entries (32,
+// or 16 / 8 when the list is too short to give every resident warp slot a
+// batch of 32) in a grid-stride loop.
 template <int METHOD, int FIT>
 __global__ void __launch_bounds__(CO_THREADS)
 k_vof_curvature(const float* __restrict__ phi, int nx, int ny, const int32_t* __restrict__ idx,
                 int64_t n, const int64_t* __restrict__ d_n, float* __restrict__ kappa,
-                uint32_t flags, float scale) {
+                uint32_t flags, float scale, int batch) {
     __shared__ float smem[CO_WARPS][CO_BATCH * CO_VALS];
     int64_t lim = n;
     if (d_n) {
@@ -33,17 +34,17 @@ k_vof_curvature(const float* __restrict__ phi, int nx, int ny, const int32_t* __
     const int64_t nxy = (int64_t)nx * ny;
     const int64_t gw = (int64_t)blockIdx.x * CO_WARPS + warp;
     const int64_t nw = (int64_t)gridDim.x * CO_WARPS;
-    for (int64_t k0 = gw * CO_BATCH; k0 < lim; k0 += nw * CO_BATCH) {
+    for (int64_t k0 = gw * batch; k0 < lim; k0 += nw * batch) {
         auto fetch = [&](int slot) {
             const int64_t k = k0 + slot;
             CoCell c;
             c.phi = phi; c.nx = nx; c.nxy = nxy;
-            c.valid = k < lim;
+            c.valid = slot < batch && k < lim;
             c.c = c.valid ? (int64_t)__ldg(idx + k) : 0;
             c.out = kappa + k;
             return c;
         };
-        co_warp_batch<METHOD, FIT>(fetch, flags, scale, smem[warp]);
+        co_warp_batch<METHOD, FIT>(fetch, batch, flags, scale, smem[warp]);
     }
 }
 
@@ -89,7 +90,7 @@ k_vof_curvature_batched(const vof_field* __restrict__ fields, const int64_t* __r
                 c.out = F.kappa + ks;
                 return c;
             };
-            co_warp_batch<METHOD, FIT>(fetch, flags, 1.0f, smem[warp]);
+            co_warp_batch<METHOD, FIT>(fetch, CO_BATCH, flags, 1.0f, smem[warp]);
         }
     }
 }
@@ -153,10 +154,14 @@ static plic_status curvature_entry(const float* phi, int nx, int ny, int nz, con
                                    fit_mode(flags), scale, stream, who);
     const void* k = select(false, m, fit_mode(flags));
     const int threads = CO_THREADS;
-    // one warp per 32 entries, at most one resident wave
-    const int grid = stride_grid(k, threads, (n_iface + CO_BATCH - 1) / CO_BATCH * 32);
+    // batches of 32 entries per warp, smaller ones when 32 would leave resident
+    // warp slots idle; at most one resident wave
+    const int64_t slots = (int64_t)sm_count() * blocks_per_sm(k, threads, 0) * CO_WARPS;
+    int batch = CO_BATCH;
+    while (batch > 8 && (n_iface + batch - 1) / batch < slots) batch >>= 1;
+    const int grid = stride_grid(k, threads, (n_iface + batch - 1) / batch * 32);
     void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&idx, (void*)&n_iface,
-                    (void*)&d_n_iface, (void*)&out, (void*)&flags, (void*)&scale};
+                    (void*)&d_n_iface, (void*)&out, (void*)&flags, (void*)&scale, (void*)&batch};
     cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, as_stream(stream));
     if (e != cudaSuccess) { set_last_error(who, e); return PLIC_ERR_CUDA; }
     return PLIC_OK;

@@ -248,24 +248,25 @@ __device__ __forceinline__ float co_solve(const float* rec, uint32_t flags) {
     return (flags & PLIC_FLAG_KAPPA_PAPER_SIGN) ? k : -k;
 }
 
-// One warp batch: `fetch(slot)` gives the CoCell of batch slot 0..31 (with
-// valid == false past the end).  `smem` holds CO_BATCH * CO_VALS floats for
-// this warp.  The stored value is scale * kappa (scale = 1 for the curvature
+// One warp batch of `batch` cells (a multiple of 4, at most CO_BATCH):
+// `fetch(slot)` gives the CoCell of batch slot 0..batch-1 (with valid == false
+// past the end of the list).  `smem` holds CO_BATCH * CO_VALS floats for this
+// warp.  The stored value is scale * kappa (scale = 1 for the curvature
 // itself, 2 sigma for the Young-Laplace pressure).
 template <int METHOD, int FIT, typename Fetch>
-__device__ __forceinline__ void co_warp_batch(Fetch fetch, uint32_t flags, float scale,
+__device__ __forceinline__ void co_warp_batch(Fetch fetch, int batch, uint32_t flags, float scale,
                                               float* smem) {
     const int lane = threadIdx.x & 31;
     const int g = lane & 7, grp = lane >> 3;
 #pragma unroll 1
-    for (int round = 0; round < CO_BATCH / 4; ++round) {
+    for (int round = 0; round < batch / 4; ++round) {
         const int slot = round * 4 + grp;
         const CoCell cell = fetch(slot);
         co_group_cell<METHOD>(cell, g, flags, smem + slot * CO_VALS);
     }
     __syncwarp();
-    const CoCell mine = fetch(lane);
-    if (mine.valid) *mine.out = scale * co_solve<FIT>(smem + lane * CO_VALS, flags);
+    const CoCell mine = fetch(lane);          // every lane: fetch may shuffle
+    if (lane < batch && mine.valid) *mine.out = scale * co_solve<FIT>(smem + lane * CO_VALS, flags);
     __syncwarp();
 }
 
