@@ -54,8 +54,8 @@ def peaks():
 # Sources of each profiled kernel's translation unit: a change to any of them
 # makes the stored ncu traffic figure stale.
 KERNEL_SOURCES = {
-    "plic_offset_sz_opt_fp32p": ("plic_offset.cu", "plic_pair.cuh", "plic_solvers.cuh",
-                                 "plic_math.cuh", "host_common.h"),
+    "plic_offset_roundtrip_sz_opt_fp32p": ("plic_offset.cu", "plic_pair.cuh", "plic_solvers.cuh",
+                                           "plic_math.cuh", "host_common.h"),
 }
 
 
@@ -209,6 +209,15 @@ def section_solvers(t32, dev, pk, steps):
     gbs = 20.0 * n * steps / sec / 1e9
     out["volume_fp32"] = {"g_cells_s": n * steps / sec / 1e9, "ms": sec / steps * 1e3,
                           "hbm_gbs": gbs, "hbm_frac": frac(gbs, pk["hbm_gbs"])}
+    # the headline step unfused: plic_offset, then plic_volume on its result
+    vr = torch.empty_like(t32[0])
+
+    def two_pass():
+        plic.offset(*t32, method="sz_opt", precision="fp32p", out=d0)
+        plic.volume(*t32[:3], d0, out=vr)
+    sec = timed(two_pass, steps, 2, s)
+    out["offset_then_volume_fp32p"] = {"g_solves_s": n * steps / sec / 1e9, "ms": sec / steps * 1e3}
+    del vr
     return out
 
 
@@ -439,6 +448,14 @@ def oracle_step(sample):
     oracle.volume(sample[0], sample[1], sample[2], d0)
 
 
+def headline_config():
+    return {"workload": "plic_offset_roundtrip: sz_opt offset (fp32 + 1 Newton polish) "
+                        "and the forward volume of the result, one fused kernel, "
+                        "2^28 SoA f32 cells per GPU, 10% within 1e-6 of a cube vertex",
+            "cells_per_gpu": CELLS, "method": "sz_opt", "precision": "fp32_polished",
+            "l2": "inputs 4 GiB per step > 129 MB L2 (no flush needed)"}
+
+
 def cpu_baseline(cells=1 << 24):
     import oracle
     sample = oracle_sample(cells)
@@ -472,11 +489,12 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "plic_offset + plic_volume round trip, FP64 CPU oracle, "
-                                   "%d-cell sample of the 2^28-cell workload per step" % per},
+            "config": headline_config(),
             "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle",
                              "cores": oracle.num_threads(),
-                             "sample": "%d cells per step" % per},
+                             "sample": "FP64 oracle (bisection offset + forward round trip) on the "
+                                       "first %d cells of the same seeded 2^28-cell stream per "
+                                       "step" % per},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -488,12 +506,15 @@ def run_case(args):
     from paper_2006_12838_gb300 import plic, synth
     B.build()
     dev = torch.device("cuda", 0)
-    if args.case in ("offset", "volume"):
+    if args.case in ("offset", "volume", "roundtrip"):
         t = make_cells_gpu(args.cells, 2, torch.float32, dev)
         d0 = torch.empty_like(t[0])
+        vr = torch.empty_like(t[0])
         for _ in range(args.steps):
             if args.case == "offset":
                 plic.offset(*t, method="sz_opt", precision="fp32p", out=d0)
+            elif args.case == "roundtrip":
+                plic.offset_roundtrip(*t, method="sz_opt", precision="fp32p", out=d0, out_rt=vr)
             else:
                 plic.volume(*t[:3], t[3], out=d0)
     elif args.case == "offset_fp64":
@@ -532,7 +553,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default=None,
                     help="profiling case: run only one kernel on --cells cells "
-                         "(offset | volume | offset_fp64 | curvature | batched)")
+                         "(offset | roundtrip | volume | offset_fp64 | curvature | batched)")
     ap.add_argument("--cells", type=int, default=1 << 24)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -566,13 +587,14 @@ def main():
     step_i = [0]
 
     def step(record=False):
+        # one launch: the fused solve + forward round trip (k_plic_offset_sz_opt_pair
+        # with ROUNDTRIP), events around it on the launching stream
         if record:
             ev[step_i[0]][0].record(s)
-        plic.offset(*t32, method="sz_opt", precision="fp32p", out=d0)
+        plic.offset_roundtrip(*t32, method="sz_opt", precision="fp32p", out=d0, out_rt=Vrt)
         if record:
             ev[step_i[0]][1].record(s)
             step_i[0] += 1
-        plic.volume(t32[0], t32[1], t32[2], d0, out=Vrt)
 
     for _ in range(args.warmup):
         step()
@@ -618,31 +640,28 @@ def main():
         e2e = {"value": CELLS * world * esteps / esec / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 16 * CELLS, "d2h_bytes_per_step": 8 * CELLS,
                "steps": esteps, "chunk_cells": 1 << 24,
-               "note": "pinned host SoA -> 3-stream chunked H2D / plic_offset+plic_volume / D2H"}
+               "note": "pinned host SoA -> 3-stream chunked H2D / plic_offset_roundtrip / D2H"}
         del hn, hd, hV, pipe
     except Exception as ex:  # report, do not hide
         e2e = {"value": None, "unit": UNIT, "error": repr(ex)[:200],
                "h2d_bytes_per_step": 16 * CELLS, "d2h_bytes_per_step": 8 * CELLS}
 
-    alg_bytes = 20.0 * CELLS
+    # 24 B/cell: nx, ny, nz, V0 in (16) + d0, V0_rt out (8)
+    alg_bytes = 24.0 * CELLS
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_plic_offset<SZ_OPT,float,polish>",
+    roof = {"bound": "hbm", "kernel": "k_plic_offset_sz_opt_pair<POLISH=1,ROUNDTRIP=1>",
             "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)",
-            "traffic": profile_traffic("plic_offset_sz_opt_fp32p"),
+            "traffic": profile_traffic("plic_offset_roundtrip_sz_opt_fp32p"),
             "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": alg_bytes}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "plic_offset (sz_opt, fp32 + 1 Newton polish) + plic_volume "
-                                   "round trip, 2^28 SoA f32 cells per GPU, 10% within 1e-6 of "
-                                   "a cube vertex",
-                       "cells_per_gpu": CELLS, "method": "sz_opt", "precision": "fp32_polished",
-                       "l2": "inputs 4 GiB per step > 129 MB L2 (no flush needed)"},
+            "config": headline_config(),
             "roofline": roof, "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "accuracy": {"roundtrip_max": rt_max, "roundtrip_mean": rt_mean}}
 

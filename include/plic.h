@@ -122,6 +122,20 @@ plic_status plic_offset(const void *nx, const void *ny, const void *nz, const vo
                         void *d0, int64_t n, plic_method m, plic_precision p, uint32_t flags,
                         int64_t *d_invalid_count, void *stream);
 
+/* plic_offset_roundtrip -- plic_offset together with the forward volume of
+ * its own result, the round trip of the paper's accuracy measure (Sec. 2.5,
+ * Eqs. 27-28): d0[i] exactly as plic_offset returns it, and
+ * V0_rt[i] = V0(n_i, d0[i]) (Eq. 10) evaluated on the stored d0[i] in the
+ * precision of the call, so |V0_rt - V0| is the cell's round-trip error.  For
+ * the optimised SZ solver in FP32 / FP32_POLISHED the two are one kernel (n
+ * and V0 read once: 16 bytes in, 8 out per cell); the other methods and
+ * precisions run plic_offset and then plic_volume.  Arguments, flags and
+ * errors as plic_offset; V0_rt (out) has the type and length of d0. */
+plic_status plic_offset_roundtrip(const void *nx, const void *ny, const void *nz, const void *V0,
+                                  void *d0, void *V0_rt, int64_t n, plic_method m,
+                                  plic_precision p, uint32_t flags, int64_t *d_invalid_count,
+                                  void *stream);
+
 /* plic_offset_backward -- vector-Jacobian product of plic_offset at its
  * solution d0 (implicit function theorem on Eq. 1 for unit n):
  *   g_V0 = g_d0 / A,    g_n = g_d0 * c,

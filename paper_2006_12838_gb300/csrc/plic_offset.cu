@@ -39,7 +39,7 @@ template <int METHOD, typename T, bool POLISH, bool FAITHFUL>
 __global__ void __launch_bounds__(256)
 k_plic_offset(const T* __restrict__ nx, const T* __restrict__ ny, const T* __restrict__ nz,
               const T* __restrict__ V0, T* __restrict__ d0, int64_t n, int vec_ok,
-              unsigned long long* invalid) {
+              unsigned long long* invalid, void* /* round trip: not fused here */) {
     typedef typename Vec16<T>::type VT;
     constexpr int W = Vec16<T>::W;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,12 +65,14 @@ k_plic_offset(const T* __restrict__ nx, const T* __restrict__ ny, const T* __res
 // 2.5) on paired FP32 instructions: each thread takes 4 cells per step as two
 // pairs.  Tail and unaligned cells go through the same pair code with the
 // cell duplicated in both lanes, so every cell sees identical arithmetic.
-template <bool POLISH>
+// With ROUNDTRIP the forward volume of each stored d0 is written to vrt in
+// the same pass (plic_offset_roundtrip).
+template <bool POLISH, bool ROUNDTRIP>
 __global__ void __launch_bounds__(256)
 k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict__ ny,
                           const float* __restrict__ nz, const float* __restrict__ V0,
                           float* __restrict__ d0, int64_t n, int vec_ok,
-                          unsigned long long* invalid) {
+                          unsigned long long* invalid, float* __restrict__ vrt) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int bad = 0;
@@ -93,19 +95,26 @@ k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict_
             c2 = __ldcs(reinterpret_cast<const float4*>(nz) + j);
             v2 = __ldcs(reinterpret_cast<const float4*>(V0) + j);
         }
-        const float2 r0 = p2::offset_sz_opt<POLISH>(make_float2(a.x, a.y), make_float2(b.x, b.y),
-                                                    make_float2(c.x, c.y), make_float2(v.x, v.y), bad);
-        const float2 r1 = p2::offset_sz_opt<POLISH>(make_float2(a.z, a.w), make_float2(b.z, b.w),
-                                                    make_float2(c.z, c.w), make_float2(v.z, v.w), bad);
+        float2 w0, w1;
+        const float2 r0 = p2::offset_sz_opt<POLISH, ROUNDTRIP>(
+            make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y), make_float2(v.x, v.y),
+            bad, &w0);
+        const float2 r1 = p2::offset_sz_opt<POLISH, ROUNDTRIP>(
+            make_float2(a.z, a.w), make_float2(b.z, b.w), make_float2(c.z, c.w), make_float2(v.z, v.w),
+            bad, &w1);
         __stcs(reinterpret_cast<float4*>(d0) + i, make_float4(r0.x, r0.y, r1.x, r1.y));
+        if (ROUNDTRIP) __stcs(reinterpret_cast<float4*>(vrt) + i, make_float4(w0.x, w0.y, w1.x, w1.y));
         a = a2; b = b2; c = c2; v = v2;
     }
     for (int64_t i = nvec * 4 + tid; i < n; i += stride) {
         int bad2 = 0;
-        const float2 r = p2::offset_sz_opt<POLISH>(make_float2(nx[i], nx[i]), make_float2(ny[i], ny[i]),
-                                                   make_float2(nz[i], nz[i]), make_float2(V0[i], V0[i]), bad2);
+        float2 w;
+        const float2 r = p2::offset_sz_opt<POLISH, ROUNDTRIP>(
+            make_float2(nx[i], nx[i]), make_float2(ny[i], ny[i]), make_float2(nz[i], nz[i]),
+            make_float2(V0[i], V0[i]), bad2, &w);
         bad += bad2 >> 1;
         d0[i] = r.x;
+        if (ROUNDTRIP) vrt[i] = w.x;
     }
     count_invalid(bad, invalid);
 }
@@ -116,7 +125,7 @@ __global__ void __launch_bounds__(256)
 k_plic_offset_refined(const double* __restrict__ nx, const double* __restrict__ ny,
                       const double* __restrict__ nz, const double* __restrict__ V0,
                       double* __restrict__ d0, int64_t n, int vec_ok,
-                      unsigned long long* invalid) {
+                      unsigned long long* invalid, void* /* round trip: not fused here */) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int bad = 0;
@@ -135,9 +144,6 @@ k_plic_offset_refined(const double* __restrict__ nx, const double* __restrict__ 
     count_invalid(bad, invalid);
 }
 
-typedef void (*offset_kernel_t)(const void*, const void*, const void*, const void*, void*,
-                                int64_t, int, unsigned long long*);
-
 template <int METHOD, typename T, bool POLISH, bool FAITHFUL>
 static const void* kptr() {
     return reinterpret_cast<const void*>(&k_plic_offset<METHOD, T, POLISH, FAITHFUL>);
@@ -153,13 +159,11 @@ static const void* pick(plic_precision p, bool faithful) {
     return faithful ? kptr<METHOD, float, false, true>() : kptr<METHOD, float, false, false>();
 }
 
-}  // namespace plic
-
-extern "C" plic_status plic_offset(const void* nx, const void* ny, const void* nz,
-                                   const void* V0, void* d0, int64_t n, plic_method m,
-                                   plic_precision p, uint32_t flags, int64_t* d_invalid_count,
-                                   void* stream) {
-    using namespace plic;
+static plic_status offset_entry(const void* nx, const void* ny, const void* nz, const void* V0,
+                                void* d0, void* vrt, int64_t n, plic_method m, plic_precision p,
+                                uint32_t flags, int64_t* d_invalid_count, void* stream,
+                                bool* fused, const char* who) {
+    *fused = false;
     if (n < 0) return PLIC_ERR_ARG;
     if ((int)m < 0 || (int)m > 4 || (int)p < 0 || (int)p > 3) return PLIC_ERR_ARG;
     if (flags & ~(uint32_t)PLIC_FLAG_FAITHFUL) return PLIC_ERR_ARG;
@@ -169,21 +173,27 @@ extern "C" plic_status plic_offset(const void* nx, const void* ny, const void* n
     const bool dbl = p == PLIC_FP64 || p == PLIC_FP64_REFINED;
     const size_t es = dbl ? 8 : 4;
     if (!aligned(nx, es) || !aligned(ny, es) || !aligned(nz, es) || !aligned(V0, es) ||
-        !aligned(d0, es) || (d_invalid_count && !aligned(d_invalid_count, 8)))
+        !aligned(d0, es) || (vrt && !aligned(vrt, es)) ||
+        (d_invalid_count && !aligned(d_invalid_count, 8)))
         return PLIC_ERR_ALIGN;
     const int vec_ok = aligned(nx, 16) && aligned(ny, 16) && aligned(nz, 16) && aligned(V0, 16) &&
-                       aligned(d0, 16);
+                       aligned(d0, 16) && (!vrt || aligned(vrt, 16));
     const bool faithful = (flags & PLIC_FLAG_FAITHFUL) != 0;
     const void* k = nullptr;
     switch (m) {
         case PLIC_ANALYTIC: k = pick<M_ANALYTIC>(p, faithful); break;
         case PLIC_SZ_ORIG: k = pick<M_SZ_ORIG>(p, faithful); break;
         case PLIC_SZ_OPT:
-            if (!dbl && !faithful)
-                k = p == PLIC_FP32_POLISHED ? reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<true>)
-                                            : reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<false>);
-            else
+            if (!dbl && !faithful) {
+                const bool pol = p == PLIC_FP32_POLISHED;
+                *fused = vrt != nullptr;
+                k = *fused ? (pol ? reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<true, true>)
+                                  : reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<false, true>))
+                           : (pol ? reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<true, false>)
+                                  : reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<false, false>));
+            } else {
                 k = pick<M_SZ_OPT>(p, faithful);
+            }
             break;
         case PLIC_NEWTON: k = pick<M_NEWTON>(p, faithful); break;
         case PLIC_NESTED: k = pick<M_NESTED>(p, faithful); break;
@@ -194,11 +204,35 @@ extern "C" plic_status plic_offset(const void* nx, const void* ny, const void* n
     const int grid = stride_grid(k, threads, work);
     unsigned long long* inv = reinterpret_cast<unsigned long long*>(d_invalid_count);
     void* args[] = {(void*)&nx, (void*)&ny, (void*)&nz, (void*)&V0, (void*)&d0,
-                    (void*)&n, (void*)&vec_ok, (void*)&inv};
+                    (void*)&n, (void*)&vec_ok, (void*)&inv, (void*)&vrt};
     cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, as_stream(stream));
     if (e != cudaSuccess) {
-        set_last_error("plic_offset", e);
+        set_last_error(who, e);
         return PLIC_ERR_CUDA;
     }
     return PLIC_OK;
+}
+
+}  // namespace plic
+
+extern "C" plic_status plic_offset(const void* nx, const void* ny, const void* nz,
+                                   const void* V0, void* d0, int64_t n, plic_method m,
+                                   plic_precision p, uint32_t flags, int64_t* d_invalid_count,
+                                   void* stream) {
+    bool fused;
+    return plic::offset_entry(nx, ny, nz, V0, d0, nullptr, n, m, p, flags, d_invalid_count, stream,
+                              &fused, "plic_offset");
+}
+
+extern "C" plic_status plic_offset_roundtrip(const void* nx, const void* ny, const void* nz,
+                                             const void* V0, void* d0, void* V0_rt, int64_t n,
+                                             plic_method m, plic_precision p, uint32_t flags,
+                                             int64_t* d_invalid_count, void* stream) {
+    if (n > 0 && !V0_rt) return PLIC_ERR_ARG;
+    bool fused;
+    plic_status s = plic::offset_entry(nx, ny, nz, V0, d0, V0_rt, n, m, p, flags, d_invalid_count,
+                                       stream, &fused, "plic_offset_roundtrip");
+    if (s != PLIC_OK || fused || n == 0) return s;
+    const plic_precision vp = (p == PLIC_FP64 || p == PLIC_FP64_REFINED) ? PLIC_FP64 : PLIC_FP32;
+    return plic_volume(nx, ny, nz, d0, V0_rt, n, vp, stream);
 }

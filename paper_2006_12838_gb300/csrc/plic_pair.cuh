@@ -144,9 +144,37 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3) {
     return sel(le(n12, n3V2), d5, d);
 }
 
-// Whole cells: two (n, V0) -> d0 by the optimised SZ solution in FP32.
-template <bool POLISH>
-__device__ __forceinline__ f2 offset_sz_opt(f2 nx, f2 ny, f2 nz, f2 V0, int& bad) {
+// Forward volume (Eq. 10) of two cells at their offsets d0, in the cell's
+// L1-normalised reduced space (m1 <= m2 <= m3, m1 + m2 + m3 = 1; Eq. 10 is
+// homogeneous of degree 0 in (d, n)), il = 1/L:
+//   d = 1/2 - |d0|/L (clamped at 0), then case (5) (d - m12/2)/m3 for
+//   d >= m1 + m2, case (1) d^3/(6 m1 m2 m3) for d < m1, else
+//   (3 d (d - m1) + m1^2 - ((d - m2)_+^3 + (d - m3)_+^3)/m1) / (6 m2 m3),
+// and V0 = 1 - V for d0 > 0.
+__device__ __forceinline__ f2 volume_reduced(f2 d0, f2 il, f2 m1, f2 m2, f2 m3) {
+    const f2 ad = make_float2(fabsf(d0.x), fabsf(d0.y));
+    const f2 d = fmax0(fma(make_float2(-ad.x, -ad.y), il, mk(0.5f)));
+    const f2 m12 = add(m1, m2);
+    const f2 v5 = mul(fma(mk(-0.5f), m12, d), rcp(m3));
+    const f2 m2m3 = mul(m2, m3);
+    const f2 v1 = mul(mul(mul(d, d), d), rcp(mul(mul(mk(6.0f), m1), m2m3)));
+    const f2 r1 = rcp(m1);
+    const f2 inv1 = make_float2(m1.x > 0.0f ? r1.x : 0.0f, m1.y > 0.0f ? r1.y : 0.0f);
+    const f2 e2 = fmax0(sub(d, m2)), e3 = fmax0(sub(d, m3));
+    const f2 cub = fma(mul(e2, e2), e2, mul(mul(e3, e3), e3));
+    f2 num = fma(mul(mk(3.0f), d), sub(d, m1), mul(m1, m1));
+    num = fma(make_float2(-cub.x, -cub.y), inv1, num);
+    const f2 v24 = mul(num, rcp(mul(mk(6.0f), m2m3)));
+    f2 v = sel(lt(d, m1), v1, v24);
+    v = sel(le(m12, d), v5, v);
+    return make_float2(d0.x > 0.0f ? 1.0f - v.x : v.x, d0.y > 0.0f ? 1.0f - v.y : v.y);
+}
+
+// Whole cells: two (n, V0) -> d0 by the optimised SZ solution in FP32; with
+// ROUNDTRIP, also the forward volume of the returned d0 into *vrt.
+template <bool POLISH, bool ROUNDTRIP = false>
+__device__ __forceinline__ f2 offset_sz_opt(f2 nx, f2 ny, f2 nz, f2 V0, int& bad,
+                                            f2* vrt = nullptr) {
     const f2 ax = make_float2(fabsf(nx.x), fabsf(nx.y));
     const f2 ay = make_float2(fabsf(ny.x), fabsf(ny.y));
     const f2 az = make_float2(fabsf(nz.x), fabsf(nz.y));
@@ -168,6 +196,12 @@ __device__ __forceinline__ f2 offset_sz_opt(f2 nx, f2 ny, f2 nz, f2 V0, int& bad
     f2 r = mul(L, make_float2(copysignf(h.x, V0.x - 0.5f), copysignf(h.y, V0.y - 0.5f)));
     if (!okx) r.x = __int_as_float(0x7fffffff);
     if (!oky) r.y = __int_as_float(0x7fffffff);
+    if (ROUNDTRIP) {
+        f2 v = volume_reduced(r, il, m1, m2, m3);
+        if (!okx) v.x = __int_as_float(0x7fffffff);
+        if (!oky) v.y = __int_as_float(0x7fffffff);
+        *vrt = v;
+    }
     return r;
 }
 

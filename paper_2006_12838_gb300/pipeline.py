@@ -19,7 +19,8 @@ class HostOffsetPipeline:
 
     ``run(nx, ny, nz, V0, d0_out, V0_roundtrip_out=None)`` solves
     d0 = plic_offset(n, V0) for host tensors (pinned) and, if
-    ``V0_roundtrip_out`` is given, also the forward volume of the result."""
+    ``V0_roundtrip_out`` is given, also the forward volume of the result
+    (plic_offset_roundtrip)."""
 
     def __init__(self, chunk: int, dtype=torch.float32, device="cuda", method="sz_opt",
                  precision=None, depth: int = 3):
@@ -56,12 +57,13 @@ class HostOffsetPipeline:
                     dst.copy_(src[start:start + k], non_blocking=True)
                 ev_in[b].record(self.h2d)
             self.comp.wait_event(ev_in[b])
-            plic.offset(bx, by, bz, bv, method=self.method, precision=self.precision, out=bd,
-                        stream=self.comp)
-            self.launches += 1
             if V_out is not None:
-                plic.volume(bx, by, bz, bd, out=bw, stream=self.comp)
-                self.launches += 1
+                plic.offset_roundtrip(bx, by, bz, bv, method=self.method, precision=self.precision,
+                                      out=bd, out_rt=bw, stream=self.comp)
+            else:
+                plic.offset(bx, by, bz, bv, method=self.method, precision=self.precision, out=bd,
+                            stream=self.comp)
+            self.launches += 1
             ev_done[b].record(self.comp)
             self.d2h.wait_event(ev_done[b])
             with torch.cuda.stream(self.d2h):

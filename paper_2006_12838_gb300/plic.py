@@ -79,6 +79,7 @@ def load():
             "vof_curvature_batched": [P, I32, P, I32, U32, P, SZ, P],
             "plic_paper_benchmark": [P, P, P, I64, I32, I32, I32, I32, P, P],
             "plic_sphere_volume": [P, P, I64, I32, P],
+            "plic_offset_roundtrip": [P, P, P, P, P, P, I64, I32, I32, U32, P, P],
             "plic_sphere_offset": [P, P, I64, I32, P],
         }
         for name, args in sigs.items():
@@ -170,6 +171,26 @@ def offset(nx, ny, nz, V0, method="sz_opt", precision=None, faithful=False, out=
                               FLAG_FAITHFUL if faithful else 0, _ptr(invalid),
                               _stream(V0, stream)), "plic_offset")
     return out
+
+
+def offset_roundtrip(nx, ny, nz, V0, method="sz_opt", precision=None, faithful=False, out=None,
+                     out_rt=None, invalid=None, stream=None):
+    """(d0, V0_rt): plic_offset and the forward volume of its result in one
+    call (Sec. 2.5 round trip); one fused kernel for SZ-opt in FP32."""
+    _cuda(nx, ny, nz, V0, out, out_rt, dtype=V0.dtype)
+    p = _prec(V0.dtype, precision)
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    if invalid is not None:
+        _cuda(V0, invalid, dtype=None)
+        if invalid.dtype != torch.int64:
+            raise PlicError("invalid counter must be int64")
+    out = torch.empty_like(V0) if out is None else out
+    out_rt = torch.empty_like(V0) if out_rt is None else out_rt
+    _check(load().plic_offset_roundtrip(_ptr(nx), _ptr(ny), _ptr(nz), _ptr(V0), _ptr(out),
+                                        _ptr(out_rt), V0.numel(), m, p,
+                                        FLAG_FAITHFUL if faithful else 0, _ptr(invalid),
+                                        _stream(V0, stream)), "plic_offset_roundtrip")
+    return out, out_rt
 
 
 def offset_backward(nx, ny, nz, d0, g_d0, stream=None, need=(True, True)):

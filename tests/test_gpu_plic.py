@@ -212,3 +212,46 @@ def test_paper_harness(dev, orc, method):
     t = _to(dev, torch.float32, n[0], n[1], n[2])
     eb = plic.paper_benchmark(*t, L=L, blank=True).item()
     assert np.isfinite(eb) and eb > 0
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("precision", ["fp32", "fp32p", "fp64", "fp64r"])
+def test_offset_roundtrip(dev, orc, c1, method, precision):
+    # plic_offset_roundtrip: d0 identical to plic_offset, V0_rt = V0(n, d0) on the
+    # stored d0 (one fused kernel for SZ-opt in FP32, offset + volume otherwise)
+    n, V0, _ = c1
+    dt = torch.float64 if precision.startswith("fp64") else torch.float32
+    t = _to(dev, dt, n[0], n[1], n[2], V0)
+    want = plic.offset(*t, method=method, precision=precision)
+    d0, vrt = plic.offset_roundtrip(*t, method=method, precision=precision)
+    assert torch.equal(torch.isnan(d0), torch.isnan(want))
+    ok = ~torch.isnan(want)
+    assert torch.equal(d0[ok], want[ok])
+    nn = [x.cpu().numpy().astype(np.float64) for x in t[:3]]
+    d = d0.cpu().numpy().astype(np.float64)
+    v = vrt.cpu().numpy().astype(np.float64)
+    good = ~np.isnan(d)
+    ref = orc.volume(nn[0][good], nn[1][good], nn[2][good], d[good])
+    err = np.abs(v[good] - ref)
+    rt = np.abs(v[good] - t[3].cpu().numpy().astype(np.float64)[good])
+    print("%s %s roundtrip: |V_rt - V(n,d0)| %.3e, |V_rt - V0| %.3e" % (method, precision, err.max(), rt.max()))
+    assert err.max() <= (1e-15 if dt == torch.float64 else 3e-7)
+    assert np.isnan(v[~good]).all()
+    if precision in ("fp32p", "fp64", "fp64r"):
+        assert rt.max() <= (1e-14 if dt == torch.float64 else 1e-6)
+
+
+def test_offset_roundtrip_ragged(dev, orc):
+    c = synth.plic_cells(4099, seed=17)
+    n, V0 = c["n"], c["V0"]
+    base = _to(dev, torch.float32, *[np.concatenate([[0.5], a]) for a in (n[0], n[1], n[2], V0)])
+    for k in (1, 2, 3, 5, 4097, 4098):
+        aligned = [b[1:1 + k].clone() for b in base]
+        shifted = [b[1:1 + k] for b in base]                 # 4-byte offset: scalar path
+        d_a, v_a = plic.offset_roundtrip(*aligned, precision="fp32p")
+        d_s, v_s = plic.offset_roundtrip(*shifted, precision="fp32p")
+        np.testing.assert_allclose(d_a.cpu().numpy(), d_s.cpu().numpy(), rtol=0, atol=1e-7)
+        np.testing.assert_allclose(v_a.cpu().numpy(), v_s.cpu().numpy(), rtol=0, atol=1e-7)
+        ref = orc.volume(n[0][:k].astype(np.float32), n[1][:k].astype(np.float32),
+                         n[2][:k].astype(np.float32), d_a.cpu().numpy().astype(np.float64))
+        assert np.abs(v_a.cpu().numpy() - ref).max() <= 3e-7

@@ -86,6 +86,13 @@ def test_full_size_sampled(dev, orc):
         samp.append((start + pick, n[:, pick], V0.astype(np.float32).astype(np.float64)[pick]))
     d0 = plic.offset(*t, method="sz_opt", precision="fp32p")
     Vb = plic.volume(t[0], t[1], t[2], d0)
+    # the fused round trip (the bench's step) gives the same d0 and a V0_rt
+    # within rounding of plic_volume's
+    d0f, vrt = plic.offset_roundtrip(*t, method="sz_opt", precision="fp32p")
+    assert torch.equal(d0f, d0)
+    assert (vrt - Vb).abs().max().item() <= 3e-7
+    assert (vrt - t[3]).abs().max().item() <= 1e-6
+    del d0f, vrt
     idx = np.concatenate([s[0] for s in samp])
     nn = np.concatenate([s[1] for s in samp], axis=1)
     VV = np.concatenate([s[2] for s in samp])
