@@ -220,6 +220,7 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
                 int32_t* __restrict__ idx, int64_t cap, int vec) {
     __shared__ unsigned bal[CT_MAX_WORDS];
     __shared__ int rowoff[CT_MAX_ROWS + 1];
+    __shared__ int rowcnt[CT_MAX_ROWS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
     const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
@@ -247,7 +248,7 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
                 for (int w = lane; w < wpr; w += 32) bal[k * wpr + w] = 0u;
             }
         }
-        if (lane == 0) rowoff[k] = cnt;
+        if (lane == 0) rowoff[k] = rowcnt[k] = cnt;
     }
     __syncthreads();
     if (warp == 0) {
@@ -272,6 +273,7 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     __syncthreads();
     const int64_t base = tile_offset[blockIdx.x];
     for (int k = warp; k < nr; k += CT_WARPS) {
+        if (rowcnt[k] == 0) continue;               // most rows of a field hold no interface cell
         const int64_t r = rbeg + k;
         int64_t pos = base + rowoff[k];
         // one lane per 32-cell word: warp prefix of the word counts, then each

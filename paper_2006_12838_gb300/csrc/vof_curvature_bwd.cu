@@ -233,31 +233,48 @@ __global__ void k_curv_slot_scatter(const int32_t* __restrict__ idx, int64_t n,
 }
 
 // g_phi[j] = sum over the 27 offsets o of contrib[slot[j - e_o]][o] (when cell
-// j - e_o is in the field and in the list).  One warp per row, one lane per x.
+// j - e_o is in the field and in the list), in the fixed order o = 0..26.
+// Only cells in the 3^3 neighbourhood of an interface cell can be non-zero,
+// so the work runs over the (list entry k, offset o) pairs: pair (k, o) looks
+// at j = idx[k] + e_o, and computes and stores g_phi[j] only if k is the
+// first list entry (smallest index, i.e. smallest cell) whose stencil holds j,
+// so every such j is written exactly once, with the same summation order as a
+// dense pass.  The rest of g_phi was zeroed before.  O(27 * 27 * K) loads of
+// the slot map instead of 27 per field cell.
 __global__ void __launch_bounds__(256)
-k_curv_gather(const int32_t* __restrict__ slot, const float* __restrict__ contrib, int nx, int ny,
+k_curv_gather(const int32_t* __restrict__ idx, int64_t n, const int64_t* __restrict__ d_n,
+              const int32_t* __restrict__ slot, const float* __restrict__ contrib, int nx, int ny,
               int nz, float* __restrict__ g_phi) {
-    const int lane = threadIdx.x & 31;
-    const int64_t rows = (int64_t)ny * nz;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t lim = n;
+    if (d_n) {
+        const int64_t dn = *d_n;
+        lim = dn < n ? dn : n;
+    }
     const int64_t nxy = (int64_t)nx * ny;
-    for (int64_t r = warp0; r < rows; r += nwarps) {
-        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        for (int x = lane; x < nx; x += 32) {
-            const int64_t j = r * nx + x;
-            float acc = 0.0f;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < lim * 27;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / 27;
+        const int o = (int)(t - k * 27);
+        int ex, ey, ez;
+        e_of(o, ex, ey, ez);
+        const int64_t c = __ldg(idx + k);
+        const int64_t j = c + ex + (int64_t)ey * nx + (int64_t)ez * nxy;
+        const int z = (int)(j / nxy), y = (int)((j / nx) % ny), x = (int)(j % nx);
+        float acc = 0.0f;
+        int32_t first = 0x7fffffff;
 #pragma unroll
-            for (int o = 0; o < 27; ++o) {
-                int ex, ey, ez;
-                e_of(o, ex, ey, ez);
-                const int sx = x - ex, sy = y - ey, sz = z - ez;
-                if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz) continue;
-                const int32_t sl = __ldg(slot + (j - ex - (int64_t)ey * nx - (int64_t)ez * nxy));
-                if (sl >= 0) acc += __ldg(contrib + (int64_t)sl * 27 + o);
+        for (int q = 0; q < 27; ++q) {
+            int fx, fy, fz;
+            e_of(q, fx, fy, fz);
+            const int sx = x - fx, sy = y - fy, sz = z - fz;
+            if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz) continue;
+            const int32_t sl = __ldg(slot + (j - fx - (int64_t)fy * nx - (int64_t)fz * nxy));
+            if (sl >= 0) {
+                acc += __ldg(contrib + (int64_t)sl * 27 + q);
+                first = sl < first ? sl : first;
             }
-            g_phi[j] = acc;
         }
+        if (first == (int32_t)k) g_phi[j] = acc;
     }
 }
 
@@ -326,8 +343,11 @@ extern "C" plic_status vof_curvature_backward(const float* phi, int nx, int ny, 
         const int sg = stride_grid(reinterpret_cast<const void*>(&k_curv_slot_scatter), 256, n_iface);
         k_curv_slot_scatter<<<sg, 256, 0, s>>>(idx, n_iface, d_n_iface, slot);
     }
-    const int64_t rows = (int64_t)ny * nz;
-    const int gg = stride_grid(reinterpret_cast<const void*>(&k_curv_gather), 256, rows * 32);
-    k_curv_gather<<<gg, 256, 0, s>>>(slot, contrib, nx, ny, nz, g_phi);
+    e = cudaMemsetAsync(g_phi, 0, (size_t)cells * sizeof(float), s);
+    if (e != cudaSuccess) { set_last_error("vof_curvature_backward", e); return PLIC_ERR_CUDA; }
+    if (n_iface > 0) {
+        const int gg = stride_grid(reinterpret_cast<const void*>(&k_curv_gather), 256, n_iface * 27);
+        k_curv_gather<<<gg, 256, 0, s>>>(idx, n_iface, d_n_iface, slot, contrib, nx, ny, nz, g_phi);
+    }
     return check_launch("vof_curvature_backward");
 }
