@@ -7,11 +7,10 @@
 // u = (r + d0)/r for d0 <= 0, the forward problem is
 //     W = u^2 (3 - u) / 4,   u in [0, 1],  W = min(V0, 1 - V0) in [0, 1/2],
 // because pi r^3 = 3/4.  The inverse is solved per cell without
-// trigonometric functions: u0 = s p(s), s = sqrt(W), a degree-4 least-squares
-// polynomial (|u0 - u| < 2.2e-4 on [0, 1/2]), then two Newton steps on
-// u^2 (3 - u) = 4W in FP32 with the MUFU reciprocal (|u - u*| < 1e-7).  FP64
-// continues from the FP32 root with two Newton steps whose residual is
-// evaluated in FP64 and whose
+// trigonometric functions: a polynomial start in s = sqrt(W) (see cap_u_f32)
+// and one Newton step on u^2 (3 - u) = 4W in FP32 with the MUFU reciprocal
+// (|d0 - d0*| < 1e-7).  FP64 continues from the FP32 root with two Newton
+// steps whose residual is evaluated in FP64 and whose
 // derivative is the FP32 reciprocal: each step multiplies the error by about
 // 1e-7, so the result is within a few ulp.  The paper's closed form (an arc
 // tangent and a sine) is the reference the oracle is pinned to; this kernel
@@ -28,18 +27,21 @@ namespace sphere {
 constexpr double R = 0.620350490899400016668;      // (3/(4 pi))^(1/3)
 constexpr double INV_R = 1.0 / R;
 
-// u^2 (3 - u) = 4W, W in [0, 1/2] -> u in [0, 1] (FP32, two Newton steps)
+// u^2 (3 - u) = 4W, W in [0, 1/2] -> u in [0, 1] (FP32).  Start:
+// u0 = s (2/sqrt3 + s p(s)), s = sqrt(W), with the exact leading term of the
+// small-W expansion u = sqrt(4W/3) + ... and a degree-4 least-squares p
+// (|u0 - u| < 1.5e-5 on [0, 1/2]); one Newton step then leaves the FP32
+// rounding of the result (|d0 - d0*| < 1e-7).
 __device__ __forceinline__ float cap_u_f32(float W) {
     const float s = W > 0.0f ? W * rsqrtf(W) : 0.0f;
-    float u = s * fmaf(s, fmaf(s, fmaf(s, 0.37590931f, -0.1529263f), 0.29526521f), 1.1486839f);
-    const float W4 = 4.0f * W;
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const float f = fmaf(u * u, 3.0f - u, -W4);
-        const float fp = 3.0f * u * (2.0f - u);
-        u = fp > 0.0f ? u - f * Fm<float>::rcp_(fp) : u;
-    }
-    return u;
+    float p = fmaf(s, 0.4812777f, -0.55447954f);
+    p = fmaf(s, p, 0.3771915f);
+    p = fmaf(s, p, 0.03742398f);
+    p = fmaf(s, p, 0.22763859f);
+    float u = s * fmaf(s, p, 1.1547005f);
+    const float f = fmaf(u * u, 3.0f - u, -4.0f * W);
+    const float fp = 3.0f * u * (2.0f - u);
+    return fp > 0.0f ? u - f * Fm<float>::rcp_(fp) : u;
 }
 
 template <typename T> __device__ __forceinline__ T offset_cell(T V0);

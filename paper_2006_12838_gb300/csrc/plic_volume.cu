@@ -7,7 +7,7 @@
 // All three kernels stream structure-of-arrays data through 16-byte vectors in
 // a one-wave grid-stride loop, as plic_offset does.
 #include "host_common.h"
-#include "plic_solvers.cuh"
+#include "plic_polygon.cuh"
 
 namespace plic {
 
@@ -49,7 +49,7 @@ __device__ __forceinline__ void adjoint_cell(T nx, T ny, T nz, T d0, T g, T& gs,
     T A, cx, cy, cz;
     const bool ok = cut_polygon<T>(nx, ny, nz, d0, A, cx, cy, cz);
     if (MODE == 0) {
-        gs = ok ? g / A : (g == T(0) ? T(0) : copysign(T(INFINITY), g));
+        gs = ok ? Fm<T>::div_(g, A) : (g == T(0) ? T(0) : copysign(T(INFINITY), g));
         gx = g * cx; gy = g * cy; gz = g * cz;
         if (!ok && !(fabs(nx) + fabs(ny) + fabs(nz) > T(0))) gs = gx = gy = gz = T(NAN);
     } else {

@@ -18,7 +18,7 @@
 //   7. mean curvature of the paraboloid at the origin (Eq. 42), negated by
 //      default so that a convex fluid region has kappa > 0.
 #pragma once
-#include "plic_solvers.cuh"
+#include "plic_polygon.cuh"
 
 namespace plic {
 

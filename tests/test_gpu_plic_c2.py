@@ -87,10 +87,10 @@ def test_full_size_sampled(dev, orc):
     d0 = plic.offset(*t, method="sz_opt", precision="fp32p")
     Vb = plic.volume(t[0], t[1], t[2], d0)
     # the fused round trip (the bench's step) gives the same d0 and a V0_rt
-    # within rounding of plic_volume's
+    # within the rounding of two FP32 evaluations of plic_volume's
     d0f, vrt = plic.offset_roundtrip(*t, method="sz_opt", precision="fp32p")
     assert torch.equal(d0f, d0)
-    assert (vrt - Vb).abs().max().item() <= 3e-7
+    assert (vrt - Vb).abs().max().item() <= 5e-7
     assert (vrt - t[3]).abs().max().item() <= 1e-6
     del d0f, vrt
     idx = np.concatenate([s[0] for s in samp])
