@@ -188,7 +188,7 @@ plic_status vof_interface_compact(const float *phi, int nx, int ny, int nz, int3
  * streams, other host threads) race and must be serialised by the caller.
  * The scratch needs no clearing between calls.  Other arguments and the
  * output are as for vof_interface_compact. */
-#define PLIC_NOALLOC_MAX_CELLS 268435456LL  /* 2^28 cells: at most 32769 tiles, 128 KiB */
+#define PLIC_NOALLOC_MAX_CELLS 268435456LL  /* 2^28 cells: at most 65537 tiles, 256 KiB */
 plic_status vof_interface_compact_noalloc(const float *phi, int nx, int ny, int nz,
                                           int32_t *idx, int64_t idx_capacity,
                                           int64_t *d_count, void *stream);

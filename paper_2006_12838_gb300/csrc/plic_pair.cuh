@@ -26,17 +26,6 @@ __device__ __forceinline__ f2 fmax0(f2 a) { return make_float2(fmaxf(a.x, 0.0f),
 
 struct b2 { bool x, y; };
 __device__ __forceinline__ f2 sel(b2 c, f2 a, f2 b) { return make_float2(c.x ? a.x : b.x, c.y ? a.y : b.y); }
-
-// Select on the FMA pipe: a 0/1 mask m (and 1 - m) turns a choice between
-// FINITE values into m a + (1 - m) b, which is exact (one product is zero,
-// the other exact).  Used where one flag picks several values, so that the
-// per-lane selects do not all land on the ALU pipe.
-struct msk { f2 m, mc; };
-__device__ __forceinline__ msk mask(b2 c) {
-    const f2 m = make_float2(c.x ? 1.0f : 0.0f, c.y ? 1.0f : 0.0f);
-    return {m, __ffma2_rn(m, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f))};
-}
-__device__ __forceinline__ f2 msel(const msk& k, f2 a, f2 b) { return __ffma2_rn(k.m, a, __fmul2_rn(k.mc, b)); }
 __device__ __forceinline__ b2 lt(f2 a, f2 b) { return {a.x < b.x, a.y < b.y}; }
 __device__ __forceinline__ b2 le(f2 a, f2 b) { return {a.x <= b.x, a.y <= b.y}; }
 
@@ -75,10 +64,10 @@ __device__ __forceinline__ f2 sqrtp(f2 x) {
 // optimised-SZ argument is never negative: it is 1.5 n1 n2 (n1+n2-2 n3 V)/t^3
 // with n1+n2 > 2 n3 V outside case (5), or 0.75 n1 n2 n3 (1-2V)/t^3 with V <= 1/2.
 __device__ __forceinline__ f2 asin01(f2 a) {
-    const msk big = mask(lt(mk(0.5f), a));
+    const b2 big = lt(mk(0.5f), a);
     const f2 zb = mul(mk(0.5f), sub(mk(1.0f), a));
-    const f2 z = msel(big, zb, mul(a, a));
-    const f2 s = msel(big, sqrtp(z), a);
+    const f2 z = sel(big, zb, mul(a, a));
+    const f2 s = sel(big, sqrtp(z), a);
     f2 p = mk(0.011551800896139705f);
     p = fma(p, z, mk(0.01396484375f));
     p = fma(p, z, mk(0.017352764423076924f));
@@ -88,7 +77,7 @@ __device__ __forceinline__ f2 asin01(f2 a) {
     p = fma(p, z, mk(0.075f));
     p = fma(p, z, mk(0.16666666666666666f));
     p = fma(mul(s, z), p, s);
-    return msel(big, fma(mk(-2.0f), p, mk(1.5707963267948966f)), p);
+    return sel(big, fma(mk(-2.0f), p, mk(1.5707963267948966f)), p);
 }
 
 // One Newton step on the cubic of Eq. 10 for cases (3)/(4) (d >= n2, n1 > 0):
@@ -132,10 +121,9 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3) {
     const f2 d32 = sub(n3, n2);
     const f2 t24 = mul(mk(0.25f), fma(n1, fma(mk(2.0f), add(n2, n3), make_float2(-n1.x, -n1.y)),
                                      make_float2(-d32.x * d32.x, -d32.y * d32.y)));
-    const msk k3 = mask(c3);
-    const f2 q = msel(k3, q3, q4);
-    const f2 t2 = msel(k3, add(n1n2, n1n2), t24);
-    const f2 c = msel(k3, n12, mk(0.5f));
+    const f2 q = sel(c3, q3, q4);
+    const f2 t2 = sel(c3, add(n1n2, n1n2), t24);
+    const f2 c = sel(c3, n12, mk(0.5f));
     const f2 rt = rsqrt(t2);
     const f2 t = mul(t2, rt);
     f2 arg = mul(q, mul(rt, mul(rt, rt)));

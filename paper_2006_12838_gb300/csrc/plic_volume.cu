@@ -47,7 +47,7 @@ template <typename T, int MODE>
 __device__ __forceinline__ void adjoint_cell(T nx, T ny, T nz, T d0, T g, T& gs, T& gx, T& gy,
                                              T& gz) {
     T A, cx, cy, cz;
-    const bool ok = cut_polygon<T>(nx, ny, nz, d0, A, cx, cy, cz);
+    const bool ok = area_centroid<T>(nx, ny, nz, d0, A, cx, cy, cz);
     if (MODE == 0) {
         gs = ok ? Fm<T>::div_(g, A) : (g == T(0) ? T(0) : copysign(T(INFINITY), g));
         gx = g * cx; gy = g * cy; gz = g * cz;

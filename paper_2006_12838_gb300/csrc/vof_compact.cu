@@ -3,7 +3,7 @@
 //
 // Three launches, no atomics and no inter-block waiting, so the list is in
 // ascending cell order and identical run to run.  A tile is a run of whole
-// x-rows (about 16384 cells):
+// x-rows (about 8192 cells):
 //   1. k_compact_count : each block counts the interface cells of its tile.
 //   2. k_compact_scan  : one block turns the per-tile counts into exclusive
 //                        offsets (in place) and writes the total to *d_count.
@@ -22,8 +22,8 @@ namespace plic {
 
 constexpr int CT_THREADS = 256;
 constexpr int CT_WARPS = CT_THREADS / 32;
-constexpr int CT_TILE = 16384;           // cells per tile (whole x-rows)
-constexpr int CT_MAX_ROWS = 4096;        // rows per tile at most (tiles >= 8192 cells for nx >= 3)
+constexpr int CT_TILE = 8192;            // cells per tile (whole x-rows)
+constexpr int CT_MAX_ROWS = 4096;        // rows per tile at most (CT_TILE / 3 for nx >= 3)
 constexpr int CT_MAX_WORDS = 2048;       // ballot words per tile kept in shared memory
 
 // Rows (x-lines) per tile: as many whole rows as fit in CT_TILE cells.
@@ -111,7 +111,8 @@ __device__ __forceinline__ float4 ld_row4(const float* __restrict__ row, bool ok
 // by the compare work).
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
-                int* __restrict__ tile_count, unsigned* __restrict__ bits, int vec) {
+                int* __restrict__ tile_count, unsigned* __restrict__ bits,
+                int* __restrict__ row_count, int vec) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpr = (nx + 31) >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
@@ -129,31 +130,42 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
             const float* rowb = phi + (hasb ? rb : ra) * nx;
             unsigned* ba = bits ? bits + ra * wpr : nullptr;
             unsigned* bb = (bits && hasb) ? bits + rb * wpr : nullptr;
+            int ca = 0, cb = 0;
             for (int x0 = 0; x0 < nx; x0 += 256) {
                 const int xa = x0 + 4 * lane, xb = xa + 128;
                 const float4 a0 = ld_row4(rowa, oka, xa, nx), a1 = ld_row4(rowa, oka, xb, nx);
                 const float4 b0 = ld_row4(rowb, okb, xa, nx), b1 = ld_row4(rowb, okb, xb, nx);
                 const unsigned ma0 = oka ? nib4(a0, xa, nx) : 0u, ma1 = oka ? nib4(a1, xb, nx) : 0u;
                 const unsigned mb0 = okb ? nib4(b0, xa, nx) : 0u, mb1 = okb ? nib4(b1, xb, nx) : 0u;
-                cnt += __popc(ma0) + __popc(ma1) + __popc(mb0) + __popc(mb1);
+                ca += __popc(ma0) + __popc(ma1);
+                cb += __popc(mb0) + __popc(mb1);
                 emit_nibbles(ma0, x0, nx, [&](int w, unsigned b) { if (ba) ba[w] = b; });
                 emit_nibbles(ma1, x0 + 128, nx, [&](int w, unsigned b) { if (ba) ba[w] = b; });
                 emit_nibbles(mb0, x0, nx, [&](int w, unsigned b) { if (bb) bb[w] = b; });
                 emit_nibbles(mb1, x0 + 128, nx, [&](int w, unsigned b) { if (bb) bb[w] = b; });
             }
+            ca = __reduce_add_sync(0xffffffffu, ca);
+            cb = __reduce_add_sync(0xffffffffu, cb);
+            if (row_count && lane == 0) {
+                row_count[ra] = ca;
+                if (hasb) row_count[rb] = cb;
+            }
+            cnt += ca + cb;
         }
-        cnt = __reduce_add_sync(0xffffffffu, cnt);
     } else {
         for (int64_t r = rbeg + warp; r < rend; r += CT_WARPS) {
             unsigned* rb = bits ? bits + r * wpr : nullptr;
             if (!interior(r)) {
                 if (rb)
                     for (int w = lane; w < wpr; w += 32) rb[w] = 0u;
+                if (row_count && lane == 0) row_count[r] = 0;
                 continue;
             }
-            cnt += row_bits(phi + r * nx, nx, false, [&](int w, unsigned b) {
+            const int c = row_bits(phi + r * nx, nx, false, [&](int w, unsigned b) {
                 if (rb) rb[w] = b;
             });
+            if (row_count && lane == 0) row_count[r] = c;
+            cnt += c;
         }
     }
     __shared__ int ws[CT_WARPS];
@@ -217,7 +229,7 @@ k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
                 const int* __restrict__ tile_offset, const unsigned* __restrict__ bits,
-                int32_t* __restrict__ idx, int64_t cap, int vec) {
+                const int* __restrict__ row_count, int32_t* __restrict__ idx, int64_t cap, int vec) {
     __shared__ unsigned bal[CT_MAX_WORDS];
     __shared__ int rowoff[CT_MAX_ROWS + 1];
     __shared__ int rowcnt[CT_MAX_ROWS];
@@ -226,8 +238,13 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
     const int nr = (int)(rend - rbeg);
     const int wpr = (nx + 31) >> 5;                 // words per row
-    const bool in_smem = (int64_t)nr * wpr <= CT_MAX_WORDS;
-    for (int k = warp; k < nr; k += CT_WARPS) {
+    // with pass 1's row counts the rows need not be recounted here, and their
+    // bits are read from global memory only for the non-empty rows
+    const bool in_smem = !row_count && (int64_t)nr * wpr <= CT_MAX_WORDS;
+    if (row_count) {
+        for (int k = threadIdx.x; k < nr; k += CT_THREADS) rowoff[k] = rowcnt[k] = __ldg(row_count + rbeg + k);
+    }
+    for (int k = warp; k < (row_count ? 0 : nr); k += CT_WARPS) {
         const int64_t r = rbeg + k;
         int cnt = 0;
         if (bits) {
@@ -333,10 +350,12 @@ extern "C" size_t plic_workspace_bytes(int op, int64_t arg) {
             // field of arg cells has at most 2 arg / CT_TILE + 1 tiles; interface
             // bits: one word per 32 cells of each row, at most arg / 16 words
             // for rows of >= 32 cells (shorter rows keep no bits)
+            // row counts: one int per row of >= 32 cells, at most arg / 32 + 1
             const int64_t t = (arg + plic::CT_TILE - 1) / plic::CT_TILE * 2 + 1;
             const size_t a = ((size_t)t * sizeof(int) + 255) / 256 * 256;
             const size_t b = ((size_t)(arg / 16 + 1) * sizeof(unsigned) + 255) / 256 * 256;
-            return a + b;
+            const size_t c = ((size_t)(arg / 32 + 1) * sizeof(int) + 255) / 256 * 256;
+            return a + b + c;
         }
         case PLIC_WS_BATCHED: {
             // descriptor table + per-field cell prefix + the ticket counter
@@ -372,21 +391,26 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
     if (tile_bytes > ws_bytes) return PLIC_ERR_ARG;
     int* tiles = reinterpret_cast<int*>(workspace);
     const int64_t words = rows * ((nx + 31) / 32);
+    const size_t bits_bytes = ((size_t)words * sizeof(unsigned) + 255) / 256 * 256;
     unsigned* bits = nullptr;
-    if (nx >= 32 && tile_bytes + (size_t)words * sizeof(unsigned) <= ws_bytes)
+    int* rowc = nullptr;
+    if (nx >= 32 && tile_bytes + bits_bytes + (size_t)rows * sizeof(int) <= ws_bytes) {
         bits = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + tile_bytes);
+        rowc = reinterpret_cast<int*>(reinterpret_cast<char*>(workspace) + tile_bytes + bits_bytes);
+    }
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
-    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, vec);
+    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, rowc,
+                                                        vec);
     k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
-    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, idx,
-                                                        idx_capacity, vec);
+    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, rowc,
+                                                        idx, idx_capacity, vec);
     return check_launch("vof_interface_compact");
 }
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant.  The per-tile scratch of the three passes lives in
 // a file-scope device array instead of a caller-provided workspace.  Every
-// GPU that loads the library holds these 128 KiB until the process exits.
+// GPU that loads the library holds these 256 KiB until the process exits.
 // ---------------------------------------------------------------------------
 namespace plic {
 
@@ -457,9 +481,10 @@ extern "C" plic_status vof_interface_compact_noalloc(const float* phi, int nx, i
     }
     // the built-in scratch holds the tile counts only; pass 3 re-reads the field
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
-    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr, vec);
+    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
+                                                        nullptr, vec);
     k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
-    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr, idx,
-                                                        idx_capacity, vec);
+    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
+                                                        nullptr, idx, idx_capacity, vec);
     return check_launch("vof_interface_compact_noalloc");
 }
