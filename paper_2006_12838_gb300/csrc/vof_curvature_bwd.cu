@@ -176,14 +176,14 @@ k_vof_curvature_vjp(const float* __restrict__ phi, int nx, int ny,
                 d00b -= zb;
                 // d0_i = d0(phi_i, n)
                 float Ai, cx, cy, cz;
-                if (cut_polygon<float>(nx_, ny_, nz_, d0i, Ai, cx, cy, cz)) {
+                if (area_centroid<float>(nx_, ny_, nz_, d0i, Ai, cx, cy, cz)) {
                     s_g[i][t] += zb / Ai;
                     nbx += zb * cx; nby += zb * cy; nbz += zb * cz;
                 }
             }
             {
                 float A0, cx, cy, cz;
-                if (cut_polygon<float>(nx_, ny_, nz_, d00, A0, cx, cy, cz)) {
+                if (area_centroid<float>(nx_, ny_, nz_, d00, A0, cx, cy, cz)) {
                     s_g[0][t] += d00b / A0;
                     nbx += d00b * cx; nby += d00b * cy; nbz += d00b * cz;
                 }

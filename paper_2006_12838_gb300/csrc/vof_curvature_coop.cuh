@@ -172,7 +172,7 @@ __device__ __forceinline__ void co_group_cell(const CoCell& cell, int g, uint32_
     float c0x = 0.0f, c0y = 0.0f, c0z = 0.0f;
     if (centroid) {
         float A;
-        if (g == 0 && ok) cut_polygon<float>(nx_, ny_, nz_, d00, A, c0x, c0y, c0z);
+        if (g == 0 && ok) area_centroid<float>(nx_, ny_, nz_, d00, A, c0x, c0y, c0z);
         c0x = __shfl_sync(0xffffffffu, c0x, leader);
         c0y = __shfl_sync(0xffffffffu, c0y, leader);
         c0z = __shfl_sync(0xffffffffu, c0z, leader);
@@ -190,7 +190,7 @@ __device__ __forceinline__ void co_group_cell(const CoCell& cell, int g, uint32_
             float qx = (float)ex, qy = (float)ey, qz = (float)ez, z;
             if (centroid) {
                 float A, cx, cy, cz;
-                cut_polygon<float>(nx_, ny_, nz_, d0s[j], A, cx, cy, cz);
+                area_centroid<float>(nx_, ny_, nz_, d0s[j], A, cx, cy, cz);
                 qx += cx - c0x; qy += cy - c0y; qz += cz - c0z;
                 z = qx * nx_ + qy * ny_ + qz * nz_;
             } else {

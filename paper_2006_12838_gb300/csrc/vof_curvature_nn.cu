@@ -59,7 +59,7 @@ k_vof_curvature_nn(const float* __restrict__ phi, int nx, int ny, int nz,
         float c0x = 0.0f, c0y = 0.0f, c0z = 0.0f;
         if (centroid) {
             float A;
-            cut_polygon<float>(nx_, ny_, nz_, d00, A, c0x, c0y, c0z);
+            area_centroid<float>(nx_, ny_, nz_, d00, A, c0x, c0y, c0z);
         }
         float M[15], bv[5];
 #pragma unroll
@@ -86,7 +86,7 @@ k_vof_curvature_nn(const float* __restrict__ phi, int nx, int ny, int nz,
             float qx = (float)ex, qy = (float)ey, qz = (float)ez;
             if (centroid) {
                 float A, cx, cy, cz;
-                cut_polygon<float>(mx, my, mz, d0i, A, cx, cy, cz);
+                area_centroid<float>(mx, my, mz, d0i, A, cx, cy, cz);
                 qx += cx - c0x; qy += cy - c0y; qz += cz - c0z;
             } else {
                 qx += d0i * mx - d00 * nx_;

@@ -143,3 +143,40 @@ def test_unsupported_combinations(dev, field):
     kap = torch.empty(idx.size, device=dev)
     with pytest.raises(plic.PlicError):
         plic.curvature_batched([(phid, it, idx.size, kap)], flags=128)
+
+
+def test_device_count_paths(dev, orc, field):
+    # every list-driven entry point follows vof_interface_compact through the
+    # device-side count, without a host round trip: a list buffer longer than
+    # the count must give the same results as the exact list
+    p, idx = field
+    phid = torch.tensor(p, device=dev)
+    buf, cnt = plic.interface_compact(phid)
+    k = int(cnt.item())
+    assert k == idx.size
+    cap = buf.numel()
+    it = buf[:k].contiguous()
+    for flags in (0, 64, 128, 128 | 64):
+        want = plic.curvature(phid, it, flags=flags)
+        got = plic.curvature(phid, buf, n_iface=cap, count=cnt, flags=flags)
+        assert torch.equal(got[:k], want)
+        dp = plic.laplace_pressure(phid, buf, 0.5, n_iface=cap, count=cnt, flags=flags)
+        assert torch.equal(dp[:k], want * 1.0)
+    n_want = plic.normals(phid, it, flags=64)
+    n_got = plic.normals(phid, buf, n_iface=cap, count=cnt, flags=64)
+    assert torch.equal(n_got[:, :k], n_want)
+
+
+def test_batched_with_cm_normal(dev, orc):
+    fields = synth.batched_fields(seed=5, n_fields=6, device=dev, max_fields=6)
+    args, refs = [], []
+    for phi, _ in fields:
+        idx, cnt = plic.interface_compact(phi)
+        k = int(cnt.item())
+        it = idx[:k].contiguous()
+        args.append((phi, it, k, torch.empty(max(k, 1), device=dev)))
+        refs.append(plic.curvature(phi, it, flags=64) if k else None)
+    plic.curvature_batched(args, flags=64)
+    for (phi, it, k, kap), ref in zip(args, refs):
+        if k:
+            assert torch.equal(kap[:k], ref)
