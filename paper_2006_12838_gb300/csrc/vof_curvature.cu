@@ -17,8 +17,8 @@ constexpr int CO_THREADS = 128;       // 4 warps per block
 constexpr int CO_WARPS = CO_THREADS / 32;
 
 // Single field: warp w of the grid takes batches of `batch` list entries (32,
-// or 16 / 8 when the list is too short to give every resident warp slot a
-// batch of 32) in a grid-stride loop.
+// or 16 / 8 / 4 when the list is too short to give every resident warp slot
+// two batches of 32) in a grid-stride loop.
 template <int METHOD, int FIT>
 __global__ void __launch_bounds__(CO_THREADS)
 k_vof_curvature(const float* __restrict__ phi, int nx, int ny, const int32_t* __restrict__ idx,
@@ -154,11 +154,14 @@ static plic_status curvature_entry(const float* phi, int nx, int ny, int nz, con
                                    fit_mode(flags), scale, stream, who);
     const void* k = select(false, m, fit_mode(flags));
     const int threads = CO_THREADS;
-    // batches of 32 entries per warp, smaller ones when 32 would leave resident
-    // warp slots idle; at most one resident wave
+    // batches of 32 entries per warp, smaller ones (down to 4) while the list
+    // would give fewer than two batches per resident warp slot: the group
+    // phase is latency bound, so short lists run faster spread thin (measured:
+    // 56 478 cells 34 us with batches of 8 against 39 us with 16 or 32; 5 538
+    // cells 9 us with 4 against 13 us with 8); at most one resident wave
     const int64_t slots = (int64_t)sm_count() * blocks_per_sm(k, threads, 0) * CO_WARPS;
     int batch = CO_BATCH;
-    while (batch > 8 && (n_iface + batch - 1) / batch < slots) batch >>= 1;
+    while (batch > 4 && (n_iface + batch - 1) / batch < 2 * slots) batch >>= 1;
     const int grid = stride_grid(k, threads, (n_iface + batch - 1) / batch * 32);
     void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&idx, (void*)&n_iface,
                     (void*)&d_n_iface, (void*)&out, (void*)&flags, (void*)&scale, (void*)&batch};

@@ -175,6 +175,35 @@ struct Ldlt {
     }
 };
 
+// Adaptive factorisation (the FIT_AUTO policy): LDL^T in FP32, repeated in
+// FP64 when the FP32 pivots show an ill-conditioned matrix (smallest pivot
+// below 1e-2 of the largest, or a dimension reduced by the FP32 pivots).
+// Same interface as Ldlt: factor(), solve(), dim.
+struct LdltAuto {
+    Ldlt<FIT_FP32> f;
+    Ldlt<FIT_FP64> w;
+    bool wide;
+    int dim;
+    __device__ __forceinline__ void factor(const float* Mf, int m) {
+        f.factor(Mf, m);
+        const int want = m < 5 ? m : 5;
+        float dmin = 3.4e38f, dmax = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+            if (j < f.dim) { dmin = fminf(dmin, f.D[j]); dmax = fmaxf(dmax, f.D[j]); }
+        wide = !(f.dim == want && dmin > 1e-2f * dmax);
+        dim = f.dim;
+        if (wide) {
+            w.factor(Mf, m);
+            dim = w.dim;
+        }
+    }
+    __device__ __forceinline__ void solve(const float* bf, float x[5]) const {
+        if (wide) w.solve(bf, x);
+        else f.solve(bf, x);
+    }
+};
+
 template <int FIT>
 __device__ __forceinline__ int fit_solve(const float* Mf, const float* bf, int m, float x[5]) {
     Ldlt<FIT> f;

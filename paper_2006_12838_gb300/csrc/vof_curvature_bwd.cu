@@ -20,6 +20,8 @@
 // sums, for every field cell j, the entries of the (at most 27) interface cells
 // whose stencil contains j, in a fixed order -- deterministic, no atomics.
 // Only the foot-point variant (Eq. 36) is differentiated.
+#include <type_traits>
+
 #include "host_common.h"
 #include "vof_curvature.cuh"
 
@@ -118,7 +120,7 @@ k_vof_curvature_vjp(const float* __restrict__ phi, int nx, int ny,
                 ++m;
             }
         }
-        Ldlt<FIT> fac;
+        typename std::conditional<FIT == FIT_AUTO, LdltAuto, Ldlt<FIT>>::type fac;
         float p[5] = {0, 0, 0, 0, 0};
         if (!zero) {
             fac.factor(M, m);
@@ -250,16 +252,18 @@ k_curv_gather(const int32_t* __restrict__ idx, int64_t n, const int64_t* __restr
         const int64_t dn = *d_n;
         lim = dn < n ? dn : n;
     }
-    const int64_t nxy = (int64_t)nx * ny;
+    // fields hold < 2^31 cells (checked by the entry point): 32-bit index math
+    const int nxy = nx * ny;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < lim * 27;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = t / 27;
-        const int o = (int)(t - k * 27);
+        const int k = (int)(t / 27);
+        const int o = (int)(t - (int64_t)k * 27);
         int ex, ey, ez;
         e_of(o, ex, ey, ez);
-        const int64_t c = __ldg(idx + k);
-        const int64_t j = c + ex + (int64_t)ey * nx + (int64_t)ez * nxy;
-        const int z = (int)(j / nxy), y = (int)((j / nx) % ny), x = (int)(j % nx);
+        const int c = __ldg(idx + k);
+        const int cz = c / nxy, cr = c - cz * nxy, cy = cr / nx, cx = cr - cy * nx;
+        const int x = cx + ex, y = cy + ey, z = cz + ez;
+        const int j = c + ex + ey * nx + ez * nxy;
         float acc = 0.0f;
         int32_t first = 0x7fffffff;
 #pragma unroll
@@ -268,13 +272,13 @@ k_curv_gather(const int32_t* __restrict__ idx, int64_t n, const int64_t* __restr
             e_of(q, fx, fy, fz);
             const int sx = x - fx, sy = y - fy, sz = z - fz;
             if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz) continue;
-            const int32_t sl = __ldg(slot + (j - fx - (int64_t)fy * nx - (int64_t)fz * nxy));
+            const int32_t sl = __ldg(slot + (j - fx - fy * nx - fz * nxy));
             if (sl >= 0) {
                 acc += __ldg(contrib + (int64_t)sl * 27 + q);
                 first = sl < first ? sl : first;
             }
         }
-        if (first == (int32_t)k) g_phi[j] = acc;
+        if (first == k) g_phi[j] = acc;
     }
 }
 
@@ -283,7 +287,8 @@ static const void* pick_vjp(int fit) {
     switch (fit) {
         case FIT_FP32: return reinterpret_cast<const void*>(&k_vof_curvature_vjp<METHOD, FIT_FP32>);
         case FIT_DF32: return reinterpret_cast<const void*>(&k_vof_curvature_vjp<METHOD, FIT_DF32>);
-        default: return reinterpret_cast<const void*>(&k_vof_curvature_vjp<METHOD, FIT_FP64>);
+        case FIT_FP64: return reinterpret_cast<const void*>(&k_vof_curvature_vjp<METHOD, FIT_FP64>);
+        default: return reinterpret_cast<const void*>(&k_vof_curvature_vjp<METHOD, FIT_AUTO>);
     }
 }
 
@@ -325,8 +330,9 @@ extern "C" plic_status vof_curvature_backward(const float* phi, int nx, int ny, 
     cudaError_t e = cudaMemsetAsync(slot, 0xff, (size_t)cells * sizeof(int32_t), s);
     if (e != cudaSuccess) { set_last_error("vof_curvature_backward", e); return PLIC_ERR_CUDA; }
     if (n_iface > 0) {
-        // the adaptive default differentiates with the FP64 factorisation
-        const int fit = (flags & PLIC_FLAG_FIT_DF32) ? FIT_DF32 : (flags & PLIC_FLAG_FIT_FP32) ? FIT_FP32 : FIT_FP64;
+        // the same fit policy as the forward call: adaptive unless a FIT flag is given
+        const int fit = (flags & PLIC_FLAG_FIT_DF32) ? FIT_DF32 : (flags & PLIC_FLAG_FIT_FP32) ? FIT_FP32
+                      : (flags & PLIC_FLAG_FIT_FP64) ? FIT_FP64 : FIT_AUTO;
         const void* k = nullptr;
         switch (m) {
             case PLIC_ANALYTIC: k = pick_vjp<M_ANALYTIC>(fit); break;
