@@ -227,11 +227,12 @@ def section_fp64(dev, pk, steps, cells):
     out = {}
     d0 = torch.empty_like(t64[0])
     for m in plic.METHODS:
-        sec = timed(lambda: plic.offset(*t64, method=m, precision="fp64", out=d0), steps, 1, s)
-        gbs = 40.0 * cells * steps / sec / 1e9
-        out["offset_%s_fp64" % m] = {"g_solves_s": cells * steps / sec / 1e9,
-                                     "ms": sec / steps * 1e3, "hbm_gbs": gbs,
-                                     "hbm_frac": frac(gbs, pk["hbm_gbs"]), "cells": cells}
+        for prec in ("fp64", "fp64r"):
+            sec = timed(lambda: plic.offset(*t64, method=m, precision=prec, out=d0), steps, 1, s)
+            gbs = 40.0 * cells * steps / sec / 1e9
+            out["offset_%s_%s" % (m, prec)] = {"g_solves_s": cells * steps / sec / 1e9,
+                                               "ms": sec / steps * 1e3, "hbm_gbs": gbs,
+                                               "hbm_frac": frac(gbs, pk["hbm_gbs"]), "cells": cells}
     del t64
     torch.cuda.empty_cache()
     return out
@@ -526,6 +527,14 @@ def run_case(args):
             idx, cnt = plic.interface_compact(phi)
             k = int(cnt.item())
             plic.curvature(phi, idx[:k].contiguous())
+    elif args.case == "curv_bwd":
+        phi, w = synth.adjoint_field(seed=4, device=dev)
+        idx, cnt = plic.interface_compact(phi)
+        k = int(cnt.item())
+        it = idx[:k].contiguous()
+        g = torch.ones(k, device=dev)
+        for _ in range(args.steps):
+            plic.curvature_backward(phi, it, g)
     elif args.case == "batched":
         fields = synth.batched_fields(seed=5, n_fields=16, device=dev)
         a = []
@@ -551,7 +560,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default=None,
                     help="profiling case: run only one kernel on --cells cells "
-                         "(offset | roundtrip | volume | offset_fp64 | curvature | batched)")
+                         "(offset | roundtrip | volume | offset_fp64 | curvature | curv_bwd | "
+                         "batched)")
     ap.add_argument("--cells", type=int, default=1 << 24)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -175,18 +175,23 @@ struct Ldlt {
     }
 };
 
-// Adaptive factorisation (the FIT_AUTO policy): LDL^T in FP32, repeated in
-// FP64 when the FP32 pivots show an ill-conditioned matrix (smallest pivot
-// below 1e-2 of the largest, or a dimension reduced by the FP32 pivots).
-// Same interface as Ldlt: factor(), solve(), dim.
+// Adaptive factorisation (the FIT_AUTO policy): LDL^T in FP32, replaced by an
+// FP64 factorisation when the FP32 pivots show an ill-conditioned matrix
+// (smallest pivot below 1e-2 of the largest, or a dimension reduced by the
+// FP32 pivots).  Same interface as Ldlt (factor(), solve(), dim).  The FP64
+// factors are not kept: the rare wide solve refactorises from Mf, which must
+// stay valid between factor() and the solves; this keeps the FP64 factors out
+// of the registers of the common path.
 struct LdltAuto {
     Ldlt<FIT_FP32> f;
-    Ldlt<FIT_FP64> w;
+    const float* Mf;
+    int m, dim;
     bool wide;
-    int dim;
-    __device__ __forceinline__ void factor(const float* Mf, int m) {
-        f.factor(Mf, m);
-        const int want = m < 5 ? m : 5;
+    __device__ __forceinline__ void factor(const float* M, int mm) {
+        Mf = M;
+        m = mm;
+        f.factor(M, mm);
+        const int want = mm < 5 ? mm : 5;
         float dmin = 3.4e38f, dmax = 0.0f;
 #pragma unroll
         for (int j = 0; j < 5; ++j)
@@ -194,13 +199,19 @@ struct LdltAuto {
         wide = !(f.dim == want && dmin > 1e-2f * dmax);
         dim = f.dim;
         if (wide) {
-            w.factor(Mf, m);
+            Ldlt<FIT_FP64> w;
+            w.factor(M, mm);
             dim = w.dim;
         }
     }
     __device__ __forceinline__ void solve(const float* bf, float x[5]) const {
-        if (wide) w.solve(bf, x);
-        else f.solve(bf, x);
+        if (wide) {
+            Ldlt<FIT_FP64> w;
+            w.factor(Mf, m);
+            w.solve(bf, x);
+        } else {
+            f.solve(bf, x);
+        }
     }
 };
 
