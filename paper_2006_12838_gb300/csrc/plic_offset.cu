@@ -77,24 +77,11 @@ k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict_
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int bad = 0;
     const int64_t nvec = vec_ok ? n / 4 : 0;
-    // software pipeline: the next step's 64 bytes are in flight while this
-    // step computes, doubling the bytes each thread keeps outstanding
-    float4 a, b, c, v;
-    if (tid < nvec) {
-        a = __ldcs(reinterpret_cast<const float4*>(nx) + tid);
-        b = __ldcs(reinterpret_cast<const float4*>(ny) + tid);
-        c = __ldcs(reinterpret_cast<const float4*>(nz) + tid);
-        v = __ldcs(reinterpret_cast<const float4*>(V0) + tid);
-    }
     for (int64_t i = tid; i < nvec; i += stride) {
-        const int64_t j = i + stride;
-        float4 a2 = a, b2 = b, c2 = c, v2 = v;
-        if (j < nvec) {
-            a2 = __ldcs(reinterpret_cast<const float4*>(nx) + j);
-            b2 = __ldcs(reinterpret_cast<const float4*>(ny) + j);
-            c2 = __ldcs(reinterpret_cast<const float4*>(nz) + j);
-            v2 = __ldcs(reinterpret_cast<const float4*>(V0) + j);
-        }
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(nx) + i);
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(ny) + i);
+        const float4 c = __ldcs(reinterpret_cast<const float4*>(nz) + i);
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(V0) + i);
         float2 w0, w1;
         const float2 r0 = p2::offset_sz_opt<POLISH, ROUNDTRIP>(
             make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y), make_float2(v.x, v.y),
@@ -104,7 +91,6 @@ k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict_
             bad, &w1);
         __stcs(reinterpret_cast<float4*>(d0) + i, make_float4(r0.x, r0.y, r1.x, r1.y));
         if (ROUNDTRIP) __stcs(reinterpret_cast<float4*>(vrt) + i, make_float4(w0.x, w0.y, w1.x, w1.y));
-        a = a2; b = b2; c = c2; v = v2;
     }
     for (int64_t i = nvec * 4 + tid; i < n; i += stride) {
         int bad2 = 0;

@@ -35,18 +35,16 @@ __device__ __forceinline__ f2 sqrt_(f2 a) {
     return make_float2(Fm<float>::sqrt_(a.x), Fm<float>::sqrt_(a.y));
 }
 
-// cube root of x >= 0: MUFU exp2(log2(x)/3) and one Newton step (see
-// Fm<float>).  1e-30 is added to x (its cube root, 1e-10, is far below the
-// FP32 resolution of an offset), which removes the zero/denormal branches;
-// the add runs on the paired FMA pipe where a max would take the ALU pipe.
+// cube root of x >= 0 as MUFU exp2(log2(x)/3): relative error below 6e-6
+// even for x = 1e-30 (the MUFU log2's absolute error, times |log2 x|/3), and
+// the cube root is only the case-(1) offset d1 <= n1, whose absolute error
+// then stays below 2e-7 -- no Newton step.  1e-30 is added to x (its cube root,
+// 1e-10, is far below the FP32 resolution of an offset), which removes the
+// zero/denormal branches on the FMA pipe.
 __device__ __forceinline__ f2 cbrt_(f2 x) {
     x = add(x, mk(1e-30f));
-    f2 r = make_float2(Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.x) * (1.0f / 3.0f)),
+    return make_float2(Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.x) * (1.0f / 3.0f)),
                        Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.y) * (1.0f / 3.0f)));
-    const f2 r2 = mul(r, r);
-    const f2 res = fma(r2, r, make_float2(-x.x, -x.y));           // r^3 - x
-    const f2 inv = rcp(mul(mk(3.0f), r2));
-    return fma(make_float2(-res.x, -res.y), inv, r);
 }
 
 // sqrt of x >= 0 as x rsqrt(x) with 1e-30 added (no zero branch).  Both
@@ -59,23 +57,22 @@ __device__ __forceinline__ f2 sqrtp(f2 x) {
     return mul(x, rsqrt(x));
 }
 
-// arcsine on [0, 1] by the series of fast_asinf (Maclaurin series of arcsin
-// to s^17 on s <= 1/2, half-angle reduction above), two lanes at once.  The
-// optimised-SZ argument is never negative: it is 1.5 n1 n2 (n1+n2-2 n3 V)/t^3
+// arcsine on [0, 1], two lanes at once: asin(s) = s + s^3 P(s^2) on
+// s <= 1/2 with P a degree-4 least-squares fit to (asin(s) - s)/s^3 on
+// [0, 1/4] (relative error below 2e-8, under the FP32 rounding), and the
+// half-angle reduction asin(a) = pi/2 - 2 asin(sqrt((1 - a)/2)) above 1/2.
+// The optimised-SZ argument is never negative: it is 1.5 n1 n2 (n1+n2-2 n3 V)/t^3
 // with n1+n2 > 2 n3 V outside case (5), or 0.75 n1 n2 n3 (1-2V)/t^3 with V <= 1/2.
 __device__ __forceinline__ f2 asin01(f2 a) {
     const b2 big = lt(mk(0.5f), a);
     const f2 zb = mul(mk(0.5f), sub(mk(1.0f), a));
     const f2 z = sel(big, zb, mul(a, a));
     const f2 s = sel(big, sqrtp(z), a);
-    f2 p = mk(0.011551800896139705f);
-    p = fma(p, z, mk(0.01396484375f));
-    p = fma(p, z, mk(0.017352764423076924f));
-    p = fma(p, z, mk(0.022372159090909092f));
-    p = fma(p, z, mk(0.030381944444444444f));
-    p = fma(p, z, mk(0.044642857142857144f));
-    p = fma(p, z, mk(0.075f));
-    p = fma(p, z, mk(0.16666666666666666f));
+    f2 p = mk(0.038206491619348526f);
+    p = fma(p, z, mk(0.026494324207305908f));
+    p = fma(p, z, mk(0.045010678470134735f));
+    p = fma(p, z, mk(0.07498809695243835f));
+    p = fma(p, z, mk(0.16666673123836517f));
     p = fma(mul(s, z), p, s);
     return sel(big, fma(mk(-2.0f), p, mk(1.5707963267948966f)), p);
 }

@@ -438,10 +438,10 @@ __device__ __forceinline__ T offset_cell(T nx, T ny, T nz, T V0, int& bad) {
 // in FP64, so the reduced volume V = min(V0, 1 - V0) keeps its full relative
 // precision (V0 = 1 - 1e-9 rounded to float first would give V = 0); the
 // method's FP32 solver then runs on the reduced problem rounded to float, and
-// two Newton steps of polish() finish it on the FP64 problem.  The FP32 root is
-// within ~1e-7 relative of the FP64 root, so the first step lands at ~1e-14
-// and the second at rounding level; the FP64 pipe runs ~50 operations per
-// cell instead of a double-precision trigonometric solve.
+// two FP64 Newton steps on Eq. 10 finish it.  The FP32 root is within ~1e-7
+// relative of the FP64 root, so the first step lands at ~1e-14 and the second
+// at rounding level; the FP64 pipe runs a few dozen operations per cell and no
+// division instead of a double-precision trigonometric solve.
 // ----------------------------------------------------------------------------
 template <int METHOD>
 __device__ __forceinline__ double offset_cell_refined(double nx, double ny, double nz, double V0,
@@ -476,8 +476,34 @@ __device__ __forceinline__ double offset_cell_refined(double nx, double ny, doub
     if (d != d) return d;                         // Kawano's NaN (axis normal, V0 in {0, 1})
     const double h = 0.5 * L;
     d = fmin(fmax(d, 0.0), h);
-    d = fmin(fmax(polish<double>(d, V, n1, n2, n3), 0.0), h);
-    d = fmin(fmax(polish<double>(d, V, n1, n2, n3), 0.0), h);
+    // 1/n1 in FP64 from the FP32 reciprocal and two Newton steps (each squares
+    // the relative error: 1e-7 -> 1e-14 -> rounding); no FP64 division
+    double inv_n1 = 0.0;
+    if (n1 > 0.0) {
+        if (n1 > 1e-30) {
+            inv_n1 = (double)Fm<float>::rcp_((float)n1);
+            inv_n1 = inv_n1 * fma(-n1, inv_n1, 2.0);
+            inv_n1 = inv_n1 * fma(-n1, inv_n1, 2.0);
+        } else {
+            inv_n1 = 1.0 / n1;
+        }
+    }
+    const double n12 = n1 + n2, rhs = 6.0 * n2 * n3 * V;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        // Newton step on Eq. 10 in FP64 with the derivative's reciprocal in
+        // FP32: the step's relative error is that of the FP32 reciprocal
+        // (~1e-7) times the error, plus the quadratic term, so two steps from
+        // the FP32 root reach rounding level
+        if (d >= n12) {
+            d = n3 * V + 0.5 * n12;                   // case (5): linear, exact
+        } else if (d > 0.0) {
+            double g, gp;
+            reduced_residual<double>(d, rhs, n1, n2, n3, inv_n1, g, gp);
+            if (gp > 0.0) d -= g * (double)Fm<float>::rcp_((float)gp);
+        }
+        d = fmin(fmax(d, 0.0), h);
+    }
     return copysign(h - d, V0 - 0.5);
 }
 

@@ -18,6 +18,7 @@
 //   7. mean curvature of the paraboloid at the origin (Eq. 42), negated by
 //      default so that a convex fluid region has kappa > 0.
 #pragma once
+#include <type_traits>
 #include "plic_polygon.cuh"
 
 namespace plic {
@@ -25,19 +26,41 @@ namespace plic {
 enum { FIT_FP64 = 0, FIT_FP32 = 1, FIT_DF32 = 2, FIT_AUTO = 3 };
 
 // D3Q27 directions e_0..e_26, packed as (ex+1) + 3 (ey+1) + 9 (ez+1).
-__constant__ unsigned char c_e27[27] = {
-    13,
-    14, 12, 16, 10, 22, 4,
-    17, 9, 23, 3, 25, 1,
-    11, 15, 5, 21, 19, 7,
-    26, 0, 8, 18, 20, 6,
-    24, 2};
+#define PLIC_E27_PACKED          \
+    13,                          \
+    14, 12, 16, 10, 22, 4,       \
+    17, 9, 23, 3, 25, 1,         \
+    11, 15, 5, 21, 19, 7,        \
+    26, 0, 8, 18, 20, 6,         \
+    24, 2
+__constant__ unsigned char c_e27[27] = {PLIC_E27_PACKED};
+struct E27Table {
+    static constexpr unsigned char v[27] = {PLIC_E27_PACKED};
+};
 
 __device__ __forceinline__ void e_of(int i, int& ex, int& ey, int& ez) {
     const int p = c_e27[i];
     ex = p % 3 - 1;
     ey = (p / 3) % 3 - 1;
     ez = p / 9 - 1;
+}
+
+// The same table for a compile-time index (fully unrolled loops): folds to
+// constants instead of constant-memory loads.
+template <int I>
+__device__ __forceinline__ void e_of_c(int& ex, int& ey, int& ez) {
+    constexpr int p = E27Table::v[I];
+    ex = p % 3 - 1;
+    ey = (p / 3) % 3 - 1;
+    ez = p / 9 - 1;
+}
+// f(std::integral_constant<int, Q>) for Q = FROM..26, in order.
+template <int FROM, typename F>
+__device__ __forceinline__ void for_e27(F&& f) {
+    if constexpr (FROM < 27) {
+        f(std::integral_constant<int, FROM>{});
+        for_e27<FROM + 1>(f);
+    }
 }
 
 // ---------------------------------------------------------------------------

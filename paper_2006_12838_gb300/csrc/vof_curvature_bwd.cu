@@ -329,18 +329,18 @@ k_curv_gather(const int32_t* __restrict__ idx, int64_t n, const int64_t* __restr
         const int j = c + ex + ey * nx + ez * nxy;
         float acc = 0.0f;
         int32_t first = 0x7fffffff;
-#pragma unroll
-        for (int q = 0; q < 27; ++q) {
+        for_e27<0>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
             int fx, fy, fz;
-            e_of(q, fx, fy, fz);
+            e_of_c<q>(fx, fy, fz);
             const int sx = x - fx, sy = y - fy, sz = z - fz;
-            if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz) continue;
+            if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz) return;
             const int32_t sl = __ldg(slot + (j - fx - fy * nx - fz * nxy));
             if (sl >= 0) {
                 acc += __ldg(contrib + (int64_t)sl * 27 + q);
                 first = sl < first ? sl : first;
             }
-        }
+        });
         if (first == k) g_phi[j] = acc;
     }
 }
