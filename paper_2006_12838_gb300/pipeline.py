@@ -5,7 +5,8 @@ The GPU work is the same C ABI call as :func:`plic.offset`; this module only
 stages data: chunk i is copied host->device on one stream while chunk i-1 is
 solved on a second and chunk i-2 is copied back on a third, so the copies over
 the host link and the kernels overlap.  Host arrays should be pinned
-(``tensor.pin_memory()``) for the copies to be asynchronous.
+(``tensor.pin_memory()``) for the copies to be asynchronous; ``capture`` turns a
+whole pass into one CUDA graph.
 """
 from __future__ import annotations
 
@@ -75,3 +76,16 @@ class HostOffsetPipeline:
                 ev_free[b] = e
         for s in (self.h2d, self.comp, self.d2h):
             cur.wait_stream(s)
+
+    def capture(self, nx, ny, nz, V0, d0_out, V_out=None):
+        """A CUDA graph of ``run`` for these host buffers: every chunk's copies and
+        kernel launches become one graph, so a step is one ``replay()`` with no
+        per-chunk host work.  The buffers must stay alive while the graph is used."""
+        cur = torch.cuda.current_stream(self.device)
+        self.run(nx, ny, nz, V0, d0_out, V_out)          # warm-up outside the capture
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(nx, ny, nz, V0, d0_out, V_out)
+        cur.wait_stream(torch.cuda.current_stream(self.device))
+        return g
