@@ -455,18 +455,38 @@ def headline_config():
             "l2": "inputs 4 GiB per step > 129 MB L2 (no flush needed)"}
 
 
-def cpu_baseline(cells=1 << 24):
+def cpu_baseline(cells=1 << 24, cells_1core=1 << 20):
+    """The FP64 oracle on the host cores: the step's workload on a sample (all
+    cores and one core), and the curvature step on the 256^3 field (all cores)."""
     import oracle
     sample = oracle_sample(cells)
     oracle_step([a[:4096] for a in sample])
+    cores = oracle.num_threads()
     t0 = time.perf_counter()
     oracle_step(sample)
     sec = time.perf_counter() - t0
-    return {"value": cells / sec / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle_step([a[:cells_1core] for a in sample])
+        sec1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    from paper_2006_12838_gb300 import synth
+    phi, _ = synth.curvature_field(seed=3, edge=256)
+    p = phi.numpy()
+    idx = oracle.interface_cells(p)
+    t0 = time.perf_counter()
+    oracle.curvature(p, idx)
+    secc = time.perf_counter() - t0
+    return {"value": cells / sec / 1e9, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": "first %d cells of the 2^28-cell workload (same seeded stream), FP64 bisection "
                       "offset + forward round trip, OpenMP over host cores" % cells,
-            "seconds": sec}
+            "seconds": sec,
+            "value_1core": cells_1core / sec1 / 1e9, "sample_1core": "first %d cells, 1 thread" % cells_1core,
+            "curvature_256_cells_s": idx.size / secc, "curvature_256_seconds": secc,
+            "curvature_256_interface_cells": int(idx.size)}
 
 
 def run_reference(args):

@@ -79,6 +79,7 @@ def _load():
         lib.oracle_offset_batch.argtypes = [P, P, P, P, P, I64]
         lib.oracle_area_centroid_batch.argtypes = [P, P, P, P, P, P, P, P, I64]
         lib.oracle_num_threads.restype = I32
+        lib.oracle_set_num_threads.argtypes = [I32]
         lib.oracle_d3q27.argtypes = [P]
         lib.oracle_py_normal.restype = I32
         lib.oracle_py_normal.argtypes = [P, P]
@@ -114,6 +115,11 @@ def _ptr(a):
 def num_threads() -> int:
     """OpenMP threads the batched oracle functions use."""
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Set the OpenMP threads of the batched oracle functions."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def volume(nx, ny, nz, d0):

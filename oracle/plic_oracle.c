@@ -282,6 +282,16 @@ ORC_EXPORT int oracle_num_threads(void)
 #endif
 }
 
+/* Threads for the batched functions that follow (timing on one core). */
+ORC_EXPORT void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ---------------------------------------------------------------------------
  * Curvature (Sec. 4.2 and Appendix B).
  *
