@@ -307,15 +307,6 @@ plic_status plic_sphere_volume(const void *d0, void *V0, int64_t n, plic_precisi
 plic_status plic_sphere_offset(const void *V0, void *d0, int64_t n, plic_precision p,
                                void *stream);
 
-/* plic_device_check -- synchronises the current device and reports whether
- * any bounded wait inside a kernel of this library gave up since the last
- * check (the staged SZ-opt solve waits on shared-memory barriers for its bulk
- * copies; a wait that exceeds its poll limit is counted, and that block
- * returns without finishing its tiles).  Clears the count.  Returns PLIC_OK,
- * PLIC_ERR_TIMEOUT (a wait gave up: outputs of that call are incomplete) or
- * PLIC_ERR_CUDA.  The paper has no counterpart. */
-plic_status plic_device_check(void);
-
 /* Workspace kinds for plic_workspace_bytes(). */
 enum {
     PLIC_WS_COMPACT = 0,     /* arg: number of field cells nx*ny*nz             */

@@ -145,12 +145,6 @@ static const void* pick(plic_precision p, bool faithful) {
     return faithful ? kptr<METHOD, float, false, true>() : kptr<METHOD, float, false, false>();
 }
 
-// The optimised-SZ FP32 solve with its inputs staged by bulk asynchronous
-// copies (plic_offset_bulk.cu); all arrays 16-byte aligned.
-plic_status launch_sz_opt_bulk(const float* nx, const float* ny, const float* nz, const float* V0,
-                               float* d0, float* vrt, int64_t n, bool polish,
-                               unsigned long long* invalid, void* stream, const char* who);
-
 static plic_status offset_entry(const void* nx, const void* ny, const void* nz, const void* V0,
                                 void* d0, void* vrt, int64_t n, plic_method m, plic_precision p,
                                 uint32_t flags, int64_t* d_invalid_count, void* stream,
@@ -176,14 +170,6 @@ static plic_status offset_entry(const void* nx, const void* ny, const void* nz, 
         case PLIC_ANALYTIC: k = pick<M_ANALYTIC>(p, faithful); break;
         case PLIC_SZ_ORIG: k = pick<M_SZ_ORIG>(p, faithful); break;
         case PLIC_SZ_OPT:
-            if (!dbl && !faithful && vec_ok) {
-                *fused = vrt != nullptr;
-                return launch_sz_opt_bulk((const float*)nx, (const float*)ny, (const float*)nz,
-                                          (const float*)V0, (float*)d0, (float*)vrt, n,
-                                          p == PLIC_FP32_POLISHED,
-                                          reinterpret_cast<unsigned long long*>(d_invalid_count),
-                                          stream, who);
-            }
             if (!dbl && !faithful) {
                 const bool pol = p == PLIC_FP32_POLISHED;
                 *fused = vrt != nullptr;

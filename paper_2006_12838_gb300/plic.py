@@ -80,7 +80,6 @@ def load():
             "plic_paper_benchmark": [P, P, P, I64, I32, I32, I32, I32, P, P],
             "plic_sphere_volume": [P, P, I64, I32, P],
             "plic_offset_roundtrip": [P, P, P, P, P, P, I64, I32, I32, U32, P, P],
-            "plic_device_check": [],
             "plic_sphere_offset": [P, P, I64, I32, P],
         }
         for name, args in sigs.items():
@@ -375,8 +374,3 @@ def sphere_offset(V0, precision=None, out=None, stream=None):
     _check(load().plic_sphere_offset(_ptr(V0), _ptr(out), V0.numel(), p, _stream(V0, stream)),
            "plic_sphere_offset")
     return out
-
-
-def device_check():
-    """Raise if a bounded in-kernel wait gave up since the last check."""
-    _check(load().plic_device_check(), "plic_device_check")

@@ -255,7 +255,7 @@ def test_offset_roundtrip_ragged(dev, orc):
         ref = orc.volume(n[0][:k].astype(np.float32), n[1][:k].astype(np.float32),
                          n[2][:k].astype(np.float32), d_a.cpu().numpy().astype(np.float64))
         assert np.abs(v_a.cpu().numpy() - ref).max() <= 3e-7
-    plic.device_check()
+
 
 
 def test_host_pipeline_and_graph(dev, orc):

@@ -105,4 +105,3 @@ def test_full_size_sampled(dev, orc):
     print("full-size round trip max %.3e mean %.3e" % (rt.max().item(), rt.double().mean().item()))
     assert err.max() <= 2e-6
     assert rt.max().item() <= 1e-6
-    plic.device_check()          # no bounded in-kernel wait gave up
