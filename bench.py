@@ -615,8 +615,8 @@ def main():
     step_i = [0]
 
     def step(record=False):
-        # one launch: the fused solve + forward round trip (k_plic_offset_sz_opt_pair
-        # with ROUNDTRIP), events around it on the launching stream
+        # one launch: the fused solve + forward round trip (k_plic_offset_pair<M_SZ_OPT, 1, 1>,
+        # the round trip fused), events around it on the launching stream
         if record:
             ev[step_i[0]][0].record(s)
         plic.offset_roundtrip(*t32, method="sz_opt", precision="fp32p", out=d0, out_rt=Vrt)
@@ -697,7 +697,7 @@ def main():
     # 24 B/cell: nx, ny, nz, V0 in (16) + d0, V0_rt out (8)
     alg_bytes = 24.0 * CELLS
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_plic_offset_sz_opt_pair<POLISH=1,ROUNDTRIP=1>",
+    roof = {"bound": "hbm", "kernel": "k_plic_offset_pair<METHOD=M_SZ_OPT,POLISH=1,ROUNDTRIP=1>",
             "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": profile_traffic("plic_offset_roundtrip_sz_opt_fp32p"),

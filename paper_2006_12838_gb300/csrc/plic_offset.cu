@@ -67,9 +67,9 @@ k_plic_offset(const T* __restrict__ nx, const T* __restrict__ ny, const T* __res
 // cell duplicated in both lanes, so every cell sees identical arithmetic.
 // With ROUNDTRIP the forward volume of each stored d0 is written to vrt in
 // the same pass (plic_offset_roundtrip).
-template <bool POLISH, bool ROUNDTRIP>
+template <int METHOD, bool POLISH, bool ROUNDTRIP>
 __global__ void __launch_bounds__(256)
-k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict__ ny,
+k_plic_offset_pair(const float* __restrict__ nx, const float* __restrict__ ny,
                           const float* __restrict__ nz, const float* __restrict__ V0,
                           float* __restrict__ d0, int64_t n, int vec_ok,
                           unsigned long long* invalid, float* __restrict__ vrt) {
@@ -83,10 +83,10 @@ k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict_
         const float4 c = __ldcs(reinterpret_cast<const float4*>(nz) + i);
         const float4 v = __ldcs(reinterpret_cast<const float4*>(V0) + i);
         float2 w0, w1;
-        const float2 r0 = p2::offset_sz_opt<POLISH, ROUNDTRIP>(
+        const float2 r0 = p2::offset_pair<METHOD, POLISH, ROUNDTRIP>(
             make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y), make_float2(v.x, v.y),
             bad, &w0);
-        const float2 r1 = p2::offset_sz_opt<POLISH, ROUNDTRIP>(
+        const float2 r1 = p2::offset_pair<METHOD, POLISH, ROUNDTRIP>(
             make_float2(a.z, a.w), make_float2(b.z, b.w), make_float2(c.z, c.w), make_float2(v.z, v.w),
             bad, &w1);
         __stcs(reinterpret_cast<float4*>(d0) + i, make_float4(r0.x, r0.y, r1.x, r1.y));
@@ -95,7 +95,7 @@ k_plic_offset_sz_opt_pair(const float* __restrict__ nx, const float* __restrict_
     for (int64_t i = nvec * 4 + tid; i < n; i += stride) {
         int bad2 = 0;
         float2 w;
-        const float2 r = p2::offset_sz_opt<POLISH, ROUNDTRIP>(
+        const float2 r = p2::offset_pair<METHOD, POLISH, ROUNDTRIP>(
             make_float2(nx[i], nx[i]), make_float2(ny[i], ny[i]), make_float2(nz[i], nz[i]),
             make_float2(V0[i], V0[i]), bad2, &w);
         bad += bad2 >> 1;
@@ -145,6 +145,18 @@ static const void* pick(plic_precision p, bool faithful) {
     return faithful ? kptr<METHOD, float, false, true>() : kptr<METHOD, float, false, false>();
 }
 
+// The paired FP32 kernels (optimised SZ, analytic); *fused is set when the
+// round-trip volume comes out of the same kernel.
+template <int METHOD>
+static const void* pick_pair(bool polish, bool roundtrip, bool* fused) {
+    *fused = roundtrip;
+    if (polish)
+        return roundtrip ? reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, true, true>)
+                         : reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, true, false>);
+    return roundtrip ? reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, false, true>)
+                     : reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, false, false>);
+}
+
 static plic_status offset_entry(const void* nx, const void* ny, const void* nz, const void* V0,
                                 void* d0, void* vrt, int64_t n, plic_method m, plic_precision p,
                                 uint32_t flags, int64_t* d_invalid_count, void* stream,
@@ -167,19 +179,14 @@ static plic_status offset_entry(const void* nx, const void* ny, const void* nz, 
     const bool faithful = (flags & PLIC_FLAG_FAITHFUL) != 0;
     const void* k = nullptr;
     switch (m) {
-        case PLIC_ANALYTIC: k = pick<M_ANALYTIC>(p, faithful); break;
+        case PLIC_ANALYTIC:
+            k = (!dbl && !faithful) ? pick_pair<M_ANALYTIC>(p == PLIC_FP32_POLISHED, vrt != nullptr, fused)
+                                    : pick<M_ANALYTIC>(p, faithful);
+            break;
         case PLIC_SZ_ORIG: k = pick<M_SZ_ORIG>(p, faithful); break;
         case PLIC_SZ_OPT:
-            if (!dbl && !faithful) {
-                const bool pol = p == PLIC_FP32_POLISHED;
-                *fused = vrt != nullptr;
-                k = *fused ? (pol ? reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<true, true>)
-                                  : reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<false, true>))
-                           : (pol ? reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<true, false>)
-                                  : reinterpret_cast<const void*>(&k_plic_offset_sz_opt_pair<false, false>));
-            } else {
-                k = pick<M_SZ_OPT>(p, faithful);
-            }
+            k = (!dbl && !faithful) ? pick_pair<M_SZ_OPT>(p == PLIC_FP32_POLISHED, vrt != nullptr, fused)
+                                    : pick<M_SZ_OPT>(p, faithful);
             break;
         case PLIC_NEWTON: k = pick<M_NEWTON>(p, faithful); break;
         case PLIC_NESTED: k = pick<M_NESTED>(p, faithful); break;

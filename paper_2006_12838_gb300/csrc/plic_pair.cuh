@@ -1,5 +1,5 @@
-// plic_pair.cuh -- the FP32 fast path of the optimised SZ solution (Sec. 2.4)
-// for two cells at once, on the paired FP32 instructions of sm_100+ (one
+// plic_pair.cuh -- the FP32 fast paths of the optimised SZ solution (Sec. 2.4)
+// and of the analytic solution (Sec. 2.3) for two cells at once, on the paired FP32 instructions of sm_100+ (one
 // FFMA2/FADD2/FMUL2 issues two FP32 operations).  Comparisons, selects and
 // MUFU operations stay per component.
 //
@@ -45,6 +45,15 @@ __device__ __forceinline__ f2 cbrt_(f2 x) {
     x = add(x, mk(1e-30f));
     return make_float2(Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.x) * (1.0f / 3.0f)),
                        Fm<float>::exp2f_approx(Fm<float>::__log2f_approx(x.y) * (1.0f / 3.0f)));
+}
+
+// The same cube root with one Newton step (relative error at FP32 rounding):
+// for the analytic solution, whose trigonometric root scales with u^(1/2).
+__device__ __forceinline__ f2 cbrt_nr(f2 x) {
+    const f2 r = cbrt_(x);
+    const f2 r2 = mul(r, r);
+    const f2 res = fma(r2, r, make_float2(-x.x - 1e-30f, -x.y - 1e-30f));     // r^3 - x
+    return fma(make_float2(-res.x, -res.y), rcp(mul(mk(3.0f), r2)), r);
 }
 
 // sqrt of x >= 0 as x rsqrt(x) with 1e-30 added (no zero branch).  Both
@@ -141,6 +150,73 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3) {
     return sel(le(n12, n3V2), d5, d);
 }
 
+// The paper's analytic solution (Sec. 2.3, Eq. 25 with the tests of Eq. 24)
+// for two cells, in the reduced space of the unit normal (n1 <= n2 <= n3,
+// |n| = 1, V the reduced volume).  As in sz_opt: case (3) or (4) is decided
+// first from the volume at d = n3 (the test d3 <= n3 of the paper, made before
+// forming d3), so that one trigonometric root f(x, y, a, b, c) is evaluated
+// with the coefficients of that case; with u^3 = x^2 + y^2 the arctangent
+// atan(y/x) (x >= 0 here) is asin(y/u^(3/2)).  With POLISH the root gets
+// one Newton step; then the closed forms of cases (2), (1), (5) replace it
+// where their tests hold.
+template <bool POLISH>
+__device__ __forceinline__ f2 analytic(f2 V, f2 n1, f2 n2, f2 n3) {
+    typedef Kc<float> K;
+    const f2 n12 = add(n1, n2), n3V = mul(n3, V);
+    const f2 n3V2 = add(n3V, n3V);
+    const f2 V6n2n3 = mul(mul(mk(6.0f), n2), n3V), sqn1 = mul(n1, n1);
+    const f2 n1n2 = mul(n1, n2);
+    // case (3) vs (4): 6 n1 n2 n3 V < n3^2 (3 n12 - n3) + n1^2 (n1 - 3 n3) + n2^2 (n2 - 3 n3)
+    f2 num3 = mul(mul(n3, n3), fma(mk(3.0f), n12, make_float2(-n3.x, -n3.y)));
+    num3 = fma(sqn1, fma(mk(-3.0f), n3, n1), num3);
+    num3 = fma(mul(n2, n2), fma(mk(-3.0f), n3, n2), num3);
+    const b2 n3small = lt(n3, n12);
+    const b2 v3lt = lt(mul(V6n2n3, n1), num3);
+    const b2 c3 = {!n3small.x || v3lt.x, !n3small.y || v3lt.y};
+    // coefficients: case (3) x3 = 81 n1 n2 (n12 - 2 n3 V), y3^2 = 23328 (n1 n2)^3 - x3^2;
+    // case (4) t4 = 9 (n12 + n3)^2 - 18, x4 = n1 n2 n3 (324 - 648 V), y4^2 = 4 t4^3 - x4^2
+    const f2 x3 = mul(mul(mk(81.0f), n1n2), sub(n12, n3V2));
+    const f2 p3 = mul(mul(n1n2, n1n2), n1n2);
+    const f2 y3 = fma(mk(23328.0f), p3, make_float2(-x3.x * x3.x, -x3.y * x3.y));
+    const f2 s4 = add(n12, n3);
+    const f2 t4 = fma(mk(9.0f), mul(s4, s4), mk(-18.0f));
+    f2 x4 = mul(mul(n1n2, n3), fma(mk(-648.0f), V, mk(324.0f)));
+    x4 = make_float2(fmaxf(x4.x, 1.17549435e-38f), fmaxf(x4.y, 1.17549435e-38f));
+    const f2 y4 = fma(mul(mk(4.0f), t4), mul(t4, t4), make_float2(-x4.x * x4.x, -x4.y * x4.y));
+    const f2 x = sel(c3, x3, x4);
+    const f2 ysq = fmax0(sel(c3, y3, y4));
+    const f2 a = sel(c3, mul(mk(K::two_cbrt54), n1n2), mul(mk(K::two_over_cbrt864), t4));
+    const f2 b = sel(c3, mk(K::two_over_cbrt432), mk(K::two_over_cbrt3456));
+    const f2 c = sel(c3, n12, mul(mk(0.5f), s4));
+    const f2 q = fma(x, x, ysq);                                     // u^3
+    const f2 u = cbrt_nr(q);
+    // atan(y/x) from sine and cosine: the arcsine of the smaller of the two
+    // (<= 1/sqrt 2), reflected about pi/4 where y > x -- the arcsine of a
+    // sine near 1 would lose half the digits (x -> 0 near V = 1/2 in case (4)
+    // and near the case-(5) boundary in case (3))
+    const f2 rq = rsqrt(add(q, mk(1e-30f)));
+    const f2 sv = mul(sqrtp(ysq), rq), cv = mul(x, rq);
+    const b2 refl = lt(cv, sv);
+    const f2 am = sel(refl, cv, sv);
+    const f2 as = asin01(make_float2(fminf(am.x, 1.0f), fminf(am.y, 1.0f)));
+    const f2 th = mul(mk(0.33333333333333333f), sel(refl, sub(mk(1.5707963267948966f), as), as));
+    const f2 ang = sub(mk(K::pi_6), th);
+    const f2 sn = make_float2(__sinf(ang.x), __sinf(ang.y));
+    f2 d = fma(mul(fma(b, u, a), rsqrt(u)), make_float2(-sn.x, -sn.y), c);
+    if (POLISH) d = polish34(d, V, n1, n2, n3);
+    // case (2) where 3 n2 (2 n3 V + n1 - n2) < n1^2, unless case (1) holds
+    const f2 t2a = mul(mul(mk(3.0f), n2), add(n3V2, sub(n1, n2)));
+    const f2 d2 = fma(mk(0.5f), n1, mul(mk(K::inv_sqrt12),
+                                        sqrtp(fma(mk(24.0f), mul(n2, n3V), make_float2(-sqn1.x, -sqn1.y)))));
+    d = sel(lt(t2a, sqn1), d2, d);
+    // case (1) where 6 n2 n3 V < n1^2
+    const f2 d1 = cbrt_nr(mul(V6n2n3, n1));
+    d = sel(lt(V6n2n3, sqn1), d1, d);
+    // case (5) where n1 + n2 <= 2 n3 V
+    const f2 d5 = fma(mk(0.5f), n12, n3V);
+    return sel(le(n12, n3V2), d5, d);
+}
+
 // Forward volume (Eq. 10) of two cells at their offsets d0, in the cell's
 // L1-normalised reduced space (m1 <= m2 <= m3, m1 + m2 + m3 = 1; Eq. 10 is
 // homogeneous of degree 0 in (d, n)), il = 1/L:
@@ -167,11 +243,13 @@ __device__ __forceinline__ f2 volume_reduced(f2 d0, f2 il, f2 m1, f2 m2, f2 m3) 
     return make_float2(d0.x > 0.0f ? 1.0f - v.x : v.x, d0.y > 0.0f ? 1.0f - v.y : v.y);
 }
 
-// Whole cells: two (n, V0) -> d0 by the optimised SZ solution in FP32; with
-// ROUNDTRIP, also the forward volume of the returned d0 into *vrt.
-template <bool POLISH, bool ROUNDTRIP = false>
-__device__ __forceinline__ f2 offset_sz_opt(f2 nx, f2 ny, f2 nz, f2 V0, int& bad,
-                                            f2* vrt = nullptr) {
+// Whole cells: two (n, V0) -> d0 in FP32 by the optimised SZ solution
+// (METHOD = M_SZ_OPT, in L1 units) or the analytic solution (M_ANALYTIC, in
+// the unit normal's units); with ROUNDTRIP, also the forward volume of the
+// returned d0 into *vrt.
+template <int METHOD, bool POLISH, bool ROUNDTRIP = false>
+__device__ __forceinline__ f2 offset_pair(f2 nx, f2 ny, f2 nz, f2 V0, int& bad,
+                                          f2* vrt = nullptr) {
     const f2 ax = make_float2(fabsf(nx.x), fabsf(nx.y));
     const f2 ay = make_float2(fabsf(ny.x), fabsf(ny.y));
     const f2 az = make_float2(fabsf(nz.x), fabsf(nz.y));
@@ -188,9 +266,15 @@ __device__ __forceinline__ f2 offset_sz_opt(f2 nx, f2 ny, f2 nz, f2 V0, int& bad
     const f2 il = rcp(L);
     const f2 m1 = mul(n1, il), m3 = mul(n3, il);
     const f2 m2 = fmax0(sub(mk(1.0f), add(m1, m3)));
-    const f2 a = sz_opt<POLISH>(V, m1, m2, m3);
-    const f2 h = sub(mk(0.5f), a);
-    f2 r = mul(L, make_float2(copysignf(h.x, V0.x - 0.5f), copysignf(h.y, V0.y - 0.5f)));
+    f2 h;
+    if (METHOD == M_SZ_OPT) {
+        h = mul(L, sub(mk(0.5f), sz_opt<POLISH>(V, m1, m2, m3)));
+    } else {
+        const f2 n2 = fmax0(sub(sub(L, n1), n3));
+        const f2 d = analytic<POLISH>(V, n1, n2, n3);
+        h = fma(mk(0.5f), L, make_float2(-d.x, -d.y));
+    }
+    f2 r = make_float2(copysignf(h.x, V0.x - 0.5f), copysignf(h.y, V0.y - 0.5f));
     if (!okx) r.x = __int_as_float(0x7fffffff);
     if (!oky) r.y = __int_as_float(0x7fffffff);
     if (ROUNDTRIP) {

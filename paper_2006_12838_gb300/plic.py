@@ -176,7 +176,7 @@ def offset(nx, ny, nz, V0, method="sz_opt", precision=None, faithful=False, out=
 def offset_roundtrip(nx, ny, nz, V0, method="sz_opt", precision=None, faithful=False, out=None,
                      out_rt=None, invalid=None, stream=None):
     """(d0, V0_rt): plic_offset and the forward volume of its result in one
-    call (Sec. 2.5 round trip); one fused kernel for SZ-opt in FP32."""
+    call (Sec. 2.5 round trip); one fused kernel for SZ-opt and the analytic solution in FP32."""
     _cuda(nx, ny, nz, V0, out, out_rt, dtype=V0.dtype)
     p = _prec(V0.dtype, precision)
     m = METHODS[method] if isinstance(method, str) else int(method)
