@@ -259,6 +259,8 @@ typedef struct {
     int block_threads;       /* threads per block (multiple of 32, <= 1024)     */
     int cells_per_chunk;     /* interface cells claimed per work-queue ticket   */
     int blocks_per_sm;       /* resident blocks per SM of the persistent grid   */
+    int lanes_per_cell;      /* 8: eight lanes per interface cell (cooperative);
+                                1: one thread per cell; 0: the library's default */
 } vof_tuning;
 
 /* vof_curvature_batched -- vof_curvature over many fields of uneven size in

@@ -1,7 +1,8 @@
 """Launch-shape autotuner for the batched persistent curvature kernel.
 
 The shape (threads per block, interface cells claimed per work-queue ticket,
-resident blocks per SM) is chosen by timing every candidate on the actual
+resident blocks per SM, lanes per interface cell: one thread per cell or
+eight cooperating lanes) is chosen by timing every candidate on the actual
 fields with CUDA events and keeping the fastest.  Results are cached in a JSON
 file keyed by GPU name, kernel (method + flags) and a shape class of the
 workload (number of fields and total interface cells, both rounded to powers
@@ -22,8 +23,8 @@ import torch
 from . import build as _build
 from . import plic
 
-CANDIDATES = [(128, ch, bps) for ch in (32, 64, 128, 256, 512, 1024, 4096)
-              for bps in (0, 1, 2, 3)]
+CANDIDATES = ([(128, ch, bps, 1) for ch in (32, 64, 128, 256, 1024) for bps in (0, 2, 3, 4)] +
+              [(128, ch, bps, 8) for ch in (32, 64, 128, 256) for bps in (0, 2, 3)])
 _lock = threading.Lock()
 
 
@@ -57,11 +58,11 @@ def shape_class(fields) -> str:
 
 def key(fields, method, flags) -> str:
     dev = torch.cuda.get_device_name(fields[0][0].device)
-    return "%s|batched|%s|%d|%s" % (dev, method, flags, shape_class(fields))
+    return "%s|batched-v2|%s|%d|%s" % (dev, method, flags, shape_class(fields))
 
 
 def tune(fields, method="sz_opt", flags=0, reps=3, candidates=None, force=False):
-    """Best (block_threads, cells_per_chunk, blocks_per_sm) for these fields;
+    """Best (block_threads, cells_per_chunk, blocks_per_sm, lanes_per_cell) for these fields;
     returns (shape, timings) where timings maps str(shape) -> ms (empty when
     the cache answered)."""
     k = key(fields, method, flags)

@@ -70,9 +70,9 @@ k_plic_offset(const T* __restrict__ nx, const T* __restrict__ ny, const T* __res
 template <int METHOD, bool POLISH, bool ROUNDTRIP>
 __global__ void __launch_bounds__(256)
 k_plic_offset_pair(const float* __restrict__ nx, const float* __restrict__ ny,
-                          const float* __restrict__ nz, const float* __restrict__ V0,
-                          float* __restrict__ d0, int64_t n, int vec_ok,
-                          unsigned long long* invalid, float* __restrict__ vrt) {
+                   const float* __restrict__ nz, const float* __restrict__ V0,
+                   float* __restrict__ d0, int64_t n, int vec_ok,
+                   unsigned long long* invalid, float* __restrict__ vrt) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int bad = 0;

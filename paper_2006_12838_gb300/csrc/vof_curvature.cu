@@ -1,13 +1,16 @@
 // vof_curvature.cu -- curvature over interface-cell lists (Sec. 4.2), for one
-// field (vof_curvature) and for many fields in one persistent launch
-// (vof_curvature_batched).
+// field (vof_curvature, vof_laplace_pressure) and for many fields in one
+// persistent launch (vof_curvature_batched).
 //
-// Eight lanes per interface cell and one lane per 5x5 solve (see
-// vof_curvature_coop.cuh).  Consecutive list entries are mostly x-neighbours
-// (the list is in ascending cell order), so the stencils of a warp's cells
-// overlap in 3 x 3 rows of consecutive floats: the gathers hit L1.  The work
-// per cell is dominated by up to 27 PLIC solves (the paper's observation that
-// PLIC is the main cost) and the 5x5 solve.
+// Two layouts of the per-cell work: one thread per interface cell
+// (vof_curvature_tpc.cu; every single-field call and the batched default)
+// and eight lanes per cell (vof_curvature_coop.cuh; a batched tuning
+// option).  Measured on GB300: the 56 478-cell list of the 256^3 curvature
+// field in 14.8 us with one thread per cell against 33.3 us with eight lanes;
+// 2.69 M cells of 64 fields in 0.39 ms against 1.11 ms.  Only a list of a few
+// thousand cells (5 538: 10.9 us against 8.9 us) runs faster on eight lanes,
+// and the single-field entry keeps one layout for every list length so that
+// a cell's kappa does not depend on the list (or the buffer) it comes in.
 #include "host_common.h"
 #include "vof_curvature_coop.cuh"
 
@@ -15,38 +18,9 @@ namespace plic {
 
 constexpr int CO_THREADS = 128;       // 4 warps per block
 constexpr int CO_WARPS = CO_THREADS / 32;
-
-// Single field: warp w of the grid takes batches of `batch` list entries (32,
-// or 16 / 8 / 4 when the list is too short to give every resident warp slot
-// two batches of 32) in a grid-stride loop.
-template <int METHOD, int FIT>
-__global__ void __launch_bounds__(CO_THREADS)
-k_vof_curvature(const float* __restrict__ phi, int nx, int ny, const int32_t* __restrict__ idx,
-                int64_t n, const int64_t* __restrict__ d_n, float* __restrict__ kappa,
-                uint32_t flags, float scale, int batch) {
-    __shared__ float smem[CO_WARPS][CO_BATCH * CO_VALS];
-    int64_t lim = n;
-    if (d_n) {
-        const int64_t dn = *d_n;
-        lim = dn < n ? dn : n;
-    }
-    const int warp = threadIdx.x >> 5;
-    const int64_t nxy = (int64_t)nx * ny;
-    const int64_t gw = (int64_t)blockIdx.x * CO_WARPS + warp;
-    const int64_t nw = (int64_t)gridDim.x * CO_WARPS;
-    for (int64_t k0 = gw * batch; k0 < lim; k0 += nw * batch) {
-        auto fetch = [&](int slot) {
-            const int64_t k = k0 + slot;
-            CoCell c;
-            c.phi = phi; c.nx = nx; c.nxy = nxy;
-            c.valid = slot < batch && k < lim;
-            c.c = c.valid ? (int64_t)__ldg(idx + k) : 0;
-            c.out = kappa + k;
-            return c;
-        };
-        co_warp_batch<METHOD, FIT>(fetch, batch, flags, scale, smem[warp]);
-    }
-}
+static_assert(TPC_THREADS == CO_THREADS, "one block shape for both layouts");
+// Layout of the batched kernel when the tuning leaves it open (lanes per cell).
+constexpr int BATCHED_DEFAULT_LANES = 1;
 
 // Persistent batched kernel: each warp claims tickets of `chunk` cells (a
 // multiple of 32) of the concatenated interface lists from a device counter
@@ -101,12 +75,6 @@ k_vof_curvature_batched(const vof_field* __restrict__ fields, const int64_t* __r
         reinterpret_cast<const void*>(&K<M, FIT_DF32>), reinterpret_cast<const void*>(&K<M, FIT_AUTO>)};
 
 template <int METHOD>
-static const void* pick_single(int fit) {
-    PLIC_FIT_TABLE(k_vof_curvature, METHOD)
-    return k_vof_curvature_tab[fit];
-}
-
-template <int METHOD>
 static const void* pick_batched(int fit) {
     PLIC_FIT_TABLE(k_vof_curvature_batched, METHOD)
     return k_vof_curvature_batched_tab[fit];
@@ -123,13 +91,14 @@ static int fit_mode(uint32_t flags) {
     return -1;
 }
 
-static const void* select(bool batched, plic_method m, int fit) {
+// The eight-lane batched kernel for a method and fit mode.
+static const void* select_coop(plic_method m, int fit) {
     switch (m) {
-        case PLIC_ANALYTIC: return batched ? pick_batched<M_ANALYTIC>(fit) : pick_single<M_ANALYTIC>(fit);
-        case PLIC_SZ_ORIG: return batched ? pick_batched<M_SZ_ORIG>(fit) : pick_single<M_SZ_ORIG>(fit);
-        case PLIC_SZ_OPT: return batched ? pick_batched<M_SZ_OPT>(fit) : pick_single<M_SZ_OPT>(fit);
-        case PLIC_NEWTON: return batched ? pick_batched<M_NEWTON>(fit) : pick_single<M_NEWTON>(fit);
-        case PLIC_NESTED: return batched ? pick_batched<M_NESTED>(fit) : pick_single<M_NESTED>(fit);
+        case PLIC_ANALYTIC: return pick_batched<M_ANALYTIC>(fit);
+        case PLIC_SZ_ORIG: return pick_batched<M_SZ_ORIG>(fit);
+        case PLIC_SZ_OPT: return pick_batched<M_SZ_OPT>(fit);
+        case PLIC_NEWTON: return pick_batched<M_NEWTON>(fit);
+        case PLIC_NESTED: return pick_batched<M_NESTED>(fit);
     }
     return nullptr;
 }
@@ -152,20 +121,12 @@ static plic_status curvature_entry(const float* phi, int nx, int ny, int nz, con
     if (flags & PLIC_FLAG_NEIGHBOR_NORMAL)
         return launch_curvature_nn(phi, nx, ny, nz, idx, n_iface, d_n_iface, out, m, flags,
                                    fit_mode(flags), scale, stream, who);
-    const void* k = select(false, m, fit_mode(flags));
-    const int threads = CO_THREADS;
-    // batches of 32 entries per warp, smaller ones (down to 4) while the list
-    // would give fewer than two batches per resident warp slot: the group
-    // phase is latency bound, so short lists run faster spread thin (measured:
-    // 56 478 cells 34 us with batches of 8 against 39 us with 16 or 32; 5 538
-    // cells 9 us with 4 against 13 us with 8); at most one resident wave
-    const int64_t slots = (int64_t)sm_count() * blocks_per_sm(k, threads, 0) * CO_WARPS;
-    int batch = CO_BATCH;
-    while (batch > 4 && (n_iface + batch - 1) / batch < 2 * slots) batch >>= 1;
-    const int grid = stride_grid(k, threads, (n_iface + batch - 1) / batch * 32);
+    const void* k = select_tpc(false, m, fit_mode(flags));
+    if (!k) return PLIC_ERR_ARG;
+    const int grid = stride_grid(k, TPC_THREADS, n_iface);
     void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&idx, (void*)&n_iface,
-                    (void*)&d_n_iface, (void*)&out, (void*)&flags, (void*)&scale, (void*)&batch};
-    cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, as_stream(stream));
+                    (void*)&d_n_iface, (void*)&out, (void*)&flags, (void*)&scale};
+    cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(TPC_THREADS), args, 0, as_stream(stream));
     if (e != cudaSuccess) { set_last_error(who, e); return PLIC_ERR_CUDA; }
     return PLIC_OK;
 }
@@ -200,15 +161,18 @@ extern "C" plic_status vof_curvature_batched(const vof_field* fields, int n_fiel
     if (!fields || !workspace) return PLIC_ERR_ARG;
     if (ws_bytes < plic_workspace_bytes(PLIC_WS_BATCHED, n_fields)) return PLIC_ERR_ARG;
     if (!aligned(workspace, 256)) return PLIC_ERR_ALIGN;
-    int threads = CO_THREADS, chunk = 128, bps = 0;
+    int threads = CO_THREADS, chunk = 128, bps = 0, lanes = 0;
     if (tuning) {
         threads = tuning->block_threads;
         chunk = tuning->cells_per_chunk;
         bps = tuning->blocks_per_sm;
-        if (threads < 32 || threads > 1024 || (threads & 31) || chunk < 1 || bps < 0)
+        lanes = tuning->lanes_per_cell;
+        if (threads < 32 || threads > 1024 || (threads & 31) || chunk < 1 || bps < 0 ||
+            (lanes != 0 && lanes != 1 && lanes != 8))
             return PLIC_ERR_ARG;
         if (threads != CO_THREADS) return PLIC_ERR_UNSUPPORTED;   // built for 4 warps per block
     }
+    if (lanes == 0) lanes = BATCHED_DEFAULT_LANES;
     chunk = (chunk + CO_BATCH - 1) / CO_BATCH * CO_BATCH;     // whole warp batches
     // host-side prefix of the list lengths and argument checks
     const size_t nf = (size_t)n_fields;
@@ -237,7 +201,8 @@ extern "C" plic_status vof_curvature_batched(const vof_field* fields, int n_fiel
     free(pre);
     if (e != cudaSuccess) { set_last_error("vof_curvature_batched", e); return PLIC_ERR_CUDA; }
     if (total == 0) return PLIC_OK;
-    const void* k = select(true, m, fit_mode(flags));
+    const void* k = lanes == 1 ? select_tpc(true, m, fit_mode(flags)) : select_coop(m, fit_mode(flags));
+    if (!k) return PLIC_ERR_ARG;
     const int occ = blocks_per_sm(k, threads, 0);
     const int per_sm = bps > 0 ? (bps < occ ? bps : occ) : occ;
     int64_t grid = (int64_t)sm_count() * per_sm;

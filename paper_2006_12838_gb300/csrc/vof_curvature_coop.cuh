@@ -23,6 +23,7 @@
 namespace plic {
 
 constexpr int CO_BATCH = 32;          // cells per warp batch
+constexpr int TPC_THREADS = 128;      // block of the one-thread-per-cell kernels
 constexpr int CO_VALS = 24;           // per-cell smem record: M (15), b (5), m, pad
 
 // Source of one list entry: its field, cell index and output slot.
@@ -269,5 +270,11 @@ __device__ __forceinline__ void co_warp_batch(Fetch fetch, int batch, uint32_t f
     if (lane < batch && mine.valid) *mine.out = scale * co_solve<FIT>(smem + lane * CO_VALS, flags);
     __syncwarp();
 }
+
+// The one-thread-per-cell kernels (vof_curvature_tpc.cu): k_vof_curvature_tpc
+// (single field; arguments as k_vof_curvature without `batch`) or
+// k_vof_curvature_batched_tpc (arguments as k_vof_curvature_batched) for a
+// method and fit mode; nullptr for an invalid pair.
+const void* select_tpc(bool batched, plic_method m, int fit);
 
 }  // namespace plic

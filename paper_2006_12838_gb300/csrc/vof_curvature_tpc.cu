@@ -1,0 +1,202 @@
+// vof_curvature_tpc.cu -- the curvature step (Sec. 4.2, Appendix B) with one
+// thread per interface cell, for long interface lists.
+//
+// The eight-lane layout of vof_curvature_coop.cuh shortens the dependent
+// chain of a cell (it wins when the list is too short to fill the GPU), but
+// every lane of a group repeats the normal, the frame and the per-normal
+// solver constants, and the group reductions add shuffles.  With enough
+// cells to fill every warp slot many times over (the batched workload), the
+// instruction count decides instead, and one thread per cell does each step
+// once:
+//   - the 27 stencil values with compile-time offsets, the Parker-Youngs (or
+//     centre-of-mass) sums and the interface mask in registers;
+//   - normal, frame, centre offset d0(phi_0, n) and the per-normal constants
+//     of the solver once;
+//   - a loop over the set bits of the mask only (the interface neighbours of
+//     Eq. 36): the neighbour's value is re-read (an L1 hit: the stencil was
+//     just loaded), its offset solved, its point accumulated into the normal
+//     equations in registers;
+//   - the 5x5 solve of the fit precision and Eq. 42, as in the lane phase of
+//     the eight-lane layout (co_solve).
+// The results equal those of the eight-lane layout up to the summation order
+// of the stencil sums and of the normal equations.
+#include "host_common.h"
+#include "vof_curvature_coop.cuh"
+
+namespace plic {
+
+// D3Q27 direction components (+1) as 2-bit fields of one 64-bit word per axis,
+// entry i at bits 2i: a runtime index decodes with a shift, without a table
+// load (a table indexed per lane would serialise its constant-cache reads).
+constexpr unsigned long long e27_pack(int axis) {
+    unsigned long long w = 0;
+    for (int i = 0; i < 27; ++i) {
+        const int p = E27Table::v[i];
+        const int e = axis == 0 ? p % 3 : axis == 1 ? (p / 3) % 3 : p / 9;
+        w |= (unsigned long long)e << (2 * i);
+    }
+    return w;
+}
+struct E27Bits {
+    static constexpr unsigned long long X = e27_pack(0), Y = e27_pack(1), Z = e27_pack(2);
+};
+
+__device__ __forceinline__ int e27_comp(unsigned long long w, int i) {
+    return (int)((w >> (2 * i)) & 3ull) - 1;
+}
+
+// kappa (sign per flags) of interface cell c of a field, one thread.
+template <int METHOD, int FIT>
+__device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx, int64_t nxy,
+                                           int64_t c, uint32_t flags) {
+    const bool cm = (flags & PLIC_FLAG_NORMAL_CM) != 0;
+    const float* p0 = phi + c;
+    // 1. stencil: normal sums (Eq. 38 weights or all 1) and interface mask
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+    unsigned mask = 0u;
+    const float phi0 = __ldg(p0);
+    for_e27<1>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int p = E27Table::v[i];
+        constexpr int ex = p % 3 - 1, ey = (p / 3) % 3 - 1, ez = p / 9 - 1;
+        constexpr int e2 = ex * ex + ey * ey + ez * ez;
+        constexpr float wpy = e2 == 1 ? 4.0f : (e2 == 2 ? 2.0f : 1.0f);
+        const float v = __ldg(p0 + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
+        const float w = cm ? 1.0f : wpy;
+        if (ex != 0) gx = fmaf(w * (float)ex, v, gx);
+        if (ey != 0) gy = fmaf(w * (float)ey, v, gy);
+        if (ez != 0) gz = fmaf(w * (float)ez, v, gz);
+        if (v > 0.0f && v < 1.0f) mask |= 1u << i;
+    });
+    // 2. normal and frame (Sec. 4.2)
+    const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
+    if (!(gl > 0.0f)) return 0.0f;                     // undefined normal: kappa = 0
+    const float inv = -1.0f / gl;
+    const float nx_ = gx * inv, ny_ = gy * inv, nz_ = gz * inv;
+    float rx = 0.56270900f, ry = 0.32704452f, rz = 0.75921047f;
+    float byx = ny_ * rz - nz_ * ry, byy = nz_ * rx - nx_ * rz, byz = nx_ * ry - ny_ * rx;
+    float bl = byx * byx + byy * byy + byz * byz;
+    if (!(bl > 1e-12f)) {
+        rx = 0.32704452f; ry = 0.75921047f; rz = 0.56270900f;
+        byx = ny_ * rz - nz_ * ry; byy = nz_ * rx - nx_ * rz; byz = nx_ * ry - ny_ * rx;
+        bl = byx * byx + byy * byy + byz * byz;
+    }
+    const float ib = rsqrtf(bl);
+    byx *= ib; byy *= ib; byz *= ib;
+    const float bxx = byy * nz_ - byz * ny_, bxy = byz * nx_ - byx * nz_, bxz = byx * ny_ - byy * nx_;
+    // 3. centre offset and, for centroid points, the centre centroid
+    CellPlic<METHOD> pl;
+    pl.prepare(nx_, ny_, nz_);
+    const float d00 = pl.offset(phi0);
+    const bool centroid = (flags & PLIC_FLAG_POINT_CENTROID) != 0;
+    float c0x = 0.0f, c0y = 0.0f, c0z = 0.0f;
+    if (centroid) {
+        float A;
+        area_centroid<float>(nx_, ny_, nz_, d00, A, c0x, c0y, c0z);
+    }
+    // 4. interface neighbours (Eq. 36): points and normal equations
+    float rec[21];
+#pragma unroll
+    for (int q = 0; q < 20; ++q) rec[q] = 0.0f;
+    rec[20] = (float)__popc(mask);
+    unsigned list = mask;
+#pragma unroll 1
+    while (list) {
+        const int i = __ffs(list) - 1;
+        list &= list - 1u;
+        const int ex = e27_comp(E27Bits::X, i), ey = e27_comp(E27Bits::Y, i), ez = e27_comp(E27Bits::Z, i);
+        const float v = __ldg(p0 + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
+        const float d0i = pl.offset(v);
+        float qx = (float)ex, qy = (float)ey, qz = (float)ez, z;
+        if (centroid) {
+            float A, cx, cy, cz;
+            area_centroid<float>(nx_, ny_, nz_, d0i, A, cx, cy, cz);
+            qx += cx - c0x; qy += cy - c0y; qz += cz - c0z;
+            z = qx * nx_ + qy * ny_ + qz * nz_;
+        } else {
+            z = qx * nx_ + qy * ny_ + qz * nz_ + (d0i - d00);
+        }
+        const float x = qx * bxx + qy * bxy + qz * bxz;
+        const float y = qx * byx + qy * byy + qz * byz;
+        const float Q[5] = {x * x, y * y, x * y, x, y};
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+#pragma unroll
+            for (int b = a; b < 5; ++b) rec[uidx(a, b)] = fmaf(Q[a], Q[b], rec[uidx(a, b)]);
+            rec[15 + a] = fmaf(z, Q[a], rec[15 + a]);
+        }
+    }
+    // 5. fit and Eq. 42
+    return co_solve<FIT>(rec, flags);
+}
+
+// Single field: thread per list entry, grid-stride.
+template <int METHOD, int FIT>
+__global__ void __launch_bounds__(TPC_THREADS)
+k_vof_curvature_tpc(const float* __restrict__ phi, int nx, int ny, const int32_t* __restrict__ idx,
+                    int64_t n, const int64_t* __restrict__ d_n, float* __restrict__ kappa,
+                    uint32_t flags, float scale) {
+    int64_t lim = n;
+    if (d_n) {
+        const int64_t dn = *d_n;
+        lim = dn < n ? dn : n;
+    }
+    const int64_t nxy = (int64_t)nx * ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lim;
+         k += (int64_t)gridDim.x * blockDim.x)
+        kappa[k] = scale * tpc_kappa<METHOD, FIT>(phi, nx, nxy, (int64_t)__ldg(idx + k), flags);
+}
+
+// Persistent batched kernel: each warp claims tickets of `chunk` cells (a
+// multiple of 32) of the concatenated lists and gives one cell to each lane.
+template <int METHOD, int FIT>
+__global__ void __launch_bounds__(TPC_THREADS)
+k_vof_curvature_batched_tpc(const vof_field* __restrict__ fields, const int64_t* __restrict__ prefix,
+                            int n_fields, int64_t total, int chunk,
+                            unsigned long long* __restrict__ ticket, uint32_t flags) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ticket, (unsigned long long)chunk);
+        const int64_t start = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        if (start >= total) break;
+        const int64_t end = start + chunk < total ? start + chunk : total;
+        for (int64_t gi = start + lane; gi < end; gi += 32) {
+            int lo = 0, hi = n_fields - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(prefix + mid) <= gi) lo = mid; else hi = mid - 1;
+            }
+            const int64_t kk = gi - __ldg(prefix + lo);
+            const vof_field& F = fields[lo];
+            const float k = tpc_kappa<METHOD, FIT>(F.phi, F.nx, (int64_t)F.nx * F.ny,
+                                                   (int64_t)__ldg(F.idx + kk), flags);
+            F.kappa[kk] = k;
+        }
+    }
+}
+
+template <int METHOD>
+static const void* pick_tpc(bool batched, int fit) {
+#define PLIC_TPC(K) \
+    {reinterpret_cast<const void*>(&K<METHOD, FIT_FP64>), reinterpret_cast<const void*>(&K<METHOD, FIT_FP32>), \
+     reinterpret_cast<const void*>(&K<METHOD, FIT_DF32>), reinterpret_cast<const void*>(&K<METHOD, FIT_AUTO>)}
+    static const void* single[4] = PLIC_TPC(k_vof_curvature_tpc);
+    static const void* many[4] = PLIC_TPC(k_vof_curvature_batched_tpc);
+#undef PLIC_TPC
+    return batched ? many[fit] : single[fit];
+}
+
+const void* select_tpc(bool batched, plic_method m, int fit) {
+    if (fit < 0 || fit > 3) return nullptr;
+    switch (m) {
+        case PLIC_ANALYTIC: return pick_tpc<M_ANALYTIC>(batched, fit);
+        case PLIC_SZ_ORIG: return pick_tpc<M_SZ_ORIG>(batched, fit);
+        case PLIC_SZ_OPT: return pick_tpc<M_SZ_OPT>(batched, fit);
+        case PLIC_NEWTON: return pick_tpc<M_NEWTON>(batched, fit);
+        case PLIC_NESTED: return pick_tpc<M_NESTED>(batched, fit);
+    }
+    return nullptr;
+}
+
+}  // namespace plic

@@ -45,7 +45,7 @@ class VofField(ctypes.Structure):
 
 class VofTuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int), ("cells_per_chunk", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("lanes_per_cell", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -316,7 +316,9 @@ def curvature_batched(fields, method="sz_opt", flags=0, tuning=None, workspace=N
                       stream=None):
     """One persistent launch over many fields.  ``fields``: list of
     (phi, idx, n_iface, kappa) with device tensors; ``tuning``: optional
-    (block_threads, cells_per_chunk, blocks_per_sm)."""
+    (block_threads, cells_per_chunk, blocks_per_sm[, lanes_per_cell]) with
+    lanes_per_cell 8 (cooperative groups), 1 (one thread per cell) or 0
+    (the library's default)."""
     arr = (VofField * len(fields))()
     dev = fields[0][0].device
     for i, (phi, idx, n, kappa) in enumerate(fields):
@@ -331,7 +333,10 @@ def curvature_batched(fields, method="sz_opt", flags=0, tuning=None, workspace=N
         workspace = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
     tun = None
     if tuning is not None:
-        tun = VofTuning(*[int(v) for v in tuning])
+        t = [int(v) for v in tuning]
+        if len(t) not in (3, 4):
+            raise PlicError("tuning: (block_threads, cells_per_chunk, blocks_per_sm[, lanes_per_cell])")
+        tun = VofTuning(*(t + [0] * (4 - len(t))))
     m = METHODS[method] if isinstance(method, str) else int(method)
     _check(load().vof_curvature_batched(ctypes.cast(arr, ctypes.c_void_p), len(fields),
                                         None if tun is None else ctypes.cast(ctypes.pointer(tun), ctypes.c_void_p),

@@ -93,6 +93,10 @@ def test_host_side_argument_checks(lib):
     f = (plic.VofField * 1)()
     assert lib.vof_curvature_batched(ctypes.cast(f, P), 1, ctypes.cast(ctypes.pointer(tun), P), 2, 0,
                                      ok, 1 << 20, None) == ERR_ARG
+    for lanes in (2, 4, -1):                     # one thread or eight lanes per cell only
+        tun = plic.VofTuning(128, 64, 0, lanes)
+        assert lib.vof_curvature_batched(ctypes.cast(f, P), 1, ctypes.cast(ctypes.pointer(tun), P), 2,
+                                         0, ok, 1 << 20, None) == ERR_ARG
     # plane-sphere: bad n, precision, null, misaligned; empty is a no-op
     assert lib.plic_sphere_offset(ok, ok, -1, 0, None) == ERR_ARG
     assert lib.plic_sphere_offset(ok, ok, 10, 4, None) == ERR_ARG

@@ -137,11 +137,24 @@ def test_batched_matches_single(dev, orc):
         kap = torch.empty(max(k, 1), device=dev)
         args.append((phid, it, k, kap))
         singles.append(plic.curvature(phid, it).cpu().numpy() if k else np.zeros(0, np.float32))
-    for tuning in (None, (128, 64, 1), (128, 7, 2), (128, 1000, 0)):
+    big = max(range(len(args)), key=lambda i: args[i][2])
+    kref, dim, _ = orc.curvature(args[big][0].cpu().numpy(), args[big][1].cpu().numpy())
+    # one thread per cell (the default and lanes_per_cell = 1): the single-field
+    # kernel's arithmetic, so the same values
+    for tuning in (None, (128, 64, 1), (128, 7, 2), (128, 1000, 0), (128, 96, 0, 1), (128, 32, 3, 0)):
         plic.curvature_batched(args, tuning=tuning)
         for (phid, it, k, kap), s in zip(args, singles):
-            np.testing.assert_allclose(kap[:k].cpu().numpy(), s, rtol=1e-6, atol=1e-7)
-    # against the oracle too, on the field with the most interface cells
-    phid, it, k, kap = max(args, key=lambda a: a[2])
-    kref, dim, _ = orc.curvature(phid.cpu().numpy(), it.cpu().numpy())
+            np.testing.assert_array_equal(kap[:k].cpu().numpy(), s)
+    # eight lanes per cell: other summation orders; against the oracle on the
+    # largest field, and against the single-field values elsewhere
+    for tuning in ((128, 64, 1, 8), (128, 7, 2, 8), (128, 1000, 0, 8)):
+        plic.curvature_batched(args, tuning=tuning)
+        for (phid, it, k, kap), s in zip(args, singles):
+            if k:
+                rel = np.abs(kap[:k].cpu().numpy() - s) / np.maximum(np.abs(s), 1 / 64)
+                assert np.mean(rel <= 2 * TOL) >= 0.99, (tuning, rel.max())
+        phid, it, k, kap = args[big]
+        _check(kap[:k].cpu().numpy().astype(np.float64), kref, dim, TOL, "batched, 8 lanes")
+    plic.curvature_batched(args)
+    phid, it, k, kap = args[big]
     _check(kap[:k].cpu().numpy().astype(np.float64), kref, dim, TOL, "batched")
