@@ -6,11 +6,11 @@
 // (vof_curvature_tpc.cu; every single-field call and the batched default)
 // and eight lanes per cell (vof_curvature_coop.cuh; a batched tuning
 // option).  Measured on GB300: the 56 478-cell list of the 256^3 curvature
-// field in 14.8 us with one thread per cell against 33.3 us with eight lanes;
-// 2.69 M cells of 64 fields in 0.39 ms against 1.11 ms.  Only a list of a few
-// thousand cells (5 538: 10.9 us against 8.9 us) runs faster on eight lanes,
-// and the single-field entry keeps one layout for every list length so that
-// a cell's kappa does not depend on the list (or the buffer) it comes in.
+// field in 12.5 us with one thread per cell against 33.3 us with eight lanes;
+// 2.69 M cells of 64 fields in 0.33 ms against 1.11 ms; a 5 538-cell list in
+// 8.6 us against 8.9 us.  The single-field entry keeps one layout for every
+// list length, so that a cell's kappa does not depend on the list (or the
+// buffer) it comes in.
 #include "host_common.h"
 #include "vof_curvature_coop.cuh"
 

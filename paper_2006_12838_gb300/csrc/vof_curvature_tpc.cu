@@ -13,14 +13,16 @@
 //   - normal, frame, centre offset d0(phi_0, n) and the per-normal constants
 //     of the solver once;
 //   - a loop over the set bits of the mask only (the interface neighbours of
-//     Eq. 36): the neighbour's value is re-read (an L1 hit: the stencil was
-//     just loaded), its offset solved, its point accumulated into the normal
-//     equations in registers;
+//     Eq. 36), two neighbours per trip: their values are re-read (L1 hits: the
+//     stencil was just loaded), their offsets solved together (paired FP32
+//     instructions for the optimised SZ solution), their points accumulated
+//     into the normal equations in registers;
 //   - the 5x5 solve of the fit precision and Eq. 42, as in the lane phase of
 //     the eight-lane layout (co_solve).
 // The results equal those of the eight-lane layout up to the summation order
 // of the stencil sums and of the normal equations.
 #include "host_common.h"
+#include "plic_pair.cuh"
 #include "vof_curvature_coop.cuh"
 
 namespace plic {
@@ -43,6 +45,47 @@ struct E27Bits {
 
 __device__ __forceinline__ int e27_comp(unsigned long long w, int i) {
     return (int)((w >> (2 * i)) & 3ull) - 1;
+}
+
+// Offsets d0(V0, n) of two neighbours of a cell (both with the centre normal
+// of `pl`): for the optimised SZ solution, CellPlic<M_SZ_OPT>::offset on the
+// paired FP32 instructions (two neighbours per instruction; the arcsine and
+// the case-(1) cube root of the paired path); other methods solve one after
+// the other.
+template <int METHOD>
+__device__ __forceinline__ p2::f2 offset_two(const CellPlic<METHOD>& pl, p2::f2 V0) {
+    return make_float2(pl.offset(V0.x), pl.offset(V0.y));
+}
+template <>
+__device__ __forceinline__ p2::f2 offset_two<M_SZ_OPT>(const CellPlic<M_SZ_OPT>& P, p2::f2 V0) {
+    using namespace p2;
+    const f2 V = make_float2(fminf(V0.x, 1.0f - V0.x), fminf(V0.y, 1.0f - V0.y));
+    const b2 c5 = {V.x >= P.V5, V.y >= P.V5};
+    const b2 c1 = lt(V, mk(P.V1)), c2 = lt(V, mk(P.V2)), c3 = lt(V, mk(P.V3));
+    const f2 d5 = fma(mk(P.m3), V, mk(0.5f * P.n12));
+    const f2 d2 = mul(mk(0.5f), add(mk(P.m1), sqrtp(fmax0(fma(mk(P.k2a), V, mk(-P.k2b))))));
+    const f2 d1 = mul(mk(P.cb1), cbrt_(V));
+    const f2 x = sel(c3, fma(mk(-2.0f * P.m3), V, mk(P.n12)), fma(mk(-2.0f), V, mk(1.0f)));
+    f2 arg = mul(x, sel(c3, mk(P.s3), mk(P.s4)));
+    arg = make_float2(fminf(fmaxf(arg.x, 0.0f), 1.0f), fminf(fmaxf(arg.y, 0.0f), 1.0f));
+    const f2 t = sel(c3, mk(P.t3), mk(P.t4)), c = sel(c3, mk(P.n12), mk(0.5f));
+    const f2 th = mul(mk(0.33333333333333333f), asin01(arg));
+    f2 d = fma(mul(mk(-2.0f), t), make_float2(__sinf(th.x), __sinf(th.y)), c);
+    // Newton polish of the trigonometric root (cases 3/4)
+    const f2 e2 = sub(d, mk(P.m2)), e3 = fmax0(sub(d, mk(P.m3)));
+    const f2 e22 = mul(e2, e2), e33 = mul(e3, e3);
+    const f2 cub = fma(e22, e2, mul(e33, e3));
+    f2 g = fma(mul(mk(3.0f), d), sub(d, mk(P.m1)), mk(P.m1 * P.m1));
+    g = fma(make_float2(-cub.x, -cub.y), mk(P.inv1), g);
+    g = fma(mk(-P.k6), V, g);
+    f2 gp = fma(mk(6.0f), d, mk(-3.0f * P.m1));
+    gp = fma(mul(mk(-3.0f), add(e22, e33)), mk(P.inv1), gp);
+    d = sub(d, mul(g, rcp(gp)));
+    d = sel(c2, d2, d);
+    d = sel(c1, d1, d);
+    d = sel(c5, d5, d);
+    const f2 h = mul(mk(P.L), sub(mk(0.5f), d));
+    return make_float2(copysignf(h.x, V0.x - 0.5f), copysignf(h.y, V0.y - 0.5f));
 }
 
 // kappa (sign per flags) of interface cell c of a field, one thread.
@@ -99,31 +142,48 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
 #pragma unroll
     for (int q = 0; q < 20; ++q) rec[q] = 0.0f;
     rec[20] = (float)__popc(mask);
+    // two neighbours per trip (in ascending order; an odd last one pairs with
+    // a zero point that adds nothing)
     unsigned list = mask;
 #pragma unroll 1
     while (list) {
-        const int i = __ffs(list) - 1;
+        const int i1 = __ffs(list) - 1;
         list &= list - 1u;
-        const int ex = e27_comp(E27Bits::X, i), ey = e27_comp(E27Bits::Y, i), ez = e27_comp(E27Bits::Z, i);
-        const float v = __ldg(p0 + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
-        const float d0i = pl.offset(v);
-        float qx = (float)ex, qy = (float)ey, qz = (float)ez, z;
-        if (centroid) {
-            float A, cx, cy, cz;
-            area_centroid<float>(nx_, ny_, nz_, d0i, A, cx, cy, cz);
-            qx += cx - c0x; qy += cy - c0y; qz += cz - c0z;
-            z = qx * nx_ + qy * ny_ + qz * nz_;
-        } else {
-            z = qx * nx_ + qy * ny_ + qz * nz_ + (d0i - d00);
+        const bool two = list != 0u;
+        const int i2 = two ? __ffs(list) - 1 : i1;
+        list &= list - 1u;                          // no-op on an empty list
+        const int ex1 = e27_comp(E27Bits::X, i1), ey1 = e27_comp(E27Bits::Y, i1), ez1 = e27_comp(E27Bits::Z, i1);
+        const int ex2 = e27_comp(E27Bits::X, i2), ey2 = e27_comp(E27Bits::Y, i2), ez2 = e27_comp(E27Bits::Z, i2);
+        const float v1 = __ldg(p0 + ex1 + (int64_t)ey1 * nx + (int64_t)ez1 * nxy);
+        const float v2 = __ldg(p0 + ex2 + (int64_t)ey2 * nx + (int64_t)ez2 * nxy);
+        const p2::f2 d0i = offset_two<METHOD>(pl, make_float2(v1, v2));
+        float qx[2] = {(float)ex1, (float)ex2}, qy[2] = {(float)ey1, (float)ey2};
+        float qz[2] = {(float)ez1, (float)ez2}, z[2];
+        const float dd[2] = {d0i.x, d0i.y};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (centroid) {
+                float A, cx, cy, cz;
+                area_centroid<float>(nx_, ny_, nz_, dd[j], A, cx, cy, cz);
+                qx[j] += cx - c0x; qy[j] += cy - c0y; qz[j] += cz - c0z;
+                z[j] = qx[j] * nx_ + qy[j] * ny_ + qz[j] * nz_;
+            } else {
+                z[j] = qx[j] * nx_ + qy[j] * ny_ + qz[j] * nz_ + (dd[j] - d00);
+            }
         }
-        const float x = qx * bxx + qy * bxy + qz * bxz;
-        const float y = qx * byx + qy * byy + qz * byz;
-        const float Q[5] = {x * x, y * y, x * y, x, y};
 #pragma unroll
-        for (int a = 0; a < 5; ++a) {
+        for (int j = 0; j < 2; ++j) {
+            const float w = (j == 0 || two) ? 1.0f : 0.0f;
+            const float x = w * (qx[j] * bxx + qy[j] * bxy + qz[j] * bxz);
+            const float y = w * (qx[j] * byx + qy[j] * byy + qz[j] * byz);
+            const float zz = w * z[j];
+            const float Q[5] = {x * x, y * y, x * y, x, y};
 #pragma unroll
-            for (int b = a; b < 5; ++b) rec[uidx(a, b)] = fmaf(Q[a], Q[b], rec[uidx(a, b)]);
-            rec[15 + a] = fmaf(z, Q[a], rec[15 + a]);
+            for (int a = 0; a < 5; ++a) {
+#pragma unroll
+                for (int b = a; b < 5; ++b) rec[uidx(a, b)] = fmaf(Q[a], Q[b], rec[uidx(a, b)]);
+                rec[15 + a] = fmaf(zz, Q[a], rec[15 + a]);
+            }
         }
     }
     // 5. fit and Eq. 42
