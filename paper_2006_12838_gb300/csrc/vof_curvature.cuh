@@ -38,6 +38,8 @@ struct E27Table {
     static constexpr unsigned char v[27] = {PLIC_E27_PACKED};
 };
 
+// e_i from the constant table: the cheapest in registers; the lanes of a warp
+// that ask for different i are served one address at a time.
 __device__ __forceinline__ void e_of(int i, int& ex, int& ey, int& ez) {
     const int p = c_e27[i];
     ex = p % 3 - 1;
@@ -45,8 +47,36 @@ __device__ __forceinline__ void e_of(int i, int& ex, int& ey, int& ez) {
     ez = p / 9 - 1;
 }
 
+// e_i decoded from immediates, for indices that differ across the lanes of a
+// warp: the components (+1) are 2-bit fields of two 32-bit words per axis
+// (entries 0-15 and 16-26), entry i at bits 2 (i mod 16).
+constexpr uint32_t e27_word(int axis, int half) {
+    uint32_t w = 0;
+    for (int i = 16 * half; i < 27 && i < 16 * half + 16; ++i) {
+        const int p = E27Table::v[i];
+        const int e = axis == 0 ? p % 3 : axis == 1 ? (p / 3) % 3 : p / 9;
+        w |= (uint32_t)e << (2 * (i - 16 * half));
+    }
+    return w;
+}
+template <int AXIS>
+struct E27Words {
+    static constexpr uint32_t lo = e27_word(AXIS, 0), hi = e27_word(AXIS, 1);
+};
+template <int AXIS>
+__device__ __forceinline__ int e27_comp(int i) {
+    const uint32_t w = i < 16 ? E27Words<AXIS>::lo : E27Words<AXIS>::hi;
+    return (int)((w >> (2 * (i & 15))) & 3u) - 1;
+}
+
+__device__ __forceinline__ void e_of_lanes(int i, int& ex, int& ey, int& ez) {
+    ex = e27_comp<0>(i);
+    ey = e27_comp<1>(i);
+    ez = e27_comp<2>(i);
+}
+
 // The same table for a compile-time index (fully unrolled loops): folds to
-// constants instead of constant-memory loads.
+// constants.
 template <int I>
 __device__ __forceinline__ void e_of_c(int& ex, int& ey, int& ez) {
     constexpr int p = E27Table::v[I];

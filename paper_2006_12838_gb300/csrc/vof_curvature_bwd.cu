@@ -315,14 +315,17 @@ k_curv_gather(const int32_t* __restrict__ idx, int64_t n, const int64_t* __restr
         const int64_t dn = *d_n;
         lim = dn < n ? dn : n;
     }
-    // fields hold < 2^31 cells (checked by the entry point): 32-bit index math
+    // fields hold < 2^31 cells (checked by the entry point): 32-bit index math;
+    // the pair index t = 27 k + o fits 32 bits unless the list is longer than
+    // 2^32 / 27 (then the 64-bit division)
     const int nxy = nx * ny;
+    const bool small = lim * 27 <= (int64_t)0xffffffffu;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < lim * 27;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(t / 27);
+        const int k = small ? (int)((uint32_t)t / 27u) : (int)(t / 27);
         const int o = (int)(t - (int64_t)k * 27);
         int ex, ey, ez;
-        e_of(o, ex, ey, ez);
+        e_of_lanes(o, ex, ey, ez);                  // o differs across the warp
         const int c = __ldg(idx + k);
         const int cz = c / nxy, cr = c - cz * nxy, cy = cr / nx, cx = cr - cy * nx;
         const int x = cx + ex, y = cy + ey, z = cz + ez;

@@ -27,26 +27,6 @@
 
 namespace plic {
 
-// D3Q27 direction components (+1) as 2-bit fields of one 64-bit word per axis,
-// entry i at bits 2i: a runtime index decodes with a shift, without a table
-// load (a table indexed per lane would serialise its constant-cache reads).
-constexpr unsigned long long e27_pack(int axis) {
-    unsigned long long w = 0;
-    for (int i = 0; i < 27; ++i) {
-        const int p = E27Table::v[i];
-        const int e = axis == 0 ? p % 3 : axis == 1 ? (p / 3) % 3 : p / 9;
-        w |= (unsigned long long)e << (2 * i);
-    }
-    return w;
-}
-struct E27Bits {
-    static constexpr unsigned long long X = e27_pack(0), Y = e27_pack(1), Z = e27_pack(2);
-};
-
-__device__ __forceinline__ int e27_comp(unsigned long long w, int i) {
-    return (int)((w >> (2 * i)) & 3ull) - 1;
-}
-
 // Offsets d0(V0, n) of two neighbours of a cell (both with the centre normal
 // of `pl`): for the optimised SZ solution, CellPlic<M_SZ_OPT>::offset on the
 // paired FP32 instructions (two neighbours per instruction; the arcsine and
@@ -152,8 +132,9 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
         const bool two = list != 0u;
         const int i2 = two ? __ffs(list) - 1 : i1;
         list &= list - 1u;                          // no-op on an empty list
-        const int ex1 = e27_comp(E27Bits::X, i1), ey1 = e27_comp(E27Bits::Y, i1), ez1 = e27_comp(E27Bits::Z, i1);
-        const int ex2 = e27_comp(E27Bits::X, i2), ey2 = e27_comp(E27Bits::Y, i2), ez2 = e27_comp(E27Bits::Z, i2);
+        int ex1, ey1, ez1, ex2, ey2, ez2;
+        e_of_lanes(i1, ex1, ey1, ez1);
+        e_of_lanes(i2, ex2, ey2, ez2);
         const float v1 = __ldg(p0 + ex1 + (int64_t)ey1 * nx + (int64_t)ez1 * nxy);
         const float v2 = __ldg(p0 + ex2 + (int64_t)ey2 * nx + (int64_t)ez2 * nxy);
         const p2::f2 d0i = offset_two<METHOD>(pl, make_float2(v1, v2));
