@@ -186,6 +186,58 @@ def frac(x, p):
     return None if x is None or p in (None, 0) else x / p
 
 
+# Curvature roofline (bound "alu"): the FP32 arithmetic of the method per
+# interface cell with m interface neighbours (PY normal, SZ-opt solves with the
+# per-normal constants computed once per cell, foot points, 5x5 LDL^T), an FMA,
+# a compare or a min/max counted as one operation and a division as one MUFU
+# reciprocal plus one multiply:
+#   per cell: stencil sums 54, interface tests 52, normal 10, frame 19,
+#     per-normal solver constants 72, LDL^T factor 55 + solve 25, Eq. 42 12 -> 299
+#     (MUFU 20: normal 2, frame 1, constants 11, pivots 5, Eq. 42 1)
+#   per PLIC solve (m + 1 of them): 59 (MUFU 6: sqrt, cube root 2, arcsine, sine,
+#     polish reciprocal)
+#   per neighbour: foot point 11, normal equations 23                     -> 34
+# The peaks are the unit counts times the maximum SM clock: 128 FP32 lanes and
+# 16 MUFU lanes per SM, 152 SMs.
+CURV_FP_CELL, CURV_FP_SOLVE, CURV_FP_NEIGHBOUR = 299, 59, 34
+CURV_XU_CELL, CURV_XU_SOLVE = 20, 6
+N_SM, FP32_PER_SM, XU_PER_SM = 152, 128, 16
+
+
+def curvature_roofline(cells_per_s, m_mean, pk):
+    clk = float(pk.get("sm_max_mhz") or 2070.0) * 1e6
+    fp_peak, xu_peak = N_SM * FP32_PER_SM * clk, N_SM * XU_PER_SM * clk
+    fp = CURV_FP_CELL + CURV_FP_SOLVE * (m_mean + 1) + CURV_FP_NEIGHBOUR * m_mean
+    xu = CURV_XU_CELL + CURV_XU_SOLVE * (m_mean + 1)
+    roof = 1.0 / max(fp / fp_peak, xu / xu_peak)          # cells/s at the busier pipe's peak
+    return {"bound": "alu", "pipe": "fp32" if fp / fp_peak >= xu / xu_peak else "mufu",
+            "achieved": cells_per_s * fp / 1e12, "peak": fp_peak / 1e12, "unit": "T FP32 op/s",
+            "frac": cells_per_s / roof, "fp32_ops_per_cell": round(fp, 1),
+            "mufu_ops_per_cell": round(xu, 1), "mean_interface_neighbours": round(m_mean, 3),
+            "roof_g_cells_s": roof / 1e9,
+            "peak_src": "152 SMs x 128 FP32 lanes x %.0f MHz (sm_max_mhz)" % (clk / 1e6)}
+
+
+def mean_interface_neighbours(fields):
+    """Mean number of interface neighbours (0 < phi < 1 among the 26) of the
+    listed cells, over (phi, idx, k) triples (workload statistic)."""
+    import torch
+    tot, cnt = 0, 0
+    for phi, idx, k in fields:
+        if k == 0:
+            continue
+        nz, ny, nx = phi.shape
+        f = ((phi > 0) & (phi < 1)).reshape(-1).to(torch.int32)
+        c = idx[:k].long()
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if dx or dy or dz:
+                        tot += int(f[c + dx + dy * nx + dz * nx * ny].sum().item())
+        cnt += k
+    return tot / max(cnt, 1)
+
+
 # ---------------------------------------------------------------------------
 # sections (each returns a dict)
 # ---------------------------------------------------------------------------
@@ -276,10 +328,13 @@ def section_curvature(dev, pk, steps):
     sec = timed(lambda: plic.interface_compact(phi, idx=idx, count=cnt2, workspace=ws), steps, 3, s)
     out["compact"] = {"ms": sec / steps * 1e3,
                       "hbm_gbs": (phi.numel() * 4 + k * 4) * steps / sec / 1e9}
+    m_mean = mean_interface_neighbours([(phi, it, k)])
     for fit, name in FITS:
         sec = timed(lambda: plic.curvature(phi, it, kappa=kap, flags=fit), steps, 3, s)
         out["curvature_sz_opt_" + name] = {"ms": sec / steps * 1e3,
                                             "m_cells_s": k * steps / sec / 1e6}
+        if fit == 0:
+            out["curvature_sz_opt_auto"]["roofline"] = curvature_roofline(k * steps / sec, m_mean, pk)
     for m in plic.METHODS:
         sec = timed(lambda: plic.curvature(phi, it, kappa=kap, method=m), steps, 2, s)
         out["curvature_%s_auto" % m] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
@@ -372,9 +427,18 @@ def section_batched(dev, pk, steps):
     out["autotune"] = {"shape": list(shape), "candidates": len(times),
                        "best_ms": min(times.values()) if times else None,
                        "worst_ms": max(times.values()) if times else None}
+    m_mean = mean_interface_neighbours([(a[0], a[1], a[2]) for a in args])
     for fit, name in FITS:
         sec = timed(lambda: plic.curvature_batched(args, flags=fit, tuning=shape), steps, 2, s)
         out["batched_" + name] = {"ms": sec / steps * 1e3, "m_cells_s": tot * steps / sec / 1e6}
+        if fit == 0:
+            out["batched_auto"]["roofline"] = curvature_roofline(tot * steps / sec, m_mean, pk)
+    # the other layout at its best tuning, for comparison
+    if times:
+        other = [c for c in times if c.endswith(", 8)" if shape[-1] == 1 else ", 1)")]
+        if other:
+            oc = min(other, key=times.get)
+            out["batched_other_layout"] = {"tuning": oc, "ms": times[oc]}
     return out
 
 
