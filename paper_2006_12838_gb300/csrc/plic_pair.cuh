@@ -86,20 +86,20 @@ __device__ __forceinline__ f2 asin01(f2 a) {
     return sel(big, fma(mk(-2.0f), p, mk(1.5707963267948966f)), p);
 }
 
-// One Newton step on the cubic of Eq. 10 for cases (3)/(4) (d >= n2, n1 > 0):
-// g = 3 d (d - n1) + n1^2 - ((d - n2)^3 + (d - n3)_+^3)/n1 - 6 n2 n3 V,
-// g' = 6 d - 3 n1 - 3 ((d - n2)^2 + (d - n3)_+^2)/n1 = 12 n2 n3 x area > 0.
-__device__ __forceinline__ f2 polish34(f2 d, f2 V, f2 n1, f2 n2, f2 n3) {
+// One Newton step on the cubic of Eq. 10 for cases (3)/(4) (d >= n2, n1 > 0),
+// with g and g' multiplied through by n1 so that one reciprocal serves:
+// n1 g = n1 (3 d (d - n1) + n1^2) - (d - n2)^3 - (d - n3)_+^3 - 6 n1 n2 n3 V,
+// n1 g' = n1 (6 d - 3 n1) - 3 ((d - n2)^2 + (d - n3)_+^2) = 12 n1 n2 n3 x area > 0.
+// V6 = 6 n1 n2 n3 V.
+__device__ __forceinline__ f2 polish34(f2 d, f2 V6, f2 n1, f2 n2, f2 n3) {
     const f2 e2 = sub(d, n2), e3 = fmax0(sub(d, n3));
-    const f2 inv1 = rcp(n1);
     const f2 e22 = mul(e2, e2), e33 = mul(e3, e3);
     const f2 cub = fma(e22, e2, mul(e33, e3));
     const f2 dd = sub(d, n1);
-    f2 g = fma(mk(3.0f), mul(d, dd), mul(n1, n1));
-    g = fma(make_float2(-cub.x, -cub.y), inv1, g);
-    g = fma(mk(-6.0f), mul(mul(n2, n3), V), g);
-    f2 gp = fma(mk(6.0f), d, mul(mk(-3.0f), n1));
-    gp = fma(mk(-3.0f), mul(add(e22, e33), inv1), gp);
+    f2 g = mul(n1, fma(mk(3.0f), mul(d, dd), mul(n1, n1)));
+    g = sub(g, add(cub, V6));
+    f2 gp = mul(n1, fma(mk(6.0f), d, mul(mk(-3.0f), n1)));
+    gp = fma(mk(-3.0f), add(e22, e33), gp);
     return sub(d, mul(g, rcp(gp)));
 }
 
@@ -119,7 +119,8 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3) {
     num3 = fma(sqn1, fma(mk(-3.0f), n3, n1), num3);
     num3 = fma(mul(n2, n2), fma(mk(-3.0f), n3, n2), num3);
     const b2 n3small = lt(n3, n12);
-    const b2 v3lt = lt(mul(V6n2n3, n1), num3);
+    const f2 V6n1n2n3 = mul(V6n2n3, n1);
+    const b2 v3lt = lt(V6n1n2n3, num3);
     const b2 c3 = {!n3small.x || v3lt.x, !n3small.y || v3lt.y};
     // arcsine argument without cancellation
     const f2 q3 = mul(mul(mk(1.5f), n1n2), sub(n12, n3V2));
@@ -137,13 +138,13 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3) {
     const f2 th = mul(mk(0.33333333333333333f), asin01(arg));
     const f2 sn = make_float2(__sinf(th.x), __sinf(th.y));
     f2 d = fma(mul(mk(-2.0f), t), sn, c);
-    if (POLISH) d = polish34(d, V, n1, n2, n3);
+    if (POLISH) d = polish34(d, V6n1n2n3, n1, n2, n3);
     // case (2) where 3 n2 (2 n3 V + n1 - n2) < n1^2, unless case (1) holds
     const f2 t2a = mul(mul(mk(3.0f), n2), add(n3V2, sub(n1, n2)));
     const f2 d2 = mul(mk(0.5f), add(n1, sqrtp(fma(mk(8.0f), mul(n2, n3V), mul(mk(-0.33333333333333333f), sqn1)))));
     d = sel(lt(t2a, sqn1), d2, d);
     // case (1) where 6 n2 n3 V < n1^2
-    const f2 d1 = cbrt_(mul(V6n2n3, n1));
+    const f2 d1 = cbrt_(V6n1n2n3);
     d = sel(lt(V6n2n3, sqn1), d1, d);
     // case (5) where n1 + n2 <= 2 n3 V
     const f2 d5 = fma(mk(0.5f), n12, n3V);
@@ -171,7 +172,8 @@ __device__ __forceinline__ f2 analytic(f2 V, f2 n1, f2 n2, f2 n3) {
     num3 = fma(sqn1, fma(mk(-3.0f), n3, n1), num3);
     num3 = fma(mul(n2, n2), fma(mk(-3.0f), n3, n2), num3);
     const b2 n3small = lt(n3, n12);
-    const b2 v3lt = lt(mul(V6n2n3, n1), num3);
+    const f2 V6n1n2n3 = mul(V6n2n3, n1);
+    const b2 v3lt = lt(V6n1n2n3, num3);
     const b2 c3 = {!n3small.x || v3lt.x, !n3small.y || v3lt.y};
     // coefficients: case (3) x3 = 81 n1 n2 (n12 - 2 n3 V), y3^2 = 23328 (n1 n2)^3 - x3^2;
     // case (4) t4 = 9 (n12 + n3)^2 - 18, x4 = n1 n2 n3 (324 - 648 V), y4^2 = 4 t4^3 - x4^2
@@ -203,14 +205,14 @@ __device__ __forceinline__ f2 analytic(f2 V, f2 n1, f2 n2, f2 n3) {
     const f2 ang = sub(mk(K::pi_6), th);
     const f2 sn = make_float2(__sinf(ang.x), __sinf(ang.y));
     f2 d = fma(mul(fma(b, u, a), rsqrt(u)), make_float2(-sn.x, -sn.y), c);
-    if (POLISH) d = polish34(d, V, n1, n2, n3);
+    if (POLISH) d = polish34(d, V6n1n2n3, n1, n2, n3);
     // case (2) where 3 n2 (2 n3 V + n1 - n2) < n1^2, unless case (1) holds
     const f2 t2a = mul(mul(mk(3.0f), n2), add(n3V2, sub(n1, n2)));
     const f2 d2 = fma(mk(0.5f), n1, mul(mk(K::inv_sqrt12),
                                         sqrtp(fma(mk(24.0f), mul(n2, n3V), make_float2(-sqn1.x, -sqn1.y)))));
     d = sel(lt(t2a, sqn1), d2, d);
     // case (1) where 6 n2 n3 V < n1^2
-    const f2 d1 = cbrt_nr(mul(V6n2n3, n1));
+    const f2 d1 = cbrt_nr(V6n1n2n3);
     d = sel(lt(V6n2n3, sqn1), d1, d);
     // case (5) where n1 + n2 <= 2 n3 V
     const f2 d5 = fma(mk(0.5f), n12, n3V);
@@ -227,17 +229,20 @@ __device__ __forceinline__ f2 analytic(f2 V, f2 n1, f2 n2, f2 n3) {
 __device__ __forceinline__ f2 volume_reduced(f2 d0, f2 il, f2 m1, f2 m2, f2 m3) {
     const f2 ad = make_float2(fabsf(d0.x), fabsf(d0.y));
     const f2 d = fmax0(fma(make_float2(-ad.x, -ad.y), il, mk(0.5f)));
+    // reciprocals: 1/m3 (m3 >= 1/3), 1/m1 and 1/(6 m2 m3), infinite for
+    // m1 = 0 / m2 = 0; 1/m1 is capped at FLT_MAX so that the case-(2) term
+    // (e2 = e3 = 0 there) stays 0, and the products with an infinite factor
+    // belong to cases that the selects below do not take
     const f2 m12 = add(m1, m2);
     const f2 v5 = mul(fma(mk(-0.5f), m12, d), rcp(m3));
-    const f2 m2m3 = mul(m2, m3);
-    const f2 v1 = mul(mul(mul(d, d), d), rcp(mul(mul(mk(6.0f), m1), m2m3)));
-    const f2 r1 = rcp(m1);
-    const f2 inv1 = make_float2(m1.x > 0.0f ? r1.x : 0.0f, m1.y > 0.0f ? r1.y : 0.0f);
+    const f2 r1 = rcp(m1), r23 = rcp(mul(mk(6.0f), mul(m2, m3)));
+    const f2 v1 = mul(mul(mul(d, d), d), mul(r1, r23));
+    const f2 inv1 = make_float2(fminf(r1.x, 3.40282347e38f), fminf(r1.y, 3.40282347e38f));
     const f2 e2 = fmax0(sub(d, m2)), e3 = fmax0(sub(d, m3));
     const f2 cub = fma(mul(e2, e2), e2, mul(mul(e3, e3), e3));
     f2 num = fma(mul(mk(3.0f), d), sub(d, m1), mul(m1, m1));
     num = fma(make_float2(-cub.x, -cub.y), inv1, num);
-    const f2 v24 = mul(num, rcp(mul(mk(6.0f), m2m3)));
+    const f2 v24 = mul(num, r23);
     f2 v = sel(lt(d, m1), v1, v24);
     v = sel(le(m12, d), v5, v);
     return make_float2(d0.x > 0.0f ? 1.0f - v.x : v.x, d0.y > 0.0f ? 1.0f - v.y : v.y);
