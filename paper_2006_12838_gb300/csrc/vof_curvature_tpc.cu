@@ -74,6 +74,8 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
                                            int64_t c, uint32_t flags) {
     const bool cm = (flags & PLIC_FLAG_NORMAL_CM) != 0;
     const float* p0 = phi + c;
+    // offsets within the field in 32 bits (list entries are int32 cell indices)
+    const int nxy32 = (int)nxy;
     // 1. stencil: normal sums (Eq. 38 weights or all 1) and interface mask
     float gx = 0.0f, gy = 0.0f, gz = 0.0f;
     unsigned mask = 0u;
@@ -84,7 +86,7 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
         constexpr int ex = p % 3 - 1, ey = (p / 3) % 3 - 1, ez = p / 9 - 1;
         constexpr int e2 = ex * ex + ey * ey + ez * ez;
         constexpr float wpy = e2 == 1 ? 4.0f : (e2 == 2 ? 2.0f : 1.0f);
-        const float v = __ldg(p0 + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
+        const float v = __ldg(p0 + (ex + ey * nx + ez * nxy32));
         const float w = cm ? 1.0f : wpy;
         if (ex != 0) gx = fmaf(w * (float)ex, v, gx);
         if (ey != 0) gy = fmaf(w * (float)ey, v, gy);
@@ -135,8 +137,8 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
         int ex1, ey1, ez1, ex2, ey2, ez2;
         e_of_lanes(i1, ex1, ey1, ez1);
         e_of_lanes(i2, ex2, ey2, ez2);
-        const float v1 = __ldg(p0 + ex1 + (int64_t)ey1 * nx + (int64_t)ez1 * nxy);
-        const float v2 = __ldg(p0 + ex2 + (int64_t)ey2 * nx + (int64_t)ez2 * nxy);
+        const float v1 = __ldg(p0 + (ex1 + ey1 * nx + ez1 * nxy32));
+        const float v2 = __ldg(p0 + (ex2 + ey2 * nx + ez2 * nxy32));
         const p2::f2 d0i = offset_two<METHOD>(pl, make_float2(v1, v2));
         float qx[2] = {(float)ex1, (float)ex2}, qy[2] = {(float)ey1, (float)ey2};
         float qz[2] = {(float)ez1, (float)ez2}, z[2];
