@@ -206,7 +206,8 @@ plic_status vof_interface_compact_noalloc(const float *phi, int nx, int ny, int 
  * sphere of radius R); PLIC_FLAG_KAPPA_PAPER_SIGN returns Eq. 42 as printed.
  * A degenerate normal (zero weighted gradient) or no interface neighbour gives
  * kappa = 0.  Every listed cell must have its 26 neighbours inside the field
- * (as vof_interface_compact guarantees); this is not re-checked. */
+ * (as vof_interface_compact guarantees); this is not re-checked.  Fields of
+ * at most 2^31 - 1 cells (PLIC_ERR_ARG otherwise), as for the compaction. */
 plic_status vof_curvature(const float *phi, int nx, int ny, int nz, const int32_t *idx,
                           int64_t n_iface, const int64_t *d_n_iface, float *kappa,
                           plic_method m, uint32_t flags, void *stream);

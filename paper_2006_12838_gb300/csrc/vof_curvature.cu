@@ -112,7 +112,9 @@ static plic_status curvature_entry(const float* phi, int nx, int ny, int nz, con
                                    int64_t n_iface, const int64_t* d_n_iface, float* out,
                                    plic_method m, uint32_t flags, float scale, void* stream,
                                    const char* who) {
-    if (nx < 3 || ny < 3 || nz < 3 || n_iface < 0) return PLIC_ERR_ARG;
+    // fields of at most 2^31 - 1 cells (int32 list entries; 32-bit stencil offsets)
+    if (nx < 3 || ny < 3 || nz < 3 || n_iface < 0 || (int64_t)nx * ny * nz > 2147483647LL)
+        return PLIC_ERR_ARG;
     if ((int)m < 0 || (int)m > 4 || (flags & ~kCurvFlags) || fit_mode(flags) < 0) return PLIC_ERR_ARG;
     if (n_iface == 0) return PLIC_OK;
     if (!phi || !idx || !out) return PLIC_ERR_ARG;
@@ -182,6 +184,7 @@ extern "C" plic_status vof_curvature_batched(const vof_field* fields, int n_fiel
     for (size_t i = 0; i < nf; ++i) {
         const vof_field& F = fields[i];
         if (F.nx < 3 || F.ny < 3 || F.nz < 3 || F.n_iface < 0 ||
+            (int64_t)F.nx * F.ny * F.nz > 2147483647LL ||
             (F.n_iface > 0 && (!F.phi || !F.idx || !F.kappa))) { free(pre); return PLIC_ERR_ARG; }
         if (!aligned(F.phi, 4) || !aligned(F.idx, 4) || !aligned(F.kappa, 4)) { free(pre); return PLIC_ERR_ALIGN; }
         pre[i + 1] = pre[i] + F.n_iface;

@@ -84,6 +84,7 @@ def test_host_side_argument_checks(lib):
     assert lib.vof_curvature(ok, 8, 8, 8, ok, 5, None, ok, 2, 8 | 16, None) == ERR_ARG
     assert lib.vof_curvature(ok, 8, 8, 8, ok, 5, None, ok, 2, 8 | 32, None) == ERR_ARG
     assert lib.vof_curvature(ok, 8, 8, 8, ok, 0, None, ok, 2, 0, None) == 0
+    assert lib.vof_curvature(ok, 2048, 2048, 513, ok, 5, None, ok, 2, 0, None) == ERR_ARG   # > 2^31 - 1 cells
     # compaction: workspace too small, unaligned workspace, oversized field
     assert lib.vof_interface_compact(ok, 64, 64, 64, ok, 10, ok, ok, 4, None) == ERR_ARG
     assert lib.vof_interface_compact(ok, 64, 64, 64, ok, 10, ok, P(264), 1 << 20, None) == ERR_ALIGN
