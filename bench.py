@@ -334,8 +334,11 @@ def section_curvature(dev, pk, steps):
         out["curvature_sz_opt_" + name] = {"ms": sec / steps * 1e3,
                                             "m_cells_s": k * steps / sec / 1e6}
         if fit == 0:
-            out["curvature_sz_opt_auto"]["roofline"] = curvature_roofline(k * steps / sec, m_mean, pk)
+            out["roofline"] = curvature_roofline(k * steps / sec, m_mean, pk)
+            out["roofline"]["of"] = "curvature_sz_opt_auto"
     for m in plic.METHODS:
+        if m == "sz_opt":
+            continue                                  # the default: timed above
         sec = timed(lambda: plic.curvature(phi, it, kappa=kap, method=m), steps, 2, s)
         out["curvature_%s_auto" % m] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
 
@@ -432,7 +435,8 @@ def section_batched(dev, pk, steps):
         sec = timed(lambda: plic.curvature_batched(args, flags=fit, tuning=shape), steps, 2, s)
         out["batched_" + name] = {"ms": sec / steps * 1e3, "m_cells_s": tot * steps / sec / 1e6}
         if fit == 0:
-            out["batched_auto"]["roofline"] = curvature_roofline(tot * steps / sec, m_mean, pk)
+            out["roofline"] = curvature_roofline(tot * steps / sec, m_mean, pk)
+            out["roofline"]["of"] = "batched_auto"
     # the other layout at its best tuning, for comparison
     if times:
         other = [c for c in times if c.endswith(", 8)" if shape[-1] == 1 else ", 1)")]
