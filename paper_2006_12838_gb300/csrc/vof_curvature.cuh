@@ -147,7 +147,9 @@ template <> struct FitReal<FIT_FP32> {
     static __device__ __forceinline__ R add(R a, R b) { return a + b; }
     static __device__ __forceinline__ R sub(R a, R b) { return a - b; }
     static __device__ __forceinline__ R mul(R a, R b) { return a * b; }
-    static __device__ __forceinline__ R div(R a, R b) { return a / b; }
+    // MUFU reciprocal and a multiply (2 ulp): the divisors are the LDL^T pivots,
+    // positive and far inside the normal range
+    static __device__ __forceinline__ R div(R a, R b) { return __fdividef(a, b); }
     static __device__ __forceinline__ float tof(R a) { return a; }
     static __device__ __forceinline__ bool gt(R a, R b) { return a > b; }
 };
@@ -330,18 +332,22 @@ struct CellPlic<M_SZ_OPT> {
     __device__ __forceinline__ void prepare(float nx, float ny, float nz) {
         const float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
         L = ax + ay + az;
-        const float il = 1.0f / L;
+        // MUFU reciprocals (no IEEE division): the thresholds only choose
+        // between case formulas that agree at the case boundaries
+        const float il = __fdividef(1.0f, L);
         m1 = fminf(fminf(ax, ay), az) * il;
         m3 = fmaxf(fmaxf(ax, ay), az) * il;
         m2 = fmaxf(1.0f - (m1 + m3), 0.0f);
         n12 = m1 + m2;
         const float m1m2 = m1 * m2, sq1 = m1 * m1;
         const float k23 = 6.0f * m2 * m3;
-        V5 = 0.5f * n12 / m3;                                    // case (5): V >= V5
-        V1 = k23 > 0.0f ? sq1 / k23 : 0.0f;                      // case (1): V < V1
-        V2 = k23 > 0.0f ? (sq1 - 3.0f * m2 * (m1 - m2)) / k23 : 0.0f;  // case (2): V < V2
+        const float rk = k23 > 0.0f ? __fdividef(1.0f, k23) : 0.0f;
+        inv1 = m1 > 0.0f ? __fdividef(1.0f, m1) : 0.0f;
+        V5 = 0.5f * n12 * __fdividef(1.0f, m3);                  // case (5): V >= V5
+        V1 = sq1 * rk;                                           // case (1): V < V1
+        V2 = (sq1 - 3.0f * m2 * (m1 - m2)) * rk;                 // case (2): V < V2
         const float num3 = m3 * m3 * (3.0f * n12 - m3) + sq1 * (m1 - 3.0f * m3) + m2 * m2 * (m2 - 3.0f * m3);
-        V3 = (m3 < n12 && m1m2 > 0.0f) ? num3 / (k23 * m1) : 3.4e38f;  // case (3): V < V3
+        V3 = (m3 < n12 && m1m2 > 0.0f) ? num3 * rk * inv1 : 3.4e38f;  // case (3): V < V3
         const float t32 = 2.0f * m1m2;
         const float r3 = t32 > 0.0f ? rsqrtf(t32) : 0.0f;
         t3 = t32 * r3;
@@ -354,7 +360,6 @@ struct CellPlic<M_SZ_OPT> {
         k2a = 8.0f * m2 * m3;
         k2b = sq1 * (1.0f / 3.0f);
         cb1 = Fm<float>::cbrt_(k23 * m1);
-        inv1 = m1 > 0.0f ? 1.0f / m1 : 0.0f;
         k6 = k23;
     }
     __device__ __forceinline__ float offset(float V0) const {

@@ -94,9 +94,9 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
         if (v > 0.0f && v < 1.0f) mask |= 1u << i;
     });
     // 2. normal and frame (Sec. 4.2)
-    const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
-    if (!(gl > 0.0f)) return 0.0f;                     // undefined normal: kappa = 0
-    const float inv = -1.0f / gl;
+    const float gl2 = gx * gx + gy * gy + gz * gz;
+    if (!(gl2 > 0.0f)) return 0.0f;                    // undefined normal: kappa = 0
+    const float inv = -rsqrtf(gl2);
     const float nx_ = gx * inv, ny_ = gy * inv, nz_ = gz * inv;
     float rx = 0.56270900f, ry = 0.32704452f, rz = 0.75921047f;
     float byx = ny_ * rz - nz_ * ry, byy = nz_ * rx - nx_ * rz, byz = nx_ * ry - ny_ * rx;
