@@ -661,7 +661,7 @@ def main():
     from paper_2006_12838_gb300 import build as B
     from paper_2006_12838_gb300 import dist as D
     from paper_2006_12838_gb300 import plic
-    from paper_2006_12838_gb300.pipeline import HostOffsetPipeline
+    from paper_2006_12838_gb300.pipeline import HostOffsetPipeline, MappedHostOffset
 
     rank, world, local = D.rank_info()
     torch.cuda.set_device(local)
@@ -715,32 +715,62 @@ def main():
     rt_max = float(rt.max().item())
     rt_mean = float(rt.double().mean().item())
 
-    # e2e: same step through the ABI from pinned host buffers (H2D + D2H in the timed region)
+    # e2e: same step through the ABI from pinned host buffers (H2D + D2H in the timed region).
+    # Two ways: zero copy (the kernel reads the pinned host arrays and writes the
+    # pinned results over the host link itself, one launch per step) and staged
+    # (chunked copies on three streams around the same kernel, one CUDA graph).
+    # The line's value is the faster; both are reported.
     e2e = None
     try:
         hn = [x.cpu().pin_memory() for x in t32]
         hd = torch.empty(CELLS, dtype=torch.float32).pin_memory()
         hV = torch.empty(CELLS, dtype=torch.float32).pin_memory()
-        pipe = HostOffsetPipeline(1 << 24, torch.float32, dev, "sz_opt", "fp32p")
         esteps = max(3, min(args.steps, 10))
-        mode = "cuda graph of the 3-stream pipeline"
+
+        def time_steps(step_e2e):
+            for _ in range(2):
+                step_e2e()
+            torch.cuda.synchronize()
+            D.barrier()
+            per = []
+            for _ in range(esteps):
+                t0 = time.perf_counter()
+                step_e2e()
+                torch.cuda.synchronize()
+                per.append(time.perf_counter() - t0)
+            return D.max_over_ranks(sum(per), dev), per
+
+        modes = {}
+        try:
+            mapped = MappedHostOffset(dev, "sz_opt", "fp32p")
+            msec, mper = time_steps(lambda: mapped.run(*hn, hd, hV))
+            # the zero-copy results against the device-resident run of the same step
+            same = bool(torch.equal(hd, d0.cpu()) and torch.equal(hV, Vrt.cpu()))
+            modes["zero_copy"] = {"value": CELLS * world * esteps / msec / 1e9,
+                                  "step_ms": [round(x * 1e3, 2) for x in mper],
+                                  "median_step_ms": float(np.median(mper) * 1e3),
+                                  "launches_per_step": 1, "results_equal_device_run": same,
+                                  "how": "plic_offset_roundtrip on the device addresses of the "
+                                         "pinned host arrays (plic_host_device_pointer): the "
+                                         "kernel streams 16 B/cell in and 8 B/cell out over "
+                                         "NVLink-C2C"}
+        except Exception as ex:  # report, do not hide
+            modes["zero_copy"] = {"value": None, "error": repr(ex)[:200]}
+        pipe = HostOffsetPipeline(1 << 24, torch.float32, dev, "sz_opt", "fp32p")
+        how = "cuda graph of the 3-stream pipeline"
         try:
             graph = pipe.capture(*hn, hd, hV)
-            step_e2e = graph.replay
+            step_staged = graph.replay
         except Exception as ex:  # report the fallback, do not hide it
-            mode = "3-stream pipeline, eager (graph capture failed: %s)" % repr(ex)[:80]
-            step_e2e = lambda: pipe.run(*hn, hd, hV)  # noqa: E731
-        for _ in range(2):
-            step_e2e()
-        torch.cuda.synchronize()
-        D.barrier()
-        per = []
-        for _ in range(esteps):
-            t0 = time.perf_counter()
-            step_e2e()
-            torch.cuda.synchronize()
-            per.append(time.perf_counter() - t0)
-        esec = D.max_over_ranks(sum(per), dev)
+            how = "3-stream pipeline, eager (graph capture failed: %s)" % repr(ex)[:80]
+            step_staged = lambda: pipe.run(*hn, hd, hV)  # noqa: E731
+        ssec, sper = time_steps(step_staged)
+        modes["staged"] = {"value": CELLS * world * esteps / ssec / 1e9,
+                           "step_ms": [round(x * 1e3, 2) for x in sper],
+                           "median_step_ms": float(np.median(sper) * 1e3),
+                           "chunk_cells": 1 << 24, "launches_per_step": pipe.launches,
+                           "how": "pinned host SoA -> chunked H2D / plic_offset_roundtrip / D2H "
+                                  "on 3 streams (%s)" % how}
         # the host link alone: one 1 GiB pinned host -> device copy
         tmp = torch.empty_like(t32[0])
         torch.cuda.synchronize()
@@ -749,14 +779,13 @@ def main():
         torch.cuda.synchronize()
         link = hn[0].numel() * 4 / (time.perf_counter() - t0) / 1e9
         del tmp
-        e2e = {"value": CELLS * world * esteps / esec / 1e9, "unit": UNIT,
+        best = max((m for m in modes if modes[m].get("value")), key=lambda m: modes[m]["value"])
+        e2e = {"value": modes[best]["value"], "unit": UNIT, "mode": best,
                "h2d_bytes_per_step": 16 * CELLS, "d2h_bytes_per_step": 8 * CELLS,
-               "steps": esteps, "chunk_cells": 1 << 24,
-               "step_ms": [round(x * 1e3, 2) for x in per],
-               "median_step_ms": float(np.median(per) * 1e3), "h2d_link_gbs": link,
-               "note": "pinned host SoA -> chunked H2D / plic_offset_roundtrip / D2H on 3 streams "
-                       "(%s); value from the total wall clock of all steps, a device sync "
-                       "after each" % mode}
+               "steps": esteps, "median_step_ms": modes[best]["median_step_ms"],
+               "h2d_copy_gbs": link, "modes": modes,
+               "note": "value from the total wall clock of all steps, a device sync after each; "
+                       "the faster of the two host paths"}
         del hn, hd, hV, pipe
     except Exception as ex:  # report, do not hide
         e2e = {"value": None, "unit": UNIT, "error": repr(ex)[:200],

@@ -8,7 +8,11 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * - Every data pointer is caller-owned DEVICE memory (cudaMalloc'd or a torch
- *   tensor's storage), contiguous, structure-of-arrays.  The library never
+ *   tensor's storage) or page-locked host memory mapped into the device's
+ *   address space, passed as the address plic_host_device_pointer() returns
+ *   for it (the kernels then read and write it over the host link; on a
+ *   Grace-Blackwell node that is NVLink-C2C); contiguous, structure-of-arrays.
+ *   The library never
  *   keeps a pointer after the call returns and allocates nothing; scratch
  *   memory is passed in as `workspace` (size from plic_workspace_bytes()).
  * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
@@ -333,6 +337,18 @@ const char *plic_last_error(void);
 
 /* Library version, for the binding's load check. */
 int plic_abi_version(void);
+
+/* plic_host_device_pointer -- the address under which the current device
+ * reaches page-locked host memory (cudaHostAlloc / cudaMallocHost memory, or
+ * cudaHostRegister'ed memory registered as mapped; on a unified-address system
+ * every page-locked allocation is mapped and the address equals host_ptr).
+ * The result may be passed to any entry point in place of a device array:
+ * the kernels then move the data over the host link themselves (no staging
+ * copy).  Any other memory (pageable host memory, device memory, an unknown
+ * address) returns PLIC_ERR_ARG and leaves *dev_ptr untouched, so that nothing
+ * is ever launched on an address the device cannot reach.  Host-side query
+ * only (cudaPointerGetAttributes); no launch, no synchronisation. */
+plic_status plic_host_device_pointer(const void *host_ptr, void **dev_ptr);
 
 #ifdef __cplusplus
 }

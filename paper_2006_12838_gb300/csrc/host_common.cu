@@ -99,4 +99,17 @@ const char* plic_last_error(void) { return plic::g_last_error; }
 
 int plic_abi_version(void) { return 1; }
 
+plic_status plic_host_device_pointer(const void* host_ptr, void** dev_ptr) {
+    if (!host_ptr || !dev_ptr) return PLIC_ERR_ARG;
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, host_ptr);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();           // an unknown address is an answer, not a failure
+        return PLIC_ERR_ARG;
+    }
+    if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return PLIC_ERR_ARG;
+    *dev_ptr = a.devicePointer;
+    return PLIC_OK;
+}
+
 }  // extern "C"

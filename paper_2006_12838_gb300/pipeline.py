@@ -1,18 +1,58 @@
 """Host-buffer entry points: PLIC offsets for arrays that live in (pinned) host
-memory, streamed through the device in chunks.
+memory.
 
-The GPU work is the same C ABI call as :func:`plic.offset`; this module only
-stages data: chunk i is copied host->device on one stream while chunk i-1 is
-solved on a second and chunk i-2 is copied back on a third, so the copies over
-the host link and the kernels overlap.  Host arrays should be pinned
-(``tensor.pin_memory()``) for the copies to be asynchronous; ``capture`` turns a
-whole pass into one CUDA graph.
+Two ways, the same C ABI call as :func:`plic.offset` / :func:`plic.offset_roundtrip`:
+
+- :class:`MappedHostOffset` (zero copy): the kernel is given the device
+  addresses of the pinned host arrays (``plic_host_device_pointer``) and reads
+  its inputs and writes its results over the host link itself, one launch per
+  pass, no staging buffers.  On a Grace-Blackwell node the link is NVLink-C2C
+  and the kernel's streaming loads keep it busy in both directions at once.
+- :class:`HostOffsetPipeline` (staged): chunk i is copied host->device on one
+  stream while chunk i-1 is solved on a second and chunk i-2 is copied back on a
+  third, so the copies and the kernels overlap; ``capture`` turns a whole pass
+  into one CUDA graph.  For hosts whose memory the device cannot map.
 """
 from __future__ import annotations
+
+import ctypes
 
 import torch
 
 from . import plic
+
+
+class MappedHostOffset:
+    """Zero-copy solve of pinned host arrays: ``run(nx, ny, nz, V0, d0_out,
+    V_out=None)`` launches plic_offset (or plic_offset_roundtrip when V_out is
+    given) on the device addresses of the host tensors, on the current stream.
+    Every tensor must be a contiguous pinned CPU tensor of the same length (the
+    address query raises PlicError otherwise, before anything is launched)."""
+
+    def __init__(self, device="cuda", method="sz_opt", precision=None):
+        self.device = torch.device(device)
+        self.method = method
+        self.precision = precision
+        self.launches = 0
+
+    def run(self, nx, ny, nz, V0, d0_out, V_out=None):
+        n = V0.numel()
+        ts = [nx, ny, nz, V0, d0_out] + ([V_out] if V_out is not None else [])
+        for t in ts:
+            if t.numel() != n or t.dtype != V0.dtype:
+                raise plic.PlicError("host arrays must have one length and dtype")
+        ptrs = [plic.host_device_pointer(t) for t in ts]
+        p = plic._prec(V0.dtype, self.precision)
+        m = plic.METHODS[self.method] if isinstance(self.method, str) else int(self.method)
+        stream = ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        P = ctypes.c_void_p
+        if V_out is not None:
+            st = plic.load().plic_offset_roundtrip(*[P(x) for x in ptrs], n, m, p, 0, None, stream)
+            plic._check(st, "plic_offset_roundtrip (host-mapped)")
+        else:
+            st = plic.load().plic_offset(*[P(x) for x in ptrs], n, m, p, 0, None, stream)
+            plic._check(st, "plic_offset (host-mapped)")
+        self.launches = 1
 
 
 class HostOffsetPipeline:

@@ -97,6 +97,8 @@ def load():
         L.plic_last_error.argtypes = []
         L.plic_last_error.restype = ctypes.c_char_p
         L.plic_abi_version.restype = ctypes.c_int
+        L.plic_host_device_pointer.argtypes = [P, ctypes.POINTER(ctypes.c_void_p)]
+        L.plic_host_device_pointer.restype = ctypes.c_int
         if L.plic_abi_version() != 1:
             raise PlicError("libplic.so ABI version mismatch")
         _lib = L
@@ -143,6 +145,17 @@ def _prec(dtype, precision):
     if dtype != want:
         raise PlicError("precision %s needs %s tensors" % (precision, want))
     return p
+
+
+def host_device_pointer(t) -> int:
+    """Device address of a page-locked (pinned) CPU tensor's storage, for the
+    zero-copy entry points; raises PlicError for any other tensor."""
+    if t.is_cuda or not t.is_contiguous():
+        raise PlicError("expected a contiguous pinned CPU tensor")
+    out = ctypes.c_void_p()
+    _check(load().plic_host_device_pointer(ctypes.c_void_p(t.data_ptr()), ctypes.byref(out)),
+           "plic_host_device_pointer (is the tensor pinned?)")
+    return int(out.value)
 
 
 def volume(nx, ny, nz, d0, out=None, stream=None):

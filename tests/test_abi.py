@@ -89,6 +89,10 @@ def test_host_side_argument_checks(lib):
     assert lib.vof_interface_compact(ok, 64, 64, 64, ok, 10, ok, ok, 4, None) == ERR_ARG
     assert lib.vof_interface_compact(ok, 64, 64, 64, ok, 10, ok, P(264), 1 << 20, None) == ERR_ALIGN
     assert lib.vof_interface_compact(ok, 2048, 2048, 1024, ok, 10, ok, ok, 1 << 30, None) == ERR_ARG
+    # host-mapped address query: null arguments
+    out = ctypes.c_void_p()
+    assert lib.plic_host_device_pointer(None, ctypes.byref(out)) == ERR_ARG
+    assert lib.plic_host_device_pointer(ok, None) == ERR_ARG
     # batched: bad tuning
     tun = plic.VofTuning(48, 16, 1)
     f = (plic.VofField * 1)()
