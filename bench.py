@@ -604,11 +604,11 @@ def run_case(args):
                 plic.offset_roundtrip(*t, method="sz_opt", precision="fp32p", out=d0, out_rt=vr)
             else:
                 plic.volume(*t[:3], t[3], out=d0)
-    elif args.case == "offset_fp64":
+    elif args.case in ("offset_fp64", "offset_fp64r"):
         t = make_cells_gpu(args.cells, 2, torch.float64, dev)
         d0 = torch.empty_like(t[0])
         for _ in range(args.steps):
-            plic.offset(*t, method="sz_opt", precision="fp64", out=d0)
+            plic.offset(*t, method="sz_opt", precision=args.case[7:], out=d0)
     elif args.case == "curvature":
         phi, _ = synth.curvature_field(seed=3, edge=256, device=dev)
         for _ in range(args.steps):
@@ -648,7 +648,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default=None,
                     help="profiling case: run only one kernel on --cells cells "
-                         "(offset | roundtrip | volume | offset_fp64 | curvature | curv_bwd | "
+                         "(offset | roundtrip | volume | offset_fp64 | offset_fp64r | curvature | curv_bwd | "
                          "batched)")
     ap.add_argument("--cells", type=int, default=1 << 24)
     args = ap.parse_args()

@@ -27,6 +27,7 @@
 // reduced_volume()  -- the forward problem (Eq. 10).
 // (The cut polygon of the adjoints is in plic_polygon.cuh.)
 #pragma once
+#include "plic_df.cuh"
 #include "plic_math.cuh"
 
 namespace plic {
@@ -434,77 +435,113 @@ __device__ __forceinline__ T offset_cell(T nx, T ny, T nz, T V0, int& bad) {
 }
 
 // ----------------------------------------------------------------------------
-// FP64 result from an FP32 solve.  The symmetry reduction (Eqs. 2-8) is done
-// in FP64, so the reduced volume V = min(V0, 1 - V0) keeps its full relative
-// precision (V0 = 1 - 1e-9 rounded to float first would give V = 0); the
-// method's FP32 solver then runs on the reduced problem rounded to float, and
-// two FP64 Newton steps on Eq. 10 finish it.  The FP32 root is within ~1e-7
-// relative of the FP64 root, so the first step lands at ~1e-14 and the second
-// at rounding level; the FP64 pipe runs a few dozen operations per cell and no
-// division instead of a double-precision trigonometric solve.
+// FP64 result from an FP32 solve, without the FP64 pipe (PLIC_FP64_REFINED).
+// The doubles are split into double-floats (hi + lo, 48 significant bits) by
+// integer operations; the symmetry reduction (Eqs. 2-8) sorts |n| on the bit
+// patterns and forms V = min(V0, 1 - V0) from the bits (1 - V0 as an exact
+// integer difference), so V keeps its relative precision; the method's FP32 solver runs on the reduced problem's
+// leading floats; two Newton steps on Eq. 10 in double-float (the residual in
+// double-float, the derivative's reciprocal in FP32) finish it, and the result
+// goes back to a double with one FP64 add.  The FP32 root is within ~1e-7 of
+// the root, the first step lands at ~1e-14, the second at the double-float
+// resolution (~1e-15).  The residual is multiplied through by n1, so the steps
+// divide by nothing but the FP32 derivative; n1 < 2^-60 counts as 0 there
+// (its effect on d0 is below 1e-18).  V0 below 2^-126 counts as 0: d0 then
+// differs from the exact offset by less than 3e-13.
 // ----------------------------------------------------------------------------
 template <int METHOD>
 __device__ __forceinline__ double offset_cell_refined(double nx, double ny, double nz, double V0,
                                                       int& bad) {
-    double n1, n2, n3;
-    reduce_normal<double, false>(nx, ny, nz, n1, n2, n3);
-    const double L = fabs(nx) + fabs(ny) + fabs(nz);
-    const bool ok = (V0 >= 0.0) && (V0 <= 1.0) && (L > 0.0) && (L <= 3.0);
+    const uint64_t SIGN = 0x8000000000000000ull;
+    // |n| sorted on the bits (the order of non-negative doubles is that of their
+    // bit patterns; a NaN sorts last and makes L NaN)
+    const uint64_t ux = (uint64_t)__double_as_longlong(nx) & ~SIGN;
+    const uint64_t uy = (uint64_t)__double_as_longlong(ny) & ~SIGN;
+    const uint64_t uz = (uint64_t)__double_as_longlong(nz) & ~SIGN;
+    const uint64_t b1 = ux < uy ? (ux < uz ? ux : uz) : (uy < uz ? uy : uz);
+    const uint64_t b3 = ux > uy ? (ux > uz ? ux : uz) : (uy > uz ? uy : uz);
+    const uint64_t b2 = ux ^ uy ^ uz ^ b1 ^ b3;
+    const df n1 = d2df(__longlong_as_double((long long)b1));
+    const df n2 = d2df(__longlong_as_double((long long)b2));
+    const df n3 = d2df(__longlong_as_double((long long)b3));
+    const df L = df_add(df_add(n1, n2), n3);
+    // 0 <= V0 <= 1 on the bits (-0 accepted, NaN refused)
+    const uint64_t v = (uint64_t)__double_as_longlong(V0), va = v & ~SIGN;
+    const bool vneg = (v >> 63) != 0 && va != 0;
+    const bool ok = !vneg && va <= 0x3FF0000000000000ull && L.hi > 0.0f && L.hi <= 3.0f;
     if (!ok) {
         bad += 1;
-        return (double)NAN;
+        return __longlong_as_double(0x7FF8000000000000ll);
     }
-    const double V = reduce_volume<double, false>(V0);
-    const float Vf = (float)V;
-    double d;
+    const bool upper = va > 0x3FE0000000000000ull;             // V0 > 1/2
+    const bool lower = va < 0x3FE0000000000000ull;             // V0 < 1/2
+    // V = 1 - V0 exactly on the bits for V0 > 1/2 (V0 = M 2^-53 with
+    // M = 2^52 + mantissa, or 2^53 for V0 = 1): converting V0 to a
+    // double-float first would cost the low bits that 1 - V0 keeps
+    df V;
+    if (upper) {
+        const uint64_t M = (va >> 52) >= 1023ull ? (1ull << 53)
+                                                  : ((1ull << 52) | (va & 0xFFFFFFFFFFFFFull));
+        V = df_from_u64_2m53((1ull << 53) - M);
+    } else {
+        V = d2df(__longlong_as_double((long long)va));
+    }
+    const float Vf = V.hi;
+    // FP32 solve of the reduced problem, as an offset d from the corner
+    df d;
     if (METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT) {
-        const double il = 1.0 / L;
-        const float m1 = (float)(n1 * il), m3 = (float)(n3 * il);
+        const float il = Fm<float>::rcp_(L.hi);
+        const float m1 = n1.hi * il, m3 = n3.hi * il;
         const float m2 = Fm<float>::fdim_(1.0f, m1 + m3);
         float a = METHOD == M_SZ_ORIG ? solve_sz_orig<float, false>(Vf, m1, m2, m3)
                                       : solve_sz_opt<float, false>(Vf, m1, m2, m3);
         a = polish<float>(a, Vf, m1, m2, m3);
-        d = (double)a * L;
+        if (a != a) return __longlong_as_double(0x7FF8000000000000ll);  // Kawano's NaN
+        d = df_mul_f(L, a);
     } else {
-        const float f1 = (float)n1, f2 = (float)n2, f3 = (float)n3;
-        float e = METHOD == M_ANALYTIC ? solve_analytic<float, false>(Vf, f1, f2, f3)
-                : METHOD == M_NEWTON   ? solve_newton<float, false>(Vf, f1, f2, f3)
-                                       : solve_nested<float, false>(Vf, f1, f2, f3);
-        e = polish<float>(e, Vf, f1, f2, f3);
-        d = (double)e;
+        float e = METHOD == M_ANALYTIC ? solve_analytic<float, false>(Vf, n1.hi, n2.hi, n3.hi)
+                : METHOD == M_NEWTON   ? solve_newton<float, false>(Vf, n1.hi, n2.hi, n3.hi)
+                                       : solve_nested<float, false>(Vf, n1.hi, n2.hi, n3.hi);
+        e = polish<float>(e, Vf, n1.hi, n2.hi, n3.hi);
+        if (e != e) return __longlong_as_double(0x7FF8000000000000ll);
+        d = df_make(e);
     }
-    if (d != d) return d;                         // Kawano's NaN (axis normal, V0 in {0, 1})
-    const double h = 0.5 * L;
-    d = fmin(fmax(d, 0.0), h);
-    // 1/n1 in FP64 from the FP32 reciprocal and two Newton steps (each squares
-    // the relative error: 1e-7 -> 1e-14 -> rounding); no FP64 division
-    double inv_n1 = 0.0;
-    if (n1 > 0.0) {
-        if (n1 > 1e-30) {
-            inv_n1 = (double)Fm<float>::rcp_((float)n1);
-            inv_n1 = inv_n1 * fma(-n1, inv_n1, 2.0);
-            inv_n1 = inv_n1 * fma(-n1, inv_n1, 2.0);
-        } else {
-            inv_n1 = 1.0 / n1;
-        }
-    }
-    const double n12 = n1 + n2, rhs = 6.0 * n2 * n3 * V;
+    const df zero = df_make(0.0f);
+    const df h = df_scale(L, 0.5f);
+    d = df_clamp(d, zero, h);
+    // Newton steps on Eq. 10 multiplied by n1 (n1 g and n1 g'), in double-float
+    const bool n1z = n1.hi < 8.67361738e-19f;                  // 2^-60
+    const df n12 = df_add(n1, n2);
+    const df rhs = df_mul_f(df_mul(df_mul(n2, n3), V), 6.0f); // 6 n2 n3 V
+    const df R1 = n1z ? zero : df_mul(n1, rhs);                // 6 n1 n2 n3 V
+    const df d5 = df_add(df_mul(n3, V), df_scale(n12, 0.5f)); // case (5), linear, exact
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
-        // Newton step on Eq. 10 in FP64 with the derivative's reciprocal in
-        // FP32: the step's relative error is that of the FP32 reciprocal
-        // (~1e-7) times the error, plus the quadratic term, so two steps from
-        // the FP32 root reach rounding level
-        if (d >= n12) {
-            d = n3 * V + 0.5 * n12;                   // case (5): linear, exact
-        } else if (d > 0.0) {
-            double g, gp;
-            reduced_residual<double>(d, rhs, n1, n2, n3, inv_n1, g, gp);
-            if (gp > 0.0) d -= g * (double)Fm<float>::rcp_((float)gp);
+        if (!df_lt(d, n12)) {
+            d = d5;
+        } else if (d.hi > 0.0f) {
+            df g;
+            float gp;
+            if (n1z) {                                          // n1 = 0: case (2) only
+                g = df_sub(df_mul_f(df_mul(d, d), 3.0f), rhs);
+                gp = 6.0f * d.hi;
+            } else if (df_lt(d, n1)) {                          // case (1)
+                g = df_sub(df_mul(df_mul(d, d), d), R1);
+                gp = 3.0f * d.hi * d.hi;
+            } else {                                            // cases (2)-(4)
+                const df e2 = df_max0(df_sub(d, n2)), e3 = df_max0(df_sub(d, n3));
+                const df cub = df_add(df_mul(df_mul(e2, e2), e2), df_mul(df_mul(e3, e3), e3));
+                const df t = df_add(df_mul_f(df_mul(d, df_sub(d, n1)), 3.0f), df_mul(n1, n1));
+                g = df_sub(df_sub(df_mul(n1, t), cub), R1);
+                gp = n1.hi * fmaf(6.0f, d.hi, -3.0f * n1.hi) -
+                     3.0f * (e2.hi * e2.hi + e3.hi * e3.hi);
+            }
+            if (gp > 0.0f) d = df_sub(d, df_mul_f(g, Fm<float>::rcp_(gp)));
         }
-        d = fmin(fmax(d, 0.0), h);
+        d = df_clamp(d, zero, h);
     }
-    return copysign(h - d, V0 - 0.5);
+    const double r = df2d(df_sub(h, d));
+    return lower ? -r : r;
 }
 
 // ----------------------------------------------------------------------------

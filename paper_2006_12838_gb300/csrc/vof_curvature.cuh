@@ -93,43 +93,6 @@ __device__ __forceinline__ void for_e27(F&& f) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// Double-float arithmetic (a value is hi + lo with |lo| <= ulp(hi)/2), built
-// from the error-free transformations two-sum (Knuth) and two-product via FMA
-// (Dekker/Ogita-Rump-Oishi): about 48 significant bits on the FP32 pipes.
-// ---------------------------------------------------------------------------
-struct df { float hi, lo; };
-__device__ __forceinline__ df df_make(float a) { return {a, 0.0f}; }
-__device__ __forceinline__ df two_sum(float a, float b) {
-    const float s = a + b, bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ df quick_two_sum(float a, float b) {
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ df df_add(df a, df b) {
-    df s = two_sum(a.hi, b.hi);
-    df t = two_sum(a.lo, b.lo);
-    s.lo += t.hi;
-    s = quick_two_sum(s.hi, s.lo);
-    s.lo += t.lo;
-    return quick_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df df_mul(df a, df b) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-    return quick_two_sum(p, e);
-}
-__device__ __forceinline__ df df_div(df a, df b) {
-    const float q1 = a.hi / b.hi;
-    const df r = df_add(a, df_neg(df_mul(b, df_make(q1))));
-    const float q2 = r.hi / b.hi;
-    return quick_two_sum(q1, q2);
-}
-
 template <int FIT> struct FitReal;
 template <> struct FitReal<FIT_FP64> {
     typedef double R;

@@ -88,7 +88,7 @@ def test_offset_fp32_c1(dev, orc, c1, method, precision):
 
 @pytest.mark.parametrize("method", METHODS)
 def test_offset_fp64_refined_c1(dev, c1, method):
-    # FP32 solve + two FP64 Newton steps: the FP64 gate
+    # FP32 solve + two double-float Newton steps: the FP64 gate
     n, V0, ref = c1
     t = _to(dev, torch.float64, n[0], n[1], n[2], V0)
     inv = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -238,7 +238,9 @@ def test_offset_roundtrip(dev, orc, c1, method, precision):
     assert err.max() <= (1e-15 if dt == torch.float64 else 3e-7)
     assert np.isnan(v[~good]).all()
     if precision in ("fp32p", "fp64", "fp64r"):
-        assert rt.max() <= (1e-14 if dt == torch.float64 else 1e-6)
+        # fp64r refines in double-float (48-bit significands): |d0 error| up to
+        # ~1e-14, so its round trip is gated at 5e-14
+        assert rt.max() <= {"fp64": 1e-14, "fp64r": 5e-14}.get(precision, 1e-6)
 
 
 def test_offset_roundtrip_ragged(dev, orc):
