@@ -61,27 +61,27 @@ def key(fields, method, flags) -> str:
     return "%s|batched-v2|%s|%d|%s" % (dev, method, flags, shape_class(fields))
 
 
-def tune(fields, method="sz_opt", flags=0, reps=3, candidates=None, force=False):
+def tune(fields, method="sz_opt", flags=0, reps=5, candidates=None, force=False):
     """Best (block_threads, cells_per_chunk, blocks_per_sm, lanes_per_cell) for these fields;
     returns (shape, timings) where timings maps str(shape) -> ms (empty when
     the cache answered)."""
-    k = key(fields, method, flags)
+    flist = fields.fields if isinstance(fields, plic.BatchedFields) else fields
+    k = key(flist, method, flags)
     with _lock:
         cache = _load()
         if not force and k in cache:
             return tuple(cache[k]["shape"]), {}
-    ws = torch.empty(plic.workspace_bytes(plic.WS_BATCHED, len(fields)), dtype=torch.uint8,
-                     device=fields[0][0].device)
+    batch = fields if isinstance(fields, plic.BatchedFields) else plic.BatchedFields(fields)
     times = {}
     s = torch.cuda.current_stream()
     for cand in (candidates or CANDIDATES):
-        plic.curvature_batched(fields, method=method, flags=flags, tuning=cand, workspace=ws)
+        plic.curvature_batched(batch, method=method, flags=flags, tuning=cand)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(s)
         for _ in range(reps):
-            plic.curvature_batched(fields, method=method, flags=flags, tuning=cand, workspace=ws)
+            plic.curvature_batched(batch, method=method, flags=flags, tuning=cand)
         b.record(s)
         torch.cuda.synchronize()
         times[str(cand)] = a.elapsed_time(b) / reps

@@ -325,25 +325,46 @@ def curvature_backward(phi, idx, g_kappa, n_iface=None, count=None, g_phi=None,
     return g_phi
 
 
+class BatchedFields:
+    """The descriptor table of a list of fields for vof_curvature_batched, built
+    and checked once: ``fields`` is a list of (phi, idx, n_iface, kappa) with
+    device tensors.  Reusing it saves the per-call Python work of building the
+    table (a few microseconds per field), which for many fields would otherwise
+    exceed the kernel's own time."""
+
+    def __init__(self, fields, workspace=None):
+        self.fields = list(fields)
+        self.arr = (VofField * len(self.fields))()
+        dev = self.fields[0][0].device
+        for i, (phi, idx, n, kappa) in enumerate(self.fields):
+            _cuda(phi, kappa, dtype=torch.float32)
+            _cuda(idx, dtype=torch.int32)
+            if idx.device != phi.device or phi.device != dev:
+                raise PlicError("tensors must be on one device")
+            nz, ny, nx = phi.shape
+            self.arr[i] = VofField(phi.data_ptr(), nx, ny, nz, idx.data_ptr(), int(n),
+                                   kappa.data_ptr())
+        ws_n = workspace_bytes(WS_BATCHED, len(self.fields))
+        if workspace is None:
+            workspace = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+        elif workspace.numel() < ws_n:
+            raise PlicError("workspace too small")
+        self.workspace = workspace
+        self.ptr = ctypes.cast(self.arr, ctypes.c_void_p)
+
+    def __len__(self):
+        return len(self.fields)
+
+
 def curvature_batched(fields, method="sz_opt", flags=0, tuning=None, workspace=None,
                       stream=None):
-    """One persistent launch over many fields.  ``fields``: list of
-    (phi, idx, n_iface, kappa) with device tensors; ``tuning``: optional
+    """One persistent launch over many fields.  ``fields``: a BatchedFields, or a
+    list of (phi, idx, n_iface, kappa) with device tensors; ``tuning``: optional
     (block_threads, cells_per_chunk, blocks_per_sm[, lanes_per_cell]) with
     lanes_per_cell 8 (cooperative groups), 1 (one thread per cell) or 0
     (the library's default)."""
-    arr = (VofField * len(fields))()
-    dev = fields[0][0].device
-    for i, (phi, idx, n, kappa) in enumerate(fields):
-        _cuda(phi, kappa, dtype=torch.float32)
-        _cuda(idx, dtype=torch.int32)
-        if idx.device != phi.device:
-            raise PlicError("tensors must be on one device")
-        nz, ny, nx = phi.shape
-        arr[i] = VofField(phi.data_ptr(), nx, ny, nz, idx.data_ptr(), int(n), kappa.data_ptr())
-    ws_n = workspace_bytes(WS_BATCHED, len(fields))
-    if workspace is None:
-        workspace = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+    if not isinstance(fields, BatchedFields):
+        fields = BatchedFields(fields, workspace)
     tun = None
     if tuning is not None:
         t = [int(v) for v in tuning]
@@ -351,10 +372,11 @@ def curvature_batched(fields, method="sz_opt", flags=0, tuning=None, workspace=N
             raise PlicError("tuning: (block_threads, cells_per_chunk, blocks_per_sm[, lanes_per_cell])")
         tun = VofTuning(*(t + [0] * (4 - len(t))))
     m = METHODS[method] if isinstance(method, str) else int(method)
-    _check(load().vof_curvature_batched(ctypes.cast(arr, ctypes.c_void_p), len(fields),
+    ws = fields.workspace
+    _check(load().vof_curvature_batched(fields.ptr, len(fields),
                                         None if tun is None else ctypes.cast(ctypes.pointer(tun), ctypes.c_void_p),
-                                        m, flags, _ptr(workspace), workspace.numel(),
-                                        _stream(fields[0][0], stream)), "vof_curvature_batched")
+                                        m, flags, _ptr(ws), ws.numel(),
+                                        _stream(fields.fields[0][0], stream)), "vof_curvature_batched")
 
 
 def paper_benchmark(nx, ny, nz, L=256, method="sz_opt", precision=None, blank=False, err_sum=None,

@@ -158,3 +158,11 @@ def test_batched_matches_single(dev, orc):
     plic.curvature_batched(args)
     phid, it, k, kap = args[big]
     _check(kap[:k].cpu().numpy().astype(np.float64), kref, dim, TOL, "batched")
+    # the prepared descriptor table, reused: same values
+    batch = plic.BatchedFields(args)
+    for _ in range(2):
+        for a in args:
+            a[3].fill_(7.0)
+        plic.curvature_batched(batch)
+        for (phid, it, k, kap), s in zip(args, singles):
+            np.testing.assert_array_equal(kap[:k].cpu().numpy(), s)
