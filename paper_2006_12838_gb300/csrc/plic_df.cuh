@@ -85,14 +85,20 @@ __device__ __forceinline__ df d2df(double x) {
     return quick_two_sum(hi, lo);
 }
 
-// K 2^-53 as a double-float (K < 2^63): the leading 24 bits of K (truncated)
-// and the rest rounded to a float, 2^-48 relative.
+// K 2^-53 as a double-float (0 <= K < 2^53): K is normalised so that its
+// leading bit is bit 52, then its top 24 bits (exact) and the next 29 bits
+// (rounded) become the two floats, 2^-48 relative.  32-bit conversions only
+// (the 64-bit integer conversions run on the FP64 pipe).
 __device__ __forceinline__ df df_from_u64_2m53(uint64_t K) {
     if (K == 0ull) return df_make(0.0f);
-    const float hf = __ull2float_rz(K);                         // exact integer value
-    const float lf = __ull2float_rn(K - __float2ull_rz(hf));
-    const float s = __uint_as_float((uint32_t)(127 - 53) << 23); // 2^-53
-    return quick_two_sum(hf * s, lf * s);
+    const int s = __clzll((long long)K) - 11;                  // K << s in [2^52, 2^53)
+    const uint64_t Kn = K << s;
+    const float hf = __uint2float_rn((uint32_t)(Kn >> 29));    // < 2^24: exact
+    const float lf = __uint2float_rn((uint32_t)(Kn & 0x1FFFFFFFull));
+    // hi * 2^(29 - 53 - s), lo * 2^(-53 - s): exponents in [-105, -24]
+    const float shi = __uint_as_float((uint32_t)(127 - 24 - s) << 23);
+    const float slo = __uint_as_float((uint32_t)(127 - 53 - s) << 23);
+    return quick_two_sum(hf * shi, lf * slo);
 }
 
 // A float as a double, by integer operations (exact for normal floats; zero
