@@ -326,3 +326,37 @@ def test_host_device_pointer_refuses_unmapped_memory(dev):
     host = [torch.zeros(64) for _ in range(5)]
     with pytest.raises(plic.PlicError):
         MappedHostOffset(dev).run(*host)
+
+
+def test_fp64r_extreme_fill_levels(dev, orc):
+    # FP64_REFINED works on double-floats built from the doubles' bits: V0
+    # next to 0 and 1 (1 - V0 formed exactly), below the float range (taken as
+    # 0: |d0 error| < 3e-13 by the stated bound), and normals with tiny
+    # components; everything else within the FP64 gate
+    rng = np.random.default_rng(41)
+    g = rng.normal(size=(3, 64))
+    n = g / np.linalg.norm(g, axis=0)
+    n[:, 0] = (1.0, 0.0, 0.0)
+    n[:, 1] = (np.sqrt(0.5), np.sqrt(0.5), 0.0)
+    n[:, 2] = (1e-200, np.sqrt(0.5), np.sqrt(0.5))
+    n[:, 3] = (1e-30, 0.6, 0.8)
+    levels = np.array([0.0, 1e-300, 1e-45, 2.0 ** -127, 2.0 ** -126, 1e-30, 1e-16, 1e-10, 0.25, 0.5,
+                       0.5 + 2.0 ** -53, 1 - 1e-10, 1 - 2.0 ** -52, 1 - 2.0 ** -53, 1.0])
+    nn = np.repeat(n, levels.size, axis=1)
+    V0 = np.tile(levels, n.shape[1])
+    ref = orc.offset(nn[0], nn[1], nn[2], V0)
+    t = _to(dev, torch.float64, nn[0], nn[1], nn[2], V0)
+    inv = torch.zeros(1, dtype=torch.int64, device=dev)
+    d0 = plic.offset(*t, method="sz_opt", precision="fp64r", invalid=inv).cpu().numpy()
+    assert inv.item() == 0 and not np.isnan(d0).any()
+    err = np.abs(d0 - ref)
+    tiny = np.minimum(V0, 1 - V0) < 2.0 ** -126
+    print("fp64r extreme levels: max|dd0| %.3e (V >= 2^-126), %.3e (V < 2^-126)" % (
+        err[~tiny].max(), err[tiny].max()))
+    assert err[~tiny].max() <= 1e-12
+    assert err[tiny].max() <= 3e-13
+    # the ends: V0 = 0 / 1 give -L/2 / +L/2 (L summed in double-float: 48 bits)
+    L = np.abs(nn).sum(0)
+    np.testing.assert_allclose(d0[V0 == 0.0], -0.5 * L[V0 == 0.0], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(d0[V0 == 1.0], 0.5 * L[V0 == 1.0], rtol=0, atol=1e-14)
+    assert (d0[V0 == 0.0] < 0).all() and (d0[V0 == 1.0] > 0).all()
