@@ -1,12 +1,16 @@
 // vof_compact.cu -- interface-cell compaction (Sec. 4.1, Eq. 33): the ordered
 // list of interior cells with 0 < phi < 1, and plic_workspace_bytes().
 //
-// Three launches, no atomics and no inter-block waiting, so the list is in
-// ascending cell order and identical run to run.  A tile is a run of whole
-// x-rows (about 8192 cells):
+// Two or three launches, no atomics and no inter-block waiting, so the list
+// is in ascending cell order and identical run to run.  A tile is a run of
+// whole x-rows (about 8192 cells):
 //   1. k_compact_count : each block counts the interface cells of its tile.
 //   2. k_compact_scan  : one block turns the per-tile counts into exclusive
-//                        offsets (in place) and writes the total to *d_count.
+//                        offsets (in place) and writes the total to *d_count;
+//                        only for fields of more than 4096 tiles (about 33 M
+//                        cells): below, each block of pass 3 sums the counts
+//                        of the tiles before its own, and the last writes the
+//                        total.
 //   3. k_compact_write : each block takes its tile's interface bits (stored by
 //                        pass 1 in the workspace, 1 bit per cell), scans the
 //                        row counts and writes the indices at its offset, in
@@ -25,6 +29,7 @@ constexpr int CT_WARPS = CT_THREADS / 32;
 constexpr int CT_TILE = 8192;            // cells per tile (whole x-rows)
 constexpr int CT_MAX_ROWS = 4096;        // rows per tile at most (CT_TILE / 3 for nx >= 3)
 constexpr int CT_MAX_WORDS = 2048;       // ballot words per tile kept in shared memory
+constexpr int64_t CT_FUSED_SCAN_TILES = 4096;   // tiles up to which pass 3 does its own prefix sum
 
 // Rows (x-lines) per tile: as many whole rows as fit in CT_TILE cells.
 __host__ __device__ inline int tile_rows(int nx) {
@@ -229,11 +234,23 @@ k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
                 const int* __restrict__ tile_offset, const unsigned* __restrict__ bits,
-                const int* __restrict__ row_count, int32_t* __restrict__ idx, int64_t cap, int vec) {
+                const int* __restrict__ row_count, int32_t* __restrict__ idx, int64_t cap, int vec,
+                int64_t* __restrict__ d_count) {
     __shared__ unsigned bal[CT_MAX_WORDS];
     __shared__ int rowoff[CT_MAX_ROWS + 1];
     __shared__ int rowcnt[CT_MAX_ROWS];
+    __shared__ long long s_base[CT_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // with d_count given, tile_offset holds the per-tile counts of pass 1 and
+    // the block sums those of the tiles before its own (few tiles: no scan
+    // launch); the last block writes the total
+    if (d_count) {
+        long long part = 0;
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += CT_THREADS) part += __ldg(tile_offset + i);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) s_base[warp] = part;
+    }
     const int64_t rbeg = (int64_t)blockIdx.x * R;
     const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
     const int nr = (int)(rend - rbeg);
@@ -288,7 +305,16 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
         }
     }
     __syncthreads();
-    const int64_t base = tile_offset[blockIdx.x];
+    int64_t base;
+    if (d_count) {
+        long long b = 0;
+#pragma unroll
+        for (int w = 0; w < CT_WARPS; ++w) b += s_base[w];
+        base = b;
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *d_count = b + tile_offset[blockIdx.x];
+    } else {
+        base = tile_offset[blockIdx.x];
+    }
     for (int k = warp; k < nr; k += CT_WARPS) {
         if (rowcnt[k] == 0) continue;               // most rows of a field hold no interface cell
         const int64_t r = rbeg + k;
@@ -401,9 +427,14 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
     k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, rowc,
                                                         vec);
-    k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
+    // up to CT_FUSED_SCAN_TILES tiles each block of pass 3 sums the counts of
+    // the tiles before it (at most that many L2 reads per block); beyond, one
+    // block scans them first
+    const bool fused = nt <= CT_FUSED_SCAN_TILES;
+    if (!fused) k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
     k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, rowc,
-                                                        idx, idx_capacity, vec);
+                                                        idx, idx_capacity, vec,
+                                                        fused ? d_count : nullptr);
     return check_launch("vof_interface_compact");
 }
 
@@ -483,8 +514,10 @@ extern "C" plic_status vof_interface_compact_noalloc(const float* phi, int nx, i
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
     k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
                                                         nullptr, vec);
-    k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
+    const bool fused = nt <= CT_FUSED_SCAN_TILES;
+    if (!fused) k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
     k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
-                                                        nullptr, idx, idx_capacity, vec);
+                                                        nullptr, idx, idx_capacity, vec,
+                                                        fused ? d_count : nullptr);
     return check_launch("vof_interface_compact_noalloc");
 }

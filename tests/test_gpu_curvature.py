@@ -42,7 +42,8 @@ def _compact(dev, p):
 
 
 @pytest.mark.parametrize("shape", [(96, 96, 96), (29, 41, 37), (3, 3, 3), (5, 70, 13), (7, 9, 100),
-                                   (5, 6, 260), (6, 5, 4), (4, 33, 8), (3, 17, 516)])
+                                   (5, 6, 260), (6, 5, 4), (4, 33, 8), (3, 17, 516),
+                                   (520, 256, 256)])   # > 4096 tiles: the separate scan launch
 def test_compaction_bit_exact(dev, orc, shape):
     rng = np.random.default_rng(sum(shape))
     p = rng.random(shape).astype(np.float32)
