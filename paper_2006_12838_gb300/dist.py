@@ -1,7 +1,8 @@
 """Multi-process helpers for running the hot path on several GPUs of a node.
 
 The PLIC batches and the VOF fields are independent units: a multi-GPU run
-gives each rank its own units (weak scaling) and needs no data-path
+gives each rank its own units (weak scaling: contiguous cell ranges, or whole
+fields balanced by their interface-cell counts) and needs no data-path
 collective.  The only collectives are around the timing: a barrier before and
 after the timed region and the maximum of the per-rank times.  Launch with
 torchrun (one process per GPU); the env variables RANK / WORLD_SIZE /
@@ -36,6 +37,22 @@ def shard(n_units: int, rank: int, world: int):
     base, rem = divmod(n_units, world)
     start = rank * base + min(rank, rem)
     return start, start + base + (1 if rank < rem else 0)
+
+
+def assign_fields(work, world: int):
+    """Rank of each field for a multi-GPU batched curvature run: whole fields,
+    largest first, each to the rank with the least work so far (the longest-
+    processing-time rule; ties to the lower rank), so every rank computes the
+    same assignment from the same per-field work (interface-cell counts) and
+    no field is split.  Returns a list of ranks, one per field."""
+    order = sorted(range(len(work)), key=lambda i: (-int(work[i]), i))
+    load = [0] * world
+    owner = [0] * len(work)
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += int(work[i])
+    return owner
 
 
 def barrier():
