@@ -68,10 +68,27 @@ __device__ __forceinline__ p2::f2 offset_two<M_SZ_OPT>(const CellPlic<M_SZ_OPT>&
     return make_float2(copysignf(h.x, V0.x - 0.5f), copysignf(h.y, V0.y - 0.5f));
 }
 
+// The D3Q27 directions as a block-shared table (integer and float
+// components), filled by the first 27 threads of the block: the neighbour loop
+// looks its directions up (one shared load each) instead of decoding them.
+struct E27Shared {
+    int4 ei[27];
+    float4 ef[27];
+    __device__ __forceinline__ void fill() {
+        if (threadIdx.x < 27) {
+            int ex, ey, ez;
+            e_of_lanes((int)threadIdx.x, ex, ey, ez);
+            ei[threadIdx.x] = make_int4(ex, ey, ez, 0);
+            ef[threadIdx.x] = make_float4((float)ex, (float)ey, (float)ez, 0.0f);
+        }
+        __syncthreads();
+    }
+};
+
 // kappa (sign per flags) of interface cell c of a field, one thread.
 template <int METHOD, int FIT>
 __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx, int64_t nxy,
-                                           int64_t c, uint32_t flags) {
+                                           int64_t c, uint32_t flags, const E27Shared& tab) {
     const bool cm = (flags & PLIC_FLAG_NORMAL_CM) != 0;
     const float* p0 = phi + c;
     // offsets within the field in 32 bits (list entries are int32 cell indices)
@@ -134,14 +151,13 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
         const bool two = list != 0u;
         const int i2 = two ? __ffs(list) - 1 : i1;
         list &= list - 1u;                          // no-op on an empty list
-        int ex1, ey1, ez1, ex2, ey2, ez2;
-        e_of_lanes(i1, ex1, ey1, ez1);
-        e_of_lanes(i2, ex2, ey2, ez2);
-        const float v1 = __ldg(p0 + (ex1 + ey1 * nx + ez1 * nxy32));
-        const float v2 = __ldg(p0 + (ex2 + ey2 * nx + ez2 * nxy32));
+        const int4 e1 = tab.ei[i1], e2 = tab.ei[i2];
+        const float4 f1 = tab.ef[i1], f2 = tab.ef[i2];
+        const float v1 = __ldg(p0 + (e1.x + e1.y * nx + e1.z * nxy32));
+        const float v2 = __ldg(p0 + (e2.x + e2.y * nx + e2.z * nxy32));
         const p2::f2 d0i = offset_two<METHOD>(pl, make_float2(v1, v2));
-        float qx[2] = {(float)ex1, (float)ex2}, qy[2] = {(float)ey1, (float)ey2};
-        float qz[2] = {(float)ez1, (float)ez2}, z[2];
+        float qx[2] = {f1.x, f2.x}, qy[2] = {f1.y, f2.y};
+        float qz[2] = {f1.z, f2.z}, z[2];
         const float dd[2] = {d0i.x, d0i.y};
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -184,10 +200,12 @@ k_vof_curvature_tpc(const float* __restrict__ phi, int nx, int ny, const int32_t
         const int64_t dn = *d_n;
         lim = dn < n ? dn : n;
     }
+    __shared__ E27Shared tab;
+    tab.fill();
     const int64_t nxy = (int64_t)nx * ny;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lim;
          k += (int64_t)gridDim.x * blockDim.x)
-        kappa[k] = scale * tpc_kappa<METHOD, FIT>(phi, nx, nxy, (int64_t)__ldg(idx + k), flags);
+        kappa[k] = scale * tpc_kappa<METHOD, FIT>(phi, nx, nxy, (int64_t)__ldg(idx + k), flags, tab);
 }
 
 // Persistent batched kernel: each warp claims tickets of `chunk` cells (a
@@ -198,6 +216,8 @@ k_vof_curvature_batched_tpc(const vof_field* __restrict__ fields, const int64_t*
                             int n_fields, int64_t total, int chunk,
                             unsigned long long* __restrict__ ticket, uint32_t flags) {
     const int lane = threadIdx.x & 31;
+    __shared__ E27Shared tab;
+    tab.fill();
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(ticket, (unsigned long long)chunk);
@@ -213,7 +233,7 @@ k_vof_curvature_batched_tpc(const vof_field* __restrict__ fields, const int64_t*
             const int64_t kk = gi - __ldg(prefix + lo);
             const vof_field& F = fields[lo];
             const float k = tpc_kappa<METHOD, FIT>(F.phi, F.nx, (int64_t)F.nx * F.ny,
-                                                   (int64_t)__ldg(F.idx + kk), flags);
+                                                   (int64_t)__ldg(F.idx + kk), flags, tab);
             F.kappa[kk] = k;
         }
     }
