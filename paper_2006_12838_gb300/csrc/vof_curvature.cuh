@@ -75,6 +75,24 @@ __device__ __forceinline__ void e_of_lanes(int i, int& ex, int& ey, int& ez) {
     ez = e27_comp<2>(i);
 }
 
+// The D3Q27 directions as a block-shared table (integer and float
+// components), filled by the first 27 threads of the block (every thread of
+// the block must call fill()): loops over per-lane entries look their
+// directions up (one shared load each) instead of decoding them.
+struct E27Shared {
+    int4 ei[27];
+    float4 ef[27];
+    __device__ __forceinline__ void fill() {
+        if (threadIdx.x < 27) {
+            int ex, ey, ez;
+            e_of_lanes((int)threadIdx.x, ex, ey, ez);
+            ei[threadIdx.x] = make_int4(ex, ey, ez, 0);
+            ef[threadIdx.x] = make_float4((float)ex, (float)ey, (float)ez, 0.0f);
+        }
+        __syncthreads();
+    }
+};
+
 // The same table for a compile-time index (fully unrolled loops): folds to
 // constants.
 template <int I>

@@ -68,23 +68,6 @@ __device__ __forceinline__ p2::f2 offset_two<M_SZ_OPT>(const CellPlic<M_SZ_OPT>&
     return make_float2(copysignf(h.x, V0.x - 0.5f), copysignf(h.y, V0.y - 0.5f));
 }
 
-// The D3Q27 directions as a block-shared table (integer and float
-// components), filled by the first 27 threads of the block: the neighbour loop
-// looks its directions up (one shared load each) instead of decoding them.
-struct E27Shared {
-    int4 ei[27];
-    float4 ef[27];
-    __device__ __forceinline__ void fill() {
-        if (threadIdx.x < 27) {
-            int ex, ey, ez;
-            e_of_lanes((int)threadIdx.x, ex, ey, ez);
-            ei[threadIdx.x] = make_int4(ex, ey, ez, 0);
-            ef[threadIdx.x] = make_float4((float)ex, (float)ey, (float)ez, 0.0f);
-        }
-        __syncthreads();
-    }
-};
-
 // kappa (sign per flags) of interface cell c of a field, one thread.
 template <int METHOD, int FIT>
 __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx, int64_t nxy,
