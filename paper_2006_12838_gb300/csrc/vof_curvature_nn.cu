@@ -66,14 +66,27 @@ k_vof_curvature_nn(const float* __restrict__ phi, int nx, int ny, int nz,
         for (int q = 0; q < 15; ++q) M[q] = 0.0f;
 #pragma unroll
         for (int q = 0; q < 5; ++q) bv[q] = 0.0f;
-        int m = 0;
-#pragma unroll 1
-        for (int i = 1; i < 27; ++i) {
+        // the interface neighbours first (compile-time offsets), then a loop
+        // over them only, so a warp runs as many trips as its busiest lane
+        // has interface neighbours instead of 26
+        unsigned mask = 0u;
+        for_e27<1>([&](auto I) {
+            constexpr int i = decltype(I)::value;
             int ex, ey, ez;
-            e_of(i, ex, ey, ez);
+            e_of_c<i>(ex, ey, ez);
+            const float v = __ldg(phi + c + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
+            if (v > 0.0f && v < 1.0f) mask |= 1u << i;
+        });
+        int m = 0;
+        unsigned list = mask;
+#pragma unroll 1
+        while (list) {
+            const int i = __ffs(list) - 1;
+            list &= list - 1u;
+            int ex, ey, ez;
+            e_of_lanes(i, ex, ey, ez);
             const int64_t ci = c + ex + (int64_t)ey * nx + (int64_t)ez * nxy;
             const float v = __ldg(phi + ci);
-            if (!(v > 0.0f && v < 1.0f)) continue;
             float mx = nx_, my = ny_, mz = nz_;
             const int xi = x + ex, yi = y + ey, zi = z + ez;
             if (xi >= 1 && yi >= 1 && zi >= 1 && xi <= nx - 2 && yi <= ny - 2 && zi <= nz - 2) {
