@@ -13,8 +13,10 @@
 // leaves the field, or whose normal is undefined, keeps the centre normal.
 // Every neighbour solve now needs its own normal-dependent constants, so the
 // per-cell hoisting of the default kernel does not apply; one thread per
-// list entry, grid-stride.
+// list entry, grid-stride, the interface neighbours two at a time (the
+// optimised SZ and analytic solutions solve both on the paired FP32 path).
 #include "host_common.h"
+#include "plic_pair.cuh"
 #include "vof_curvature.cuh"
 
 namespace plic {
@@ -77,46 +79,74 @@ k_vof_curvature_nn(const float* __restrict__ phi, int nx, int ny, int nz,
             const float v = __ldg(phi + c + ex + (int64_t)ey * nx + (int64_t)ez * nxy);
             if (v > 0.0f && v < 1.0f) mask |= 1u << i;
         });
-        int m = 0;
+        const int m = __popc(mask);
         unsigned list = mask;
 #pragma unroll 1
         while (list) {
-            const int i = __ffs(list) - 1;
+            // two neighbours per trip (an odd last one pairs with itself at
+            // weight 0); each with its own normal, so no per-normal constants
+            // are shared: the optimised SZ and analytic solutions solve the
+            // two on the paired FP32 path, the other methods one by one
+            int ii[2];
+            ii[0] = __ffs(list) - 1;
             list &= list - 1u;
-            int ex, ey, ez;
-            e_of_lanes(i, ex, ey, ez);
-            const int64_t ci = c + ex + (int64_t)ey * nx + (int64_t)ez * nxy;
-            const float v = __ldg(phi + ci);
-            float mx = nx_, my = ny_, mz = nz_;
-            const int xi = x + ex, yi = y + ey, zi = z + ez;
-            if (xi >= 1 && yi >= 1 && zi >= 1 && xi <= nx - 2 && yi <= ny - 2 && zi <= nz - 2) {
-                float ax, ay, az;
-                if (stencil_normal(phi, ci, nx, nxy, cm, ax, ay, az)) { mx = ax; my = ay; mz = az; }
+            const bool two = list != 0u;
+            ii[1] = two ? __ffs(list) - 1 : ii[0];
+            list &= list - 1u;                      // no-op on an empty list
+            int ex[2], ey[2], ez[2];
+            float v[2], mx[2], my[2], mz[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                e_of_lanes(ii[j], ex[j], ey[j], ez[j]);
+                const int64_t ci = c + ex[j] + (int64_t)ey[j] * nx + (int64_t)ez[j] * nxy;
+                v[j] = __ldg(phi + ci);
+                mx[j] = nx_; my[j] = ny_; mz[j] = nz_;
+                const int xi = x + ex[j], yi = y + ey[j], zi = z + ez[j];
+                if (xi >= 1 && yi >= 1 && zi >= 1 && xi <= nx - 2 && yi <= ny - 2 && zi <= nz - 2) {
+                    float ax, ay, az;
+                    if (stencil_normal(phi, ci, nx, nxy, cm, ax, ay, az)) { mx[j] = ax; my[j] = ay; mz[j] = az; }
+                }
             }
-            CellPlic<METHOD> pi;
-            pi.prepare(mx, my, mz);
-            const float d0i = pi.offset(v);
-            float qx = (float)ex, qy = (float)ey, qz = (float)ez;
-            if (centroid) {
-                float A, cx, cy, cz;
-                area_centroid<float>(mx, my, mz, d0i, A, cx, cy, cz);
-                qx += cx - c0x; qy += cy - c0y; qz += cz - c0z;
+            float d0i[2];
+            if (METHOD == M_SZ_OPT || METHOD == M_ANALYTIC) {
+                int bad = 0;
+                const p2::f2 r = p2::offset_pair<METHOD, true, false>(
+                    make_float2(mx[0], mx[1]), make_float2(my[0], my[1]), make_float2(mz[0], mz[1]),
+                    make_float2(v[0], v[1]), bad);
+                d0i[0] = r.x;
+                d0i[1] = r.y;
             } else {
-                qx += d0i * mx - d00 * nx_;
-                qy += d0i * my - d00 * ny_;
-                qz += d0i * mz - d00 * nz_;
-            }
-            const float px = qx * bxx + qy * bxy + qz * bxz;
-            const float py = qx * byx + qy * byy + qz * byz;
-            const float pz = qx * nx_ + qy * ny_ + qz * nz_;
-            const float Q[5] = {px * px, py * py, px * py, px, py};
 #pragma unroll
-            for (int a = 0; a < 5; ++a) {
-#pragma unroll
-                for (int b = a; b < 5; ++b) M[uidx(a, b)] = fmaf(Q[a], Q[b], M[uidx(a, b)]);
-                bv[a] = fmaf(pz, Q[a], bv[a]);
+                for (int j = 0; j < 2; ++j) {
+                    CellPlic<METHOD> pi;
+                    pi.prepare(mx[j], my[j], mz[j]);
+                    d0i[j] = pi.offset(v[j]);
+                }
             }
-            ++m;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                float qx = (float)ex[j], qy = (float)ey[j], qz = (float)ez[j];
+                if (centroid) {
+                    float A, cx, cy, cz;
+                    area_centroid<float>(mx[j], my[j], mz[j], d0i[j], A, cx, cy, cz);
+                    qx += cx - c0x; qy += cy - c0y; qz += cz - c0z;
+                } else {
+                    qx += d0i[j] * mx[j] - d00 * nx_;
+                    qy += d0i[j] * my[j] - d00 * ny_;
+                    qz += d0i[j] * mz[j] - d00 * nz_;
+                }
+                const float w = (j == 0 || two) ? 1.0f : 0.0f;
+                const float px = w * (qx * bxx + qy * bxy + qz * bxz);
+                const float py = w * (qx * byx + qy * byy + qz * byz);
+                const float pz = w * (qx * nx_ + qy * ny_ + qz * nz_);
+                const float Q[5] = {px * px, py * py, px * py, px, py};
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+#pragma unroll
+                    for (int b = a; b < 5; ++b) M[uidx(a, b)] = fmaf(Q[a], Q[b], M[uidx(a, b)]);
+                    bv[a] = fmaf(pz, Q[a], bv[a]);
+                }
+            }
         }
         float xs[5];
         int dim;
