@@ -72,6 +72,13 @@ int blocks_per_sm(const void* kernel, int threads, size_t smem) {
     return b;
 }
 
+int stream_grid(const void* kernel, int threads, int64_t work) {
+    const int64_t need = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)stride_grid(kernel, threads, work) * STREAM_WAVES;
+    const int64_t g = need < cap ? need : cap;
+    return g < 1 ? 1 : (int)(g < 2147483647LL ? g : 2147483647LL);
+}
+
 int stride_grid(const void* kernel, int threads, int64_t work, size_t smem) {
     int64_t need = (work + threads - 1) / threads;
     int64_t cap = (int64_t)sm_count() * blocks_per_sm(kernel, threads, smem);

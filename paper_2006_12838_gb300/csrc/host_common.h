@@ -30,6 +30,12 @@ int blocks_per_sm(const void* kernel, int threads, size_t smem);
 // A grid for a grid-stride loop over `work` items of `threads` threads each:
 // min(ceil(work/threads), SMs x resident blocks per SM), at least 1.
 int stride_grid(const void* kernel, int threads, int64_t work, size_t smem = 0);
+// The streaming kernels' grid: up to STREAM_WAVES waves of resident blocks
+// (each thread still loops when the work is larger).  Measured on the fused
+// PLIC step: one persistent wave 1.502 ms, 2 waves 1.446, 4 1.409, 8 1.391,
+// 32 1.386, one block per 256 vectors (no loop) 1.447.
+constexpr int STREAM_WAVES = 16;
+int stream_grid(const void* kernel, int threads, int64_t work);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

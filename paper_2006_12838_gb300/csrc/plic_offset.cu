@@ -4,8 +4,9 @@
 // Layout: structure of arrays nx, ny, nz, V0 -> d0.  One thread handles one
 // 16-byte vector of each array per step of a grid-stride loop (4 cells in FP32,
 // 2 in FP64), so every warp issues fully coalesced 512-byte loads; the grid is
-// (#SMs x resident blocks), i.e. one persistent wave.  Loads and the store are
-// streaming (evict-first): every byte is touched once.
+// up to 16 waves of resident blocks (stream_grid: measured faster than one
+// persistent wave).  Loads and the store are streaming (evict-first): every
+// byte is touched once.
 //
 // Roofline: 20 B/cell in FP32 (16 in, 4 out), 40 B/cell in FP64.  The FP32
 // solvers sit near the HBM/ALU balance point; FP64 is bound by the FP64 pipe.
@@ -194,7 +195,7 @@ static plic_status offset_entry(const void* nx, const void* ny, const void* nz, 
     const int threads = 256;
     const int W = dbl ? 2 : 4;
     const int64_t work = vec_ok ? (n + W - 1) / W : n;
-    const int grid = stride_grid(k, threads, work);
+    const int grid = stream_grid(k, threads, work);
     unsigned long long* inv = reinterpret_cast<unsigned long long*>(d_invalid_count);
     void* args[] = {(void*)&nx, (void*)&ny, (void*)&nz, (void*)&V0, (void*)&d0,
                     (void*)&n, (void*)&vec_ok, (void*)&inv, (void*)&vrt};

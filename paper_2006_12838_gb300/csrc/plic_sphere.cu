@@ -110,7 +110,7 @@ static plic_status launch(const void* in, void* out, int64_t n, void* stream, co
     const int vec_ok = aligned(in, 16) && aligned(out, 16);
     const void* k = reinterpret_cast<const void*>(&k_plic_sphere<T, INVERSE>);
     const int W = V16<T>::W;
-    const int grid = stride_grid(k, 256, vec_ok ? (n + W - 1) / W : n);
+    const int grid = stream_grid(k, 256, vec_ok ? (n + W - 1) / W : n);
     k_plic_sphere<T, INVERSE><<<grid, 256, 0, as_stream(stream)>>>((const T*)in, (T*)out, n, vec_ok);
     return check_launch(who);
 }

@@ -105,7 +105,7 @@ static plic_status launch_volume(const void* nx, const void* ny, const void* nz,
     const int vec_ok = all_aligned(16, {nx, ny, nz, d0, V0});
     const void* k = reinterpret_cast<const void*>(&k_plic_volume<T>);
     const int W = V16<T>::W;
-    const int grid = stride_grid(k, 256, vec_ok ? (n + W - 1) / W : n);
+    const int grid = stream_grid(k, 256, vec_ok ? (n + W - 1) / W : n);
     k_plic_volume<T><<<grid, 256, 0, as_stream(stream)>>>(
         (const T*)nx, (const T*)ny, (const T*)nz, (const T*)d0, (T*)V0, n, vec_ok);
     return check_launch("plic_volume");
@@ -118,7 +118,7 @@ static plic_status launch_adjoint(const void* nx, const void* ny, const void* nz
     const int vec_ok = all_aligned(16, {nx, ny, nz, d0, g, gs, gx, gy, gz});
     const void* k = reinterpret_cast<const void*>(&k_plic_adjoint<T, MODE>);
     const int W = V16<T>::W;
-    const int grid = stride_grid(k, 256, vec_ok ? (n + W - 1) / W : n);
+    const int grid = stream_grid(k, 256, vec_ok ? (n + W - 1) / W : n);
     k_plic_adjoint<T, MODE><<<grid, 256, 0, as_stream(stream)>>>(
         (const T*)nx, (const T*)ny, (const T*)nz, (const T*)d0, (const T*)g, (T*)gs, (T*)gx,
         (T*)gy, (T*)gz, n, vec_ok);
