@@ -17,7 +17,8 @@
 // spends a handful of FMAs and one MUFU reciprocal per step instead.
 //
 // Data: one array in, one out (SoA streams of float or double), 16-byte
-// vectors in a one-wave grid-stride loop; 8 (FP32) or 16 (FP64) bytes per cell.
+// vectors in a grid-stride loop on up to 16 waves of blocks (stream_grid);
+// 8 (FP32) or 16 (FP64) bytes per cell.
 #include "host_common.h"
 #include "plic_math.cuh"
 

@@ -5,7 +5,8 @@
 // c the centroid of the cut polygon of the plane n . x = d0,
 //   dV0/dd0 = A,   dV0/dn = -A c,   dd0/dV0 = 1/A,   dd0/dn = c.
 // All three kernels stream structure-of-arrays data through 16-byte vectors in
-// a one-wave grid-stride loop, as plic_offset does.
+// a grid-stride loop on up to 16 waves of blocks (stream_grid), as plic_offset
+// does.
 #include "host_common.h"
 #include "plic_polygon.cuh"
 
