@@ -90,7 +90,7 @@ extern "C" plic_status plic_paper_benchmark(const void* nx, const void* ny, cons
         case PLIC_NEWTON: k = pick_bench<M_NEWTON>(p); break;
         case PLIC_NESTED: k = pick_bench<M_NESTED>(p); break;
     }
-    const int grid = stride_grid(k, 256, n_normals);
+    const int grid = stream_grid(k, 256, n_normals);
     void* args[] = {(void*)&nx, (void*)&ny, (void*)&nz, (void*)&n_normals, (void*)&L,
                     (void*)&blank, (void*)&d_err_sum};
     cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(256), args, 0, as_stream(stream));
