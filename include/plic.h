@@ -158,6 +158,9 @@ plic_status plic_offset_backward(const void *nx, const void *ny, const void *nz,
 
 /* plic_volume_backward -- vector-Jacobian product of plic_volume (unit n):
  *   g_d0 = g_V0 * A,    g_n = -g_V0 * A * c.
+ * The volume of Eq. 10 (Sec. 2.2) grows with d0 at the rate of the cut
+ * polygon's area A; a change dn of the normal moves the plane at each point x
+ * of the polygon by -dn . x, so dV0 = -A dn . c (c the centroid).
  * Arrays: nx, ny, nz, d0, g_V0 (in); g_d0, g_nx, g_ny, g_nz (out, nullable). */
 plic_status plic_volume_backward(const void *nx, const void *ny, const void *nz,
                                  const void *d0, const void *g_V0, void *g_d0, void *g_nx,
@@ -178,7 +181,7 @@ plic_status vof_interface_compact(const float *phi, int nx, int ny, int nz, int3
                                   size_t ws_bytes, void *stream);
 
 /* vof_interface_compact_noalloc -- the same interface-cell list as
- * vof_interface_compact (identical output), for callers that cannot allocate
+ * vof_interface_compact (Sec. 4.1, Eq. 33; identical output), for callers that cannot allocate
  * device memory: a solver that owns every byte of the GPU through its own
  * pool, code that runs where cudaMalloc is not allowed or too slow to call (a
  * real-time step loop, a callback that must not synchronise the device), or a
@@ -239,7 +242,8 @@ plic_status vof_laplace_pressure(const float *phi, int nx, int ny, int nz, const
                                  int64_t n_iface, const int64_t *d_n_iface, float sigma,
                                  float *dp, plic_method m, uint32_t flags, void *stream);
 
-/* vof_curvature_backward -- vector-Jacobian product of vof_curvature with
+/* vof_curvature_backward -- vector-Jacobian product of vof_curvature (the
+ * curvature step of Sec. 4.2 and Appendix B: Eqs. 36, 38 and 42) with
  * respect to the fill field: g_phi = d(sum_k g_kappa[k] kappa[k]) / d phi,
  * with the interface set (idx and the neighbour flags 0 < phi < 1) held fixed.
  * g_phi is dense (nx*ny*nz floats) and overwritten.  Per interface cell the 27
@@ -271,8 +275,9 @@ typedef struct {
                                 1: one thread per cell; 0: the library's default */
 } vof_tuning;
 
-/* vof_curvature_batched -- vof_curvature over many fields of uneven size in
- * ONE persistent launch: the interface lists are concatenated logically, and
+/* vof_curvature_batched -- vof_curvature (Sec. 4.2, Appendix B) over many
+ * fields of uneven size in ONE persistent launch: the interface lists are
+ * concatenated logically, and
  * a grid of (#SMs x blocks_per_sm) blocks claims chunks of cells from a
  * device-side ticket counter until the work is exhausted (no waiting on other
  * blocks).  `fields` is a HOST array of n_fields descriptors; it is copied to
@@ -316,6 +321,9 @@ plic_status plic_sphere_volume(const void *d0, void *V0, int64_t n, plic_precisi
                                void *stream);
 plic_status plic_sphere_offset(const void *V0, void *d0, int64_t n, plic_precision p,
                                void *stream);
+
+/* The functions below are library plumbing (workspace sizes, status text,
+ * version, host-memory addressing); the paper has no counterpart. */
 
 /* Workspace kinds for plic_workspace_bytes(). */
 enum {

@@ -41,6 +41,25 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+# entry points with no counterpart in the paper (sizes, status text, version,
+# host-memory addressing)
+PLUMBING = {"plic_workspace_bytes", "plic_curv_bwd_workspace_bytes", "plic_status_string",
+            "plic_last_error", "plic_abi_version", "plic_host_device_pointer"}
+
+
+def test_every_compute_entry_cites_its_passage():
+    txt = open(HEADER).read()
+    blocks = re.findall(r"/\*(.*?)\*/", txt, flags=re.S)
+    cite = re.compile(r"\b(Sec\.\s*\d|Eqs?\.\s*\d|Appendix\s+[A-Z])")
+    for name in declared_functions():
+        if name in PLUMBING:
+            continue
+        heads = [b for b in blocks if re.match(r"\s*(\w+\s*/\s*)?%s\b" % name, b)]
+        assert heads, "%s has no doc block naming it" % name
+        assert any(cite.search(b) for b in heads), "%s cites no passage" % name
+    assert PLUMBING <= set(declared_functions())
+
+
 def test_status_strings_and_version(lib):
     assert lib.plic_abi_version() == 1
     for s in range(6):
