@@ -166,6 +166,8 @@ static const int CUBE_EDGES[12][2] = {
     {0, 4}, {1, 5}, {2, 6}, {3, 7}        /* along z */
 };
 
+/* Vertex v of the cell [-1/2,1/2]^3 of Sec. 2.1; bit k of v picks the sign of
+ * coordinate k. */
 static void cube_vertex(int v, double p[3])
 {
     p[0] = (v & 1) ? 0.5 : -0.5;
@@ -173,6 +175,8 @@ static void cube_vertex(int v, double p[3])
     p[2] = (v & 4) ? 0.5 : -0.5;
 }
 
+/* Area and centroid of the cut polygon of the plane n.x = d0 (Eq. 1), as the
+ * block comment above describes. */
 ORC_EXPORT int oracle_area_centroid(double nx, double ny, double nz, double d0,
                                     double *area, double centroid[3])
 {
@@ -242,7 +246,9 @@ ORC_EXPORT int oracle_area_centroid(double nx, double ny, double nz, double d0,
 }
 
 /* ---------------------------------------------------------------------------
- * Batched wrappers (OpenMP over cells).
+ * Batched wrappers (OpenMP over cells): Eq. 10 (oracle_volume), Eq. 1
+ * (oracle_offset) and the cut polygon of Eq. 1 (oracle_area_centroid), cell by
+ * cell.
  * ------------------------------------------------------------------------- */
 ORC_EXPORT void oracle_volume_batch(const double *nx, const double *ny, const double *nz,
                                     const double *d0, double *V0, int64_t n)
@@ -273,6 +279,7 @@ ORC_EXPORT void oracle_area_centroid_batch(const double *nx, const double *ny, c
     }
 }
 
+/* OpenMP threads the batched functions use (plumbing; no passage). */
 ORC_EXPORT int oracle_num_threads(void)
 {
 #ifdef _OPENMP
@@ -308,6 +315,7 @@ static const int E27[27][3] = {
     {-1, 1, 1}, { 1,-1,-1}
 };
 
+/* The D3Q27 directions above (Appendix B), as 27 x 3 ints. */
 ORC_EXPORT void oracle_d3q27(int *e81)
 {
     int i, k;
@@ -347,7 +355,8 @@ ORC_EXPORT int oracle_cm_normal(const double *phi27, double n[3])
 }
 
 /* Gaussian elimination with partial pivoting on a k x k system (row-major
- * a[5][5], right-hand side b[5]); solution in x.  Returns the determinant. */
+ * a[5][5], right-hand side b[5]); solution in x.  Returns the determinant.
+ * The solve of the paraboloid fit's normal equations (Appendix B, Eqs. 43-48). */
 static double gauss_solve(int k, const double ain[5][5], const double *bin, double *x)
 {
     double a[5][6], det = 1.0;
@@ -508,7 +517,8 @@ ORC_EXPORT double oracle_curvature_cell(const double *phi27, const int *iface27,
                                           : -oracle_paraboloid_kappa(x5);
 }
 
-/* Gather the 27 stencil values of cell (x,y,z) of a field stored x-fastest. */
+/* Gather the 27 stencil values phi(x + e_i) of cell (x,y,z) of a field stored
+ * x-fastest, in the D3Q27 order of Appendix B. */
 static void gather27(const float *phi, int nx, int ny, int64_t c, double *out)
 {
     int i;
@@ -518,9 +528,10 @@ static void gather27(const float *phi, int nx, int ny, int64_t c, double *out)
     }
 }
 
-/* Neighbour normals for ORC_NEIGHBOR_NORMAL: for each interface neighbour i
- * of cell c whose own 26 neighbours lie inside the field, its PY (or CM)
- * normal; zero (centre normal) otherwise. */
+/* Neighbour normals for ORC_NEIGHBOR_NORMAL (the variant of Sec. 4.2 in which
+ * each neighbour's PLIC point uses its own normal): for each interface
+ * neighbour i of cell c whose own 26 neighbours lie inside the field, its PY
+ * (Eq. 38) or CM (Appendix B) normal; zero (centre normal) otherwise. */
 static void neighbour_normals(const float *phi, int nx, int ny, int nz, int64_t c,
                               const double *s27, unsigned flags, double *nn81)
 {
@@ -540,7 +551,8 @@ static void neighbour_normals(const float *phi, int nx, int ny, int nz, int64_t 
     }
 }
 
-/* Curvature for a list of interface cells (linear indices x + nx*(y + ny*z)). */
+/* Curvature (Sec. 4.2, Appendix B: oracle_curvature_cell) for a list of
+ * interface cells (linear indices x + nx*(y + ny*z)). */
 ORC_EXPORT void oracle_curvature_batch(const float *phi, int nx, int ny, int nz,
                                        const int32_t *idx, int64_t n_iface, unsigned flags,
                                        double *kappa, int32_t *dim, int32_t *npts)
@@ -559,8 +571,8 @@ ORC_EXPORT void oracle_curvature_batch(const float *phi, int nx, int ny, int nz,
     }
 }
 
-/* Normals (PY, or CM with ORC_NORMAL_CM) of a list of interface cells; zero
- * where undefined. */
+/* Normals (PY of Eq. 38, or the CM normal of Appendix B with ORC_NORMAL_CM)
+ * of a list of interface cells; zero where undefined. */
 ORC_EXPORT void oracle_normal_batch(const float *phi, int nx, int ny, int nz,
                                     const int32_t *idx, int64_t n_iface, unsigned flags,
                                     double *nx_out, double *ny_out, double *nz_out)
@@ -579,7 +591,8 @@ ORC_EXPORT void oracle_normal_batch(const float *phi, int nx, int ny, int nz,
     }
 }
 
-/* Central finite differences of J = sum_k w_k kappa_k with respect to every
+/* The adjoint of the curvature step (Sec. 4.2, Appendix B) by brute force:
+ * central finite differences of J = sum_k w_k kappa_k with respect to every
  * fill value in the field (FP64 perturbations of the FP32 field values).  The
  * interface set is the given list and is held fixed.  For each interface cell
  * k and each of its 27 stencil entries j, kappa_k is re-evaluated at
@@ -630,6 +643,7 @@ ORC_EXPORT void oracle_curvature_grad_fd(const float *phi, int nx, int ny, int n
  * ------------------------------------------------------------------------- */
 static double sphere_radius(void) { return cbrt(3.0 / (4.0 * 3.14159265358979323846)); }
 
+/* The cap volume of Sec. 3 described above. */
 ORC_EXPORT double oracle_sphere_volume(double d0)
 {
     double r = sphere_radius(), h;
@@ -640,10 +654,10 @@ ORC_EXPORT double oracle_sphere_volume(double d0)
     return 3.14159265358979323846 / 3.0 * h * h * (3.0 * r - h);
 }
 
-/* The inverse: d0 in [-r, r] with V0(d0) = V0, by bisection down to adjacent
- * doubles (V0 increases strictly on [-r, r]).  By the symmetry
- * V0(-d0) = 1 - V0(d0) the search runs for W = min(V0, 1 - V0) on [-r, 0]
- * and the sign is restored, so the residual stays relative to W. */
+/* The inverse problem of Sec. 3: d0 in [-r, r] with V0(d0) = V0, by
+ * bisection down to adjacent doubles (V0 increases strictly on [-r, r]).  By
+ * the symmetry V0(-d0) = 1 - V0(d0) the search runs for W = min(V0, 1 - V0)
+ * on [-r, 0] and the sign is restored, so the residual stays relative to W. */
 ORC_EXPORT double oracle_sphere_offset(double V0)
 {
     double r = sphere_radius(), W, lo, hi, d;
@@ -666,6 +680,7 @@ ORC_EXPORT double oracle_sphere_offset(double V0)
     return V0 <= 0.5 ? d : -d;
 }
 
+/* Sec. 3, cell by cell (OpenMP). */
 ORC_EXPORT void oracle_sphere_volume_batch(const double *d0, double *V0, int64_t n)
 {
     int64_t i;
@@ -673,6 +688,7 @@ ORC_EXPORT void oracle_sphere_volume_batch(const double *d0, double *V0, int64_t
     for (i = 0; i < n; ++i) V0[i] = oracle_sphere_volume(d0[i]);
 }
 
+/* Sec. 3, cell by cell (OpenMP). */
 ORC_EXPORT void oracle_sphere_offset_batch(const double *V0, double *d0, int64_t n)
 {
     int64_t i;
