@@ -141,7 +141,8 @@ def offset(nx, ny, nz, V0):
 
 
 def area_centroid(nx, ny, nz, d0):
-    """Area and centroid (cube-centred coordinates) of the cut polygon."""
+    """Area and centroid (cube-centred coordinates) of the cut polygon of the
+    plane n.x = d0 (Eq. 1) with the cell."""
     lib = _load()
     nx, ny, nz, d0 = (_f64(a).ravel() for a in np.broadcast_arrays(nx, ny, nz, d0))
     A, cx, cy, cz = (np.empty(nx.shape, np.float64) for _ in range(4))
@@ -151,7 +152,8 @@ def area_centroid(nx, ny, nz, d0):
 
 
 def offset_grad(nx, ny, nz, d0, g):
-    """Vector-Jacobian product of d0(n, V0) at the solution d0.
+    """Vector-Jacobian product of d0(n, V0) at the solution d0 (implicit
+    function theorem on Eq. 1).
 
     Returns (g_V0, g_nx, g_ny, g_nz) = g * (|n|/A, c_x, c_y, c_z)."""
     nx, ny, nz, d0, g = (_f64(a).ravel() for a in np.broadcast_arrays(nx, ny, nz, d0, g))
@@ -161,7 +163,8 @@ def offset_grad(nx, ny, nz, d0, g):
 
 
 def volume_grad(nx, ny, nz, d0, g):
-    """Vector-Jacobian product of V0(n, d0).
+    """Vector-Jacobian product of V0(n, d0) (derivatives of Eq. 10: slice area
+    and first moment of the cut polygon).
 
     Returns (g_d0, g_nx, g_ny, g_nz) = g * (A/|n|, -A c/|n|)."""
     nx, ny, nz, d0, g = (_f64(a).ravel() for a in np.broadcast_arrays(nx, ny, nz, d0, g))
@@ -201,7 +204,8 @@ def paraboloid_kappa(x5) -> float:
 
 
 def curvature_cell(phi27, flags: int = 0, iface27=None, nn=None):
-    """Curvature of one stencil; returns (kappa, fit_dim, n_points).
+    """Curvature of one stencil (Sec. 4.2, Appendix B: Eqs. 36, 38, 42);
+    returns (kappa, fit_dim, n_points).
 
     ``nn`` (27 x 3, optional, used with NEIGHBOR_NORMAL): the normal of each
     neighbour's PLIC plane; zero rows mean the centre normal."""
@@ -228,7 +232,8 @@ def cm_normal(phi27):
 
 
 def normals(phi, idx, flags: int = 0):
-    """PY (or CM with NORMAL_CM) normals of the listed cells, shape (3, k)."""
+    """PY (Eq. 38; or the CM normal of Appendix B with NORMAL_CM) normals of
+    the listed cells, shape (3, k)."""
     phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float32))
     nz, ny, nx = phi.shape
     idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
@@ -273,7 +278,8 @@ def interface_cells(phi) -> np.ndarray:
 
 
 def curvature(phi, idx, flags: int = 0):
-    """kappa (FP64) for the curvature cells ``idx`` of the FP32 field ``phi``.
+    """kappa (FP64) for the curvature cells ``idx`` of the FP32 field ``phi``
+    (the curvature step of Sec. 4.2 and Appendix B).
 
     ``phi`` has shape (nz, ny, nx).  Returns (kappa, fit_dim, n_points)."""
     phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float32))
@@ -288,7 +294,8 @@ def curvature(phi, idx, flags: int = 0):
 
 
 def curvature_grad_fd(phi, idx, w, h: float = 1e-4, flags: int = 0):
-    """Central-difference gradient of sum_k w_k kappa_k w.r.t. the dense field."""
+    """Central-difference gradient of sum_k w_k kappa_k w.r.t. the dense field
+    (the adjoint of the curvature step of Sec. 4.2, by brute force)."""
     phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float32))
     nz, ny, nx = phi.shape
     idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
