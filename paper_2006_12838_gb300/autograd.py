@@ -69,12 +69,16 @@ class VofCurvature(torch.autograd.Function):
 
 
 def offset(nx, ny, nz, V0, method="sz_opt", precision=None):
+    """d0(n, V0) of Eq. 1, differentiable in n and V0 (implicit function theorem)."""
     return PlicOffset.apply(nx, ny, nz, V0, method, precision)
 
 
 def volume(nx, ny, nz, d0):
+    """V0(n, d0) of Eq. 10, differentiable in n and d0."""
     return PlicVolume.apply(nx, ny, nz, d0)
 
 
 def curvature(phi, idx, method="sz_opt", flags=0):
+    """kappa of the listed interface cells (Sec. 4.2, Appendix B), differentiable
+    in phi with the interface set held fixed."""
     return VofCurvature.apply(phi, idx, method, flags)

@@ -207,7 +207,9 @@ def offset_roundtrip(nx, ny, nz, V0, method="sz_opt", precision=None, faithful=F
 
 
 def offset_backward(nx, ny, nz, d0, g_d0, stream=None, need=(True, True)):
-    """(g_V0, g_nx, g_ny, g_nz) of plic_offset at its solution d0."""
+    """(g_V0, g_nx, g_ny, g_nz) of plic_offset at its solution d0 (implicit
+    function theorem on Eq. 1: g/A and g c, A and c the cut polygon's area and
+    centroid)."""
     _cuda(nx, ny, nz, d0, g_d0, dtype=d0.dtype)
     p = 2 if d0.dtype == torch.float64 else 0
     gV = torch.empty_like(d0) if need[0] else None
@@ -219,7 +221,8 @@ def offset_backward(nx, ny, nz, d0, g_d0, stream=None, need=(True, True)):
 
 
 def volume_backward(nx, ny, nz, d0, g_V0, stream=None, need=(True, True)):
-    """(g_d0, g_nx, g_ny, g_nz) of plic_volume."""
+    """(g_d0, g_nx, g_ny, g_nz) of plic_volume (derivatives of Eq. 10: g A and
+    -g A c)."""
     _cuda(nx, ny, nz, d0, g_V0, dtype=d0.dtype)
     p = 2 if d0.dtype == torch.float64 else 0
     gd = torch.empty_like(d0) if need[0] else None
@@ -308,7 +311,8 @@ def normals(phi, idx, n_iface=None, count=None, out=None, flags=0, stream=None):
 
 def curvature_backward(phi, idx, g_kappa, n_iface=None, count=None, g_phi=None,
                        method="sz_opt", flags=0, workspace=None, stream=None):
-    """g_phi = d(sum g_kappa * kappa)/d phi (dense, same shape as phi)."""
+    """g_phi = d(sum g_kappa * kappa)/d phi (dense, same shape as phi): the
+    adjoint of the curvature step of Sec. 4.2 and Appendix B."""
     _cuda(phi, g_kappa, dtype=torch.float32)
     nz, ny, nx = phi.shape
     n = idx.numel() if n_iface is None else int(n_iface)
@@ -358,11 +362,12 @@ class BatchedFields:
 
 def curvature_batched(fields, method="sz_opt", flags=0, tuning=None, workspace=None,
                       stream=None):
-    """One persistent launch over many fields.  ``fields``: a BatchedFields, or a
-    list of (phi, idx, n_iface, kappa) with device tensors; ``tuning``: optional
-    (block_threads, cells_per_chunk, blocks_per_sm[, lanes_per_cell]) with
-    lanes_per_cell 8 (cooperative groups), 1 (one thread per cell) or 0
-    (the library's default)."""
+    """The curvature step (Sec. 4.2, Appendix B) over many fields in one
+    persistent launch.  ``fields``: a BatchedFields, or a list of (phi, idx,
+    n_iface, kappa) with device tensors; ``tuning``: optional (block_threads,
+    cells_per_chunk, blocks_per_sm[, lanes_per_cell]) with lanes_per_cell 8
+    (cooperative groups), 1 (one thread per cell) or 0 (the library's
+    default)."""
     if not isinstance(fields, BatchedFields):
         fields = BatchedFields(fields, workspace)
     tun = None
