@@ -180,8 +180,8 @@ plic_status vof_interface_compact(const float *phi, int nx, int ny, int nz, int3
                                   int64_t idx_capacity, int64_t *d_count, void *workspace,
                                   size_t ws_bytes, void *stream);
 
-/* vof_interface_compact_noalloc -- the same interface-cell list as
- * vof_interface_compact (Sec. 4.1, Eq. 33; identical output), for callers that cannot allocate
+/* vof_interface_compact_noalloc -- the same interface-cell list and count as
+ * vof_interface_compact (identical output), for callers that cannot allocate
  * device memory: a solver that owns every byte of the GPU through its own
  * pool, code that runs where cudaMalloc is not allowed or too slow to call (a
  * real-time step loop, a callback that must not synchronise the device), or a
@@ -190,14 +190,17 @@ plic_status vof_interface_compact(const float *phi, int nx, int ny, int nz, int3
  * Its scratch (one int per tile of at least 8192 cells) is a fixed array inside the
  * library, held by every GPU that loads the library until the process exits,
  * so fields are limited to PLIC_NOALLOC_MAX_CELLS cells; larger fields return
- * PLIC_ERR_ARG with an explanation in plic_last_error().  The call allocates
- * nothing.  Its first call on a device looks up the scratch address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before capturing a stream into a graph.  All calls on a device share the
- * one scratch array: calls that may run at the same time on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
- * The scratch needs no clearing between calls.  Other arguments and the
- * output are as for vof_interface_compact. */
+ * PLIC_ERR_ARG with an explanation in plic_last_error() and launch nothing.
+ * The call allocates nothing.  Its first call on a device looks up the
+ * scratch address (cudaGetSymbolAddress) with that device current and keeps
+ * it for the life of the process; make that first call before capturing a
+ * stream into a graph, and do not keep calling it across a reset of the
+ * device (cudaDeviceReset): the kept address belongs to the old context.
+ * All calls on a device share the one scratch array: calls that may run at
+ * the same time on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  The scratch needs no clearing between calls
+ * (every entry a call reads is written earlier in the same call).  Other
+ * arguments and the output are as for vof_interface_compact. */
 #define PLIC_NOALLOC_MAX_CELLS 268435456LL  /* 2^28 cells: at most 65537 tiles, 256 KiB */
 plic_status vof_interface_compact_noalloc(const float *phi, int nx, int ny, int nz,
                                           int32_t *idx, int64_t idx_capacity,

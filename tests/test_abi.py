@@ -47,17 +47,27 @@ PLUMBING = {"plic_workspace_bytes", "plic_curv_bwd_workspace_bytes", "plic_statu
             "plic_last_error", "plic_abi_version", "plic_host_device_pointer"}
 
 
+# deployment variants of a compute entry: no passage of the paper defines
+# them, and their comment says so instead of citing one
+DEPLOYMENT = {"vof_interface_compact_noalloc"}
+
+
 def test_every_compute_entry_cites_its_passage():
     txt = open(HEADER).read()
     blocks = re.findall(r"/\*(.*?)\*/", txt, flags=re.S)
     cite = re.compile(r"\b(Sec\.\s*\d|Eqs?\.\s*\d|Appendix\s+[A-Z])")
+    for name in DEPLOYMENT:
+        heads = [b for b in blocks if re.match(r"\s*%s\b" % name, b)]
+        flat = " ".join(heads[0].replace("*", " ").split()) if heads else ""
+        assert "no counterpart" in flat and not cite.search(flat), name
     for name in declared_functions():
-        if name in PLUMBING:
+        if name in PLUMBING or name in DEPLOYMENT:
             continue
         heads = [b for b in blocks if re.match(r"\s*(\w+\s*/\s*)?%s\b" % name, b)]
         assert heads, "%s has no doc block naming it" % name
         assert any(cite.search(b) for b in heads), "%s cites no passage" % name
     assert PLUMBING <= set(declared_functions())
+    assert DEPLOYMENT <= set(declared_functions())
 
 
 def test_status_strings_and_version(lib):
@@ -108,6 +118,12 @@ def test_host_side_argument_checks(lib):
     assert lib.vof_interface_compact(ok, 64, 64, 64, ok, 10, ok, ok, 4, None) == ERR_ARG
     assert lib.vof_interface_compact(ok, 64, 64, 64, ok, 10, ok, P(264), 1 << 20, None) == ERR_ALIGN
     assert lib.vof_interface_compact(ok, 2048, 2048, 1024, ok, 10, ok, ok, 1 << 30, None) == ERR_ARG
+    # allocation-free compaction: 2^28 + 1 = 17 x 15790321 cells, one cell over
+    # the built-in scratch's limit, is refused before any CUDA call
+    assert lib.vof_interface_compact_noalloc(ok, 17, 15790321, 1, ok, 10, ok, None) == ERR_ARG
+    assert b"limit" in lib.plic_last_error()
+    assert lib.vof_interface_compact_noalloc(ok, -1, 8, 8, ok, 10, ok, None) == ERR_ARG
+    assert lib.vof_interface_compact_noalloc(ok, 8, 8, 8, ok, 10, None, None) == ERR_ARG
     # host-mapped address query: null arguments
     out = ctypes.c_void_p()
     assert lib.plic_host_device_pointer(None, ctypes.byref(out)) == ERR_ARG

@@ -202,3 +202,62 @@ def test_fd_gradient_consistency(orc):
         x, y, z = c % nx, (c // nx) % ny, c // (nx * ny)
         near[z - 1:z + 2, y - 1:y + 2, x - 1:x + 2] = True
     assert np.all(g1[~near] == 0)
+
+
+def test_fd_gradient_matches_global_difference_quotient(orc):
+    """The oracle's curvature gradient against the plain definition of a
+    derivative: for a probe cell j, phi_j is moved by +-h in the whole field,
+    kappa is recomputed by the curvature oracle on the fixed list, and
+    sum_k w_k (kappa_k(+) - kappa_k(-)) is divided by the actual step.  A
+    mirrored or shifted scatter offset, or a weight applied to the wrong cell,
+    moves the gradient of j to another cell and fails here.  The field is the
+    adjoint workload in miniature: an ellipsoid with 1e-3 noise on the
+    interface cells, clamped to [2e-4, 1 - 2e-4], so that no probe (an
+    interface cell) crosses 0 or 1 under the step."""
+    phi, _ = synth.adjoint_field(seed=4, edge=48, semi=(8.0, 11.0, 14.0))
+    p = phi.numpy().copy()
+    idx = orc.interface_cells(p)
+    rng = np.random.default_rng(46)
+    w = rng.standard_normal(idx.size)
+    h = 1e-6
+    g = orc.curvature_grad_fd(p, idx, w, h).ravel()
+    nz, ny, nx = p.shape
+    offs = np.array([dx + nx * (dy + ny * dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1)
+                     for dx in (-1, 0, 1)])
+    cover = np.zeros(p.size, np.int64)
+    for o in offs:
+        np.add.at(cover, idx.astype(np.int64) + o, 1)
+    flat = p.ravel()
+    iface = (flat > 0) & (flat < 1)
+    cand = np.flatnonzero(iface & (cover > 0))
+    # cells inside the most overlapping stencils, interface cells inside the
+    # fewest, and the corner entries (+-1, +-1, +-1) of listed cells
+    dense = cand[np.argsort(-cover[cand], kind="stable")[:20]]
+    low = cand[cover[cand] <= np.sort(cover[cand])[40]]
+    sparse = rng.choice(low, 15, replace=False)
+    corner_off = [dx + nx * (dy + ny * dz) for dz in (-1, 1) for dy in (-1, 1) for dx in (-1, 1)]
+    corners = []
+    for k in rng.permutation(idx.size):
+        j = int(idx[k]) + corner_off[len(corners) % 8]
+        if iface[j]:
+            corners.append(j)
+        if len(corners) == 15:
+            break
+    probes = np.unique(np.concatenate([dense, sparse, np.array(corners)]))
+    assert probes.size >= 45
+    assert cover[dense].min() >= 16 and cover[sparse].max() <= 11
+    gscale = np.abs(g).max()
+    worst = 0.0
+    for j in probes:
+        q = flat.copy()
+        q[j] = np.float32(flat[j] + h)
+        sp = float(q[j])
+        kp, *_ = orc.curvature(q.reshape(p.shape), idx)
+        q[j] = np.float32(flat[j] - h)
+        sm = float(q[j])
+        km, *_ = orc.curvature(q.reshape(p.shape), idx)
+        gq = float(np.dot(w, kp - km)) / (sp - sm)
+        rel = abs(gq - g[j]) / max(abs(gq), 1e-3 * gscale)
+        worst = max(worst, rel)
+        assert rel <= 1e-6, (j, gq, g[j], cover[j])
+    print("global difference quotient: %d probes, max rel %.2e" % (probes.size, worst))
