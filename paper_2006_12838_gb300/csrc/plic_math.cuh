@@ -3,7 +3,7 @@
 // Fm<float>  : the FP32 fast path: MUFU-based sin/cos (__sinf/__cosf), MUFU
 //              reciprocal and reciprocal square root for division and sqrt, a
 //              cube root from the MUFU exp2/log2 pair refined by one Newton
-//              step, and arcsine/arccosine/arctangent from one arcsine series.
+//              step, and arcsine/arccosine/polar angle from one arcsine series.
 // Fm<double> : plain double-precision library functions.
 //
 // Constants are written as their closed forms (the decimals printed in the
@@ -61,25 +61,23 @@ template <> struct Fm<float> {
     static __device__ __forceinline__ T cos_(T x) { return __cosf(x); }
     static __device__ __forceinline__ T asin_(T x) { return fast_asinf(x); }
     static __device__ __forceinline__ T acos_(T x) { return 1.5707963267948966f - fast_asinf(x); }
-    // atan(u) for u >= 0 through the arcsine: atan(u) = asin(u / sqrt(1+u^2)),
-    // evaluated on min(u, 1/u) so that the arcsine argument stays <= 1/sqrt 2
-    static __device__ __forceinline__ T atan_(T u) {
-        const bool inv = u > 1.0f;
-        const float w = inv ? __fdividef(1.0f, u) : u;
-        const float r = fast_asinf(w * rsqrtf(fmaf(w, w, 1.0f)));
-        return inv ? 1.5707963267948966f - r : r;
+    // atan2(y, x) for x, y >= 0 from sine and cosine: the arcsine of the
+    // smaller of y/r and x/r (at most 1/sqrt 2), reflected about pi/4 where
+    // y > x; the arcsine of a sine near 1 would lose half the digits
+    static __device__ __forceinline__ T polar_angle_(T x, T y) {
+        const float r2 = fmaf(x, x, y * y);
+        if (!(r2 > 0.0f)) return 0.0f;
+        const float ir = rsqrtf(r2);
+        const float a = fast_asinf(fminf(fminf(x, y) * ir, 1.0f));
+        return y <= x ? a : 1.5707963267948966f - a;
     }
     static __device__ __forceinline__ T div_(T a, T b) { return __fdividef(a, b); }
     static __device__ __forceinline__ T rcp_(T a) { return __fdividef(1.0f, a); }
     static __device__ __forceinline__ T fdim_(T a, T b) { return fmaxf(a - b, 0.0f); }
     static __device__ __forceinline__ T tiny() { return 1.17549435e-38f; }   // FLT_MIN
     static __device__ __forceinline__ T eps() { return 5.9604645e-08f; }    // 2^-24
-    // number of halvings that shrink a width w to the unit roundoff, as the
-    // nested-interval listing computes it: floor(log2(w * 2^24)) from the
-    // exponent bits (w > 0)
-    static __device__ __forceinline__ int log2_halvings(T w) {
-        return (int)((__float_as_uint(w * 16777216.0f) >> 23) & 0xff) - 127;
-    }
+    // binary exponent floor(log2 |w|) (the library's ilogb)
+    static __device__ __forceinline__ int ilogb_(T w) { return ilogbf(w); }
     static __device__ __forceinline__ float exp2f_approx(float x) {
         float r;
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -101,30 +99,31 @@ template <> struct Fm<double> {
     static __device__ __forceinline__ T cos_(T x) { return cos(x); }
     static __device__ __forceinline__ T asin_(T x) { return asin(x); }
     static __device__ __forceinline__ T acos_(T x) { return acos(x); }
-    static __device__ __forceinline__ T atan_(T x) { return atan(x); }
+    static __device__ __forceinline__ T polar_angle_(T x, T y) { return atan2(y, x); }
     static __device__ __forceinline__ T div_(T a, T b) { return a / b; }
     static __device__ __forceinline__ T rcp_(T a) { return 1.0 / a; }
     static __device__ __forceinline__ T fdim_(T a, T b) { return fmax(a - b, 0.0); }
     static __device__ __forceinline__ T tiny() { return 2.2250738585072014e-308; }  // DBL_MIN
     static __device__ __forceinline__ T eps() { return 1.1102230246251565e-16; }    // 2^-53
-    static __device__ __forceinline__ int log2_halvings(T w) {
-        return (int)((__double_as_longlong(w * 9007199254740992.0) >> 52) & 0x7ff) - 1023;
-    }
+    static __device__ __forceinline__ int ilogb_(T w) { return ilogb(w); }
 };
 
-// Closed-form constants (Sec. 2.3, Eqs. 13-22; Sec. 2.4).
+// Closed-form constants (Sec. 2.3, Eqs. 13-22; Sec. 2.4).  The two_* values are
+// the factor 2 of Eq. 11 folded into a3, b3, a4, b4 (the FP32 paired solver).
 template <typename T> struct Kc {
+    static constexpr T cbrt54 = (T)3.7797631496846195;             // 54^(1/3)       (a3 / n1 n2)
+    static constexpr T inv_cbrt432 = (T)0.13228342099734996;       // 1 / 432^(1/3)  (b3)
+    static constexpr T inv_cbrt864 = (T)0.10499342082457276;       // 1 / 864^(1/3)  (a4 / t4)
+    static constexpr T inv_cbrt3456 = (T)0.066141710498674978;     // 1 / 3456^(1/3) (b4)
     static constexpr T two_cbrt54 = (T)7.559526299369239;          // 2 * 54^(1/3)
     static constexpr T two_over_cbrt432 = (T)0.26456684199469993;  // 2 / 432^(1/3)
     static constexpr T two_over_cbrt864 = (T)0.20998684164914555;  // 2 / 864^(1/3)
     static constexpr T two_over_cbrt3456 = (T)0.13228342099734997; // 2 / 3456^(1/3)
     static constexpr T inv_sqrt12 = (T)0.28867513459481287;        // 1 / sqrt(12)
     static constexpr T pi_6 = (T)0.52359877559829887;              // pi / 6
-    static constexpr T four_pi_3 = (T)4.1887902047863905;          // 4 pi / 3
+    static constexpr T four_pi = (T)12.566370614359173;            // 4 pi
     static constexpr T third = (T)0.33333333333333333;
-    static constexpr T sixth = (T)0.16666666666666667;
-    static constexpr T ninth = (T)0.11111111111111111;
-    static constexpr T inv27 = (T)0.037037037037037037;
+    static constexpr T twelfth = (T)0.083333333333333333;
 };
 
 template <typename T> __device__ __forceinline__ T sq(T x) { return x * x; }

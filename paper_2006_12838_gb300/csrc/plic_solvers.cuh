@@ -5,22 +5,22 @@
 // the cube corner, and d0 = sign(V0 - 1/2) ((n1+n2+n3)/2 - d).
 //
 // Solvers (reduced space, one function each, templated on float/double):
-//   solve_analytic  -- the paper's inversion (Sec. 2.3, Eqs. 11-25): a-priori
-//                      tests for cases (5), (2), (1) (Eq. 24, with the factor 2
-//                      of the case-(2) test that the derivation d2 <= n2 gives),
-//                      then the trigonometric root f(x, y, a, b, c) of Eq. 11
-//                      for case (3) and, if d3 > n3, for case (4).
+//   solve_analytic  -- the paper's inversion (Sec. 2.3, Eqs. 11-25): the
+//                      closed forms of cases (5), (1), (2) by the tests of
+//                      Eq. 24, then the real root f(x, y, a, b, c) of Eq. 11
+//                      for case (3) or (4).
 //   solve_sz_orig   -- Scardovelli-Zaleski as Kawano implements it (Sec. 2.4):
-//                      L1-normalised n, thresholds v1, v3, the cubic solved by
-//                      the cosine form.
+//                      L1-normalised n, its volume thresholds, the case-(3)/(4)
+//                      cubic in Viete's trigonometric form.
 //   solve_sz_opt    -- the paper's optimised SZ (Sec. 2.4): order 5 -> 2 -> 1,
-//                      cases (3)/(4) merged through the coefficients (a, b, c)
-//                      and the sine/arcsine form.
+//                      cases (3)/(4) merged into one arcsine/sine root.
 //   solve_newton    -- Newton-Raphson for cases (1), (3), (4) (Sec. 2.5).
 //   solve_nested    -- nested intervals for cases (3), (4) (Sec. 2.5).
-// FAITHFUL selects the paper-literal variant of each (printed iteration counts,
-// no argument clamps); the default adds clamps, convergence tests and a
-// cancellation-free cubic where the printed form loses digits.
+// FAITHFUL selects the paper-literal behaviour of each (the printed front end
+// of Eqs. 4-5, the printed iteration counts on Eq. 10 as printed, no clamp of
+// the trigonometric arguments, the analytic solution's a-posteriori case
+// order); the default adds clamps, convergence tests and cancellation-free
+// forms where the printed ones lose digits.
 //
 // polish()          -- one Newton step on the reduced volume (Eq. 10) written
 //                      without cancellation; used by PLIC_FP32_POLISHED.
@@ -44,13 +44,13 @@ __device__ __forceinline__ void reduce_normal(T nx, T ny, T nz, T& n1, T& n2, T&
     const T ax = fabs(nx), ay = fabs(ny), az = fabs(nz);
     n1 = fmin(fmin(ax, ay), az);
     n3 = fmax(fmax(ax, ay), az);
-    if (FAITHFUL) n2 = ax - n1 + ay + az - n3;
+    if (FAITHFUL) n2 = (ax + ay + az) - n1 - n3;               // Eq. 4 as printed
     else n2 = fmax(fmin(ax, ay), fmin(fmax(ax, ay), az));
 }
 
 template <typename T, bool FAITHFUL>
 __device__ __forceinline__ T reduce_volume(T V0) {
-    if (FAITHFUL) return T(0.5) - fabs(V0 - T(0.5));
+    if (FAITHFUL) return T(0.5) - fabs(V0 - T(0.5));          // Eq. 5 as printed
     return V0 <= T(0.5) ? V0 : T(1) - V0;
 }
 
@@ -94,143 +94,189 @@ __device__ __forceinline__ T polish(T d, T V, T n1, T n2, T n3) {
 }
 
 // ----------------------------------------------------------------------------
-// Sec. 2.3: the analytic solution (Eq. 25 with the a-priori tests of Eq. 24).
+// Eqs. 24-25: the closed-form cases.  classify() applies the a-priori tests on
+// V of Eq. 24 (case (2) with the factor 2 that its condition d2 <= n2 gives)
+// and keeps the products that the closed forms reuse.  The tests of cases (1)
+// and (2) exclude each other (n1^2 > 6 V n2 n3 against n1^2 <= 6 V n2 n3), so
+// (1) is tested before (2).  After case (5) n2 > 0; a normal with n1 = 0
+// always ends in case (2) or (5), so cases (1), (3), (4) have n1 > 0.
 // ----------------------------------------------------------------------------
-template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T solve_analytic(T V, T n1, T n2, T n3) {
+template <typename T> struct Cases {
+    T n12;   // n1 + n2
+    T h;     // V n3            (the case-(5) offset is h + n12/2)
+    T w;     // 6 V n2 n3       (compared with n1^2 in Eq. 24)
+    T q;     // n1^2
+    int c;   // 5, 1 or 2; 0 when the offset lies in case (3) or (4)
+};
+
+template <typename T>
+__device__ __forceinline__ Cases<T> classify(T V, T n1, T n2, T n3) {
+    Cases<T> k;
+    k.n12 = n1 + n2;
+    k.h = n3 * V;
+    k.w = T(6) * n2 * k.h;
+    k.q = n1 * n1;
+    if (k.n12 <= k.h + k.h) k.c = 5;
+    else if (k.w < k.q) k.c = 1;
+    else if (T(3) * n2 * (k.h + k.h + n1 - n2) <= k.q) k.c = 2;
+    else k.c = 0;
+    return k;
+}
+
+// The offset of case (5), (2) or (1) of Eq. 25:
+//   d5 = V n3 + (n1 + n2)/2,  d2 = n1/2 + sqrt(2 V n2 n3 - n1^2/12),
+//   d1 = (6 V n1 n2 n3)^(1/3).
+template <typename T>
+__device__ __forceinline__ T closed_form(const Cases<T>& k, T n1) {
     typedef Fm<T> F;
-    typedef Kc<T> K;
-    const T n12 = n1 + n2, n3V = n3 * V;
-    if (n12 <= T(2) * n3V) return n3V + T(0.5) * n12;                          // case (5)
-    const T V6n2n3 = T(6) * n2 * n3V, sqn1 = n1 * n1;
-    if (V6n2n3 >= sqn1 && T(3) * n2 * (T(2) * n3V + n1 - n2) <= sqn1)            // case (2)
-        return T(0.5) * n1 + K::inv_sqrt12 * F::sqrt_(T(24) * n2 * n3V - sqn1);
-    if (V6n2n3 < sqn1) return F::cbrt_(V6n2n3 * n1);                             // case (1)
-    // case (3): f(x3, y3, a3, b3, c3); x3 > 0 since n1, n2 > 0 here
-    const T n1n2 = n1 * n2;
-    const T x3 = T(81) * n1n2 * (n12 - T(2) * n3V);
-    const T y32 = F::fdim_(T(23328) * cb(n1n2), x3 * x3);
-    const T u3 = F::cbrt_(x3 * x3 + y32);
-    const T d3 = n12 - (K::two_cbrt54 * n1n2 + K::two_over_cbrt432 * u3) * F::rsqrt_(u3) *
-                           F::sin_(K::pi_6 - K::third * F::atan_(F::div_(F::sqrt_(y32), x3)));
-    if (d3 <= n3) return d3;
-    // case (4): f(x4, y4, a4, b4, c4); x4 kept > 0 so that atan(y/x) replaces atan2
-    const T t4 = T(9) * sq(n12 + n3) - T(18);
-    const T x4 = fmax(n1n2 * n3 * (T(324) - T(648) * V), F::tiny());
-    T y42 = T(4) * cb(t4) - x4 * x4;
-    if (!FAITHFUL) y42 = fmax(y42, T(0));
-    const T u4 = F::cbrt_(x4 * x4 + y42);
-    return T(0.5) * (n12 + n3) -
-           (K::two_over_cbrt864 * t4 + K::two_over_cbrt3456 * u4) * F::rsqrt_(u4) *
-               F::sin_(K::pi_6 - K::third * F::atan_(F::div_(F::sqrt_(y42), x4)));
+    if (k.c == 5) return k.h + T(0.5) * k.n12;
+    if (k.c == 2) return T(0.5) * n1 + F::sqrt_(k.w * T(1.0 / 3.0) - k.q * T(1.0 / 12.0));
+    return F::cbrt_(k.w * n1);
+}
+
+// Cases (3) or (4): the volume grows with d, so the offset lies in case (3)
+// (d <= n3) exactly when the volume at d = n3 is at least V; for
+// n3 >= n1 + n2 the offsets beyond n1 + n2 belong to case (5), so case (3) is
+// the only one left.  The volume at n3 comes from the cancellation-free
+// residual of Eq. 10 (n1 > 0 here).
+template <typename T>
+__device__ __forceinline__ bool offset_in_case3(const Cases<T>& k, T n1, T n2, T n3) {
+    if (!(n3 < k.n12)) return true;
+    T g, gp;
+    reduced_residual<T>(n3, k.w, n1, n2, n3, Fm<T>::rcp_(n1), g, gp);
+    return g >= T(0);
 }
 
 // ----------------------------------------------------------------------------
-// Sec. 2.4: Scardovelli-Zaleski as in Kawano's implementation.  Inputs are
-// the L1-normalised reduced quantities (m1 <= m2 <= m3, m1 + m2 + m3 = 1) and
-// the reduced volume w; returns the reduced offset alpha in L1 units.
-// For m = (0, 0, 1) and w = 0 the cubic branch is re-entered with alpha == 0
-// and its square-root argument is -1/4: the result is NaN, as the paper
-// reports for this implementation.
+// Sec. 2.3: the analytic solution.  The real form of Eq. 11,
+//   f(x, y, a, b, c) = c - 2 (a + b u) u^(-1/2) sin(pi/6 - theta/3),
+// with u = (x^2 + y^2)^(1/3) and theta = atan2(y, x), is the root of the cubic
+// of case (3) with the coefficients of Eqs. 12-16 and of case (4) with those
+// of Eqs. 17-22 (both need |n| = 1).  y enters only through y^2 >= 0 (its
+// rounding may make it slightly negative: clamped at 0).
+// Default: the case is decided first (offset_in_case3), and only that case's
+// root is formed.  FAITHFUL: the paper's a-posteriori order -- d3 first, kept
+// if d3 <= n3, else d4.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T eq11_root(T x, T y2, T a, T b, T c) {
+    typedef Fm<T> F;
+    y2 = fmax(y2, T(0));
+    const T u3 = x * x + y2;
+    const T u = F::cbrt_(u3);
+    const T ru = F::rsqrt_(u);
+    const T theta = F::polar_angle_(x, F::sqrt_(y2));
+    return c - T(2) * (a * ru + b * (u * ru)) * F::sin_(Kc<T>::pi_6 - Kc<T>::third * theta);
+}
+
+template <typename T>
+__device__ __forceinline__ T analytic_case3(T V, T n1, T n2, T n3, T n12) {
+    const T p = n1 * n2;
+    const T x = T(81) * p * (n12 - T(2) * V * n3);
+    return eq11_root<T>(x, T(23328) * p * p * p - x * x, Kc<T>::cbrt54 * p, Kc<T>::inv_cbrt432, n12);
+}
+
+template <typename T>
+__device__ __forceinline__ T analytic_case4(T V, T n1, T n2, T n3) {
+    const T L = n1 + n2 + n3;
+    const T t = T(9) * L * L - T(18);
+    const T x = T(324) * n1 * n2 * n3 * (T(1) - T(2) * V);
+    return eq11_root<T>(x, T(4) * t * t * t - x * x, Kc<T>::inv_cbrt864 * t, Kc<T>::inv_cbrt3456,
+                        T(0.5) * L);
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_analytic(T V, T n1, T n2, T n3) {
+    const Cases<T> k = classify<T>(V, n1, n2, n3);
+    if (k.c != 0) return closed_form<T>(k, n1);
+    if (FAITHFUL) {
+        const T d3 = analytic_case3<T>(V, n1, n2, n3, k.n12);
+        return d3 <= n3 ? d3 : analytic_case4<T>(V, n1, n2, n3);
+    }
+    return offset_in_case3<T>(k, n1, n2, n3) ? analytic_case3<T>(V, n1, n2, n3, k.n12)
+                                             : analytic_case4<T>(V, n1, n2, n3);
+}
+
+// ----------------------------------------------------------------------------
+// Sec. 2.4: the Scardovelli-Zaleski solution in the form of Kawano's
+// implementation, which the paper compares.  Inputs: the L1-normalised
+// m1 <= m2 <= m3 (m1 + m2 + m3 = 1) and the reduced volume w; the result is
+// the offset in L1 units.  Its cases are told apart by volumes: case (1) ends
+// at Vb1 = m1^2 / (6 m2 m3) (that implementation adds 1e-25 to the
+// denominator), case (2) at Vb2 = Vb1 + (m2 - m1)/(2 m3); case (3) ends at the
+// volume of the plane through the vertex m3 when m3 < m1 + m2 (case (4)
+// follows), else at that of the plane d = m1 + m2 (case (5) follows).  Cases
+// (3)/(4) are the monic cubic alpha^3 + a2 alpha^2 + a1 alpha + a0 = 0 of
+// Eq. 10, solved in Viete's trigonometric form: with alpha = t - a2/3 it
+// becomes t^3 + p t + q = 0, and the root is
+//   alpha = -a2/3 + 2 s cos((acos(r) + 4 pi)/3),  s^2 = -p/3,  r = -q/(2 s^3).
+// Default: s^2 and -q/2 multiplied out with m1 + m2 + m3 = 1 (case (3):
+// 2 m1 m2 and 1.5 m1 m2 (m1 + m2 - 2 m3 w); case (4):
+// (m1 (2 (m2 + m3) - m1) - (m3 - m2)^2)/4 and 0.75 m1 m2 m3 (1 - 2 w)), since
+// the general forms subtract O(1) terms to reach O(s^3) and lose every digit
+// when m1 << m2; r clamped to [-1, 1].  FAITHFUL: p and q from a2, a1, a0 and
+// no clamp.
+// That implementation treats a zero case-(5) offset as "no case found yet"
+// and solves the case-(4) cubic instead.  For m = (0, 0, 1) and w = 0 (V0 in
+// {0, 1}) that cubic has s^2 = -1/4 and the result is NaN, as the paper
+// reports; this reproduces it.
 // ----------------------------------------------------------------------------
 template <typename T, bool FAITHFUL>
 __device__ __forceinline__ T solve_sz_orig(T w, T m1, T m2, T m3) {
     typedef Fm<T> F;
     typedef Kc<T> K;
-    const T m12 = m1 + m2;
-    T alpha = T(0);
-    const T v1 = F::div_(sq(m1), T(6) * m2 * m3 + T(1e-25));
-    const T w6 = T(6) * m1 * m2 * m3 * w;
-    if (w < v1) {
-        alpha = F::cbrt_(w6);                                                     // case (1)
-    } else if (w < v1 + F::div_(T(0.5) * (m2 - m1), m3)) {
-        alpha = T(0.5) * (m1 + F::sqrt_(sq(m1) + T(8) * m2 * m3 * (w - v1)));     // case (2)
-    } else {
-        T v3;
-        if (m3 < m12) {
-            v3 = (sq(m3) * (T(3) * m12 - m3) + sq(m1) * (m1 - T(3) * m3) +
-                  sq(m2) * (m2 - T(3) * m3)) * F::rcp_(T(6) * m1 * m2 * m3);
-        } else {
-            v3 = F::div_(T(0.5) * m12, m3);
-            if (v3 <= w) alpha = m3 * w + T(0.5) * m12;                           // case (5)
-        }
-        if (alpha == T(0)) {
-            const bool case3 = w < v3;
-            T q0, sp, a2;
-            if (FAITHFUL) {
-                T a0, a1;
-                if (case3) {                                                      // case (3)
-                    a2 = T(-3) * m12;
-                    a1 = T(3) * (sq(m1) + sq(m2));
-                    a0 = w6 - cb(m1) - cb(m2);
-                } else {                                                          // case (4)
-                    a2 = T(-1.5);
-                    a1 = T(1.5) * (sq(m1) + sq(m2) + sq(m3));
-                    a0 = T(0.5) * (w6 - cb(m1) - cb(m2) - cb(m3));
-                }
-                q0 = K::sixth * (a1 * a2 - T(3) * a0) - K::inv27 * cb(a2);
-                sp = F::sqrt_(K::ninth * sq(a2) - K::third * a1);
-            } else {
-                // the same q0 and sp multiplied out: q0 = 1.5 m1 m2 (m12 - 2 m3 w),
-                // sp^2 = 2 m1 m2 in case (3); q0 = 0.75 m1 m2 m3 (1 - 2w),
-                // sp^2 = (m1 (2 (m2 + m3) - m1) - (m3 - m2)^2)/4 in case (4), using
-                // m1 + m2 + m3 = 1.  The printed forms subtract O(1) terms to get
-                // O(sp^3) and lose all digits when m1 << m2.
-                a2 = case3 ? T(-3) * m12 : T(-1.5);
-                q0 = case3 ? T(1.5) * m1 * m2 * (m12 - T(2) * m3 * w)
-                           : T(0.75) * m1 * m2 * m3 * (T(1) - T(2) * w);
-                sp = F::sqrt_(case3 ? T(2) * m1 * m2
-                                    : T(0.25) * (m1 * (T(2) * (m2 + m3) - m1) - sq(m3 - m2)));
-            }
-            T arg = F::div_(q0, cb(sp));
-            if (!FAITHFUL) arg = fmin(fmax(arg, T(-1)), T(1));
-            alpha = T(2) * sp * F::cos_(K::four_pi_3 + K::third * F::acos_(arg)) - K::third * a2;
-        }
+    const T m12 = m1 + m2, e3 = m1 * m2 * m3;
+    const T vb1 = F::div_(m1 * m1, T(6) * m2 * m3 + T(1e-25));
+    if (w < vb1) return F::cbrt_(T(6) * e3 * w);                                   // (1)
+    if (w < vb1 + F::div_(T(0.5) * (m2 - m1), m3))
+        return T(0.5) * m1 + F::sqrt_(T(2) * m2 * m3 * w - K::twelfth * m1 * m1);    // (2)
+    const bool tall = !(m3 < m12);
+    const T vb3 = tall ? F::div_(T(0.5) * m12, m3)
+                       : F::div_(cb(m3) - cb(m3 - m1) - cb(m3 - m2), T(6) * e3);
+    bool case3 = w < vb3;
+    if (!case3 && tall) {
+        const T a5 = m3 * w + T(0.5) * m12;                                         // (5)
+        if (a5 != T(0)) return a5;
     }
-    return alpha;
+    T s2, mq2, shift;                     // s^2, -q/2, -a2/3
+    if (FAITHFUL) {
+        const T w6 = T(6) * e3 * w;
+        const T a2 = case3 ? T(-3) * m12 : T(-1.5);
+        const T a1 = case3 ? T(3) * (m1 * m1 + m2 * m2) : T(1.5) * (m1 * m1 + m2 * m2 + m3 * m3);
+        const T a0 = case3 ? w6 - cb(m1) - cb(m2) : T(0.5) * (w6 - cb(m1) - cb(m2) - cb(m3));
+        const T p = a1 - K::third * a2 * a2;
+        const T q = T(2.0 / 27.0) * cb(a2) - K::third * a1 * a2 + a0;
+        s2 = -K::third * p;
+        mq2 = T(-0.5) * q;
+        shift = -K::third * a2;
+    } else {
+        s2 = case3 ? T(2) * m1 * m2 : T(0.25) * (m1 * (T(2) * (m2 + m3) - m1) - sq(m3 - m2));
+        mq2 = case3 ? T(1.5) * m1 * m2 * (m12 - T(2) * m3 * w) : T(0.75) * e3 * (T(1) - T(2) * w);
+        shift = case3 ? m12 : T(0.5);
+    }
+    const T s = F::sqrt_(s2);
+    T r = F::div_(mq2, s2 * s);
+    if (!FAITHFUL) r = fmin(fmax(r, T(-1)), T(1));
+    return shift + T(2) * s * F::cos_(K::third * (F::acos_(r) + K::four_pi));
 }
 
 // ----------------------------------------------------------------------------
-// Sec. 2.4: the paper's optimised SZ solution (L1-normalised inputs, the
-// reduced volume V; returns the reduced offset in L1 units).
-// ----------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T solve_sz_opt_listing(T V, T n1, T n2, T n3) {
-    typedef Fm<T> F;
-    typedef Kc<T> K;
-    const T n12 = n1 + n2, n3V = n3 * V;
-    if (n12 <= T(2) * n3V) return n3V + T(0.5) * n12;                          // case (5)
-    const T sqn1 = n1 * n1, n26 = T(6) * n2, v1 = sqn1 / n26;                   // n2 > 0 here
-    if (v1 <= n3V && n3V < v1 + T(0.5) * (n2 - n1))                              // case (2)
-        return T(0.5) * (n1 + F::sqrt_(sqn1 + T(8) * n2 * (n3V - v1)));
-    const T V6 = n1 * n26 * n3V;
-    if (n3V < v1) return F::cbrt_(V6);                                           // case (1)
-    // n1 > 0 here
-    const T v3 = n3 < n12 ? (sq(n3) * (T(3) * n12 - n3) + sqn1 * (n1 - T(3) * n3) +
-                             sq(n2) * (n2 - T(3) * n3)) / (n1 * n26)
-                          : T(0.5) * n12;
-    const T sqn12 = sqn1 + sq(n2), V6cbn12 = V6 - cb(n1) - cb(n2);
-    const bool case3 = n3V < v3;                                                 // else case (4)
-    const T a = case3 ? V6cbn12 : T(0.5) * (V6cbn12 - cb(n3));
-    const T b = case3 ? sqn12 : T(0.5) * (sqn12 + sq(n3));
-    const T c = case3 ? n12 : T(0.5);
-    const T t = F::sqrt_(sq(c) - b);
-    const T arg = (cb(c) - T(0.5) * a - T(1.5) * b * c) / cb(t);
-    return c - T(2) * t * F::sin_(K::third * F::asin_(arg));
-}
-
-// Default form of the optimised SZ solution.  Same cases, thresholds and
-// trigonometric root as the listing, with
-//  - the case tests multiplied out so that no division is needed
-//    (v1 <= n3 V  <=>  n1^2 <= 6 n2 n3 V;  n3 V < v3  <=>  6 n1 n2 n3 V < num3),
-//  - the arcsine argument (c^3 - a/2 - 3bc/2)/t^3 written without cancellation:
+// Sec. 2.4: the paper's optimised SZ solution: cases tested in the order
+// (5), (2), (1), cases (3) and (4) merged into one arcsine/sine root through
+// their coefficients (L1-normalised inputs, the reduced volume V; the result
+// in L1 units).  Here
+//  - the case tests are multiplied out so that no division is needed
+//    (Vb1 <= n3 V  <=>  n1^2 <= 6 n2 n3 V;  the case-(3)/(4) boundary
+//    6 n1 n2 n3 V < n3^3 - (n3 - n1)^3 - (n3 - n2)^3, written expanded),
+//  - the arcsine argument is written without cancellation:
 //    case (3): 1.5 n1 n2 (n1 + n2 - 2 n3 V) / (2 n1 n2)^(3/2),
-//    case (4): 0.75 n1 n2 n3 (1 - 2V) / t^3, t^2 = (n1 (2(n2+n3) - n1) - (n3-n2)^2)/4,
-//    (algebraically identical for n1 + n2 + n3 = 1), clamped to [-1, 1].
+//    case (4): 0.75 n1 n2 n3 (1 - 2V) / t^3, t^2 = (n1 (2(n2+n3) - n1) - (n3-n2)^2)/4
+//    (exact for n1 + n2 + n3 = 1), clamped to [-1, 1] unless FAITHFUL.
 // In FP32 every case is evaluated and the result selected (no divergent
 // branches; the warp pays for cases (1), (2) and (5) a few instructions each).
 // In FP64 the cases branch (the FP64 pipe is the bottleneck there).
-template <typename T>
+// ----------------------------------------------------------------------------
+template <typename T, bool CLAMP = true>
 __device__ __forceinline__ T solve_sz_opt_default(T V, T n1, T n2, T n3) {
     typedef Fm<T> F;
     typedef Kc<T> K;
@@ -252,7 +298,8 @@ __device__ __forceinline__ T solve_sz_opt_default(T V, T n1, T n2, T n3) {
     const T c = c3 ? n12 : T(0.5);
     const T rt = F::rsqrt_(t2);
     const T t = t2 * rt;
-    const T arg = fmin(fmax(q * (rt * rt * rt), T(-1)), T(1));
+    T arg = q * (rt * rt * rt);
+    if (CLAMP) arg = fmin(fmax(arg, T(-1)), T(1));
     const T d34 = c - T(2) * t * F::sin_(K::third * F::asin_(arg));
     if (sizeof(T) == 8) return d34;
     const T d5 = n3V + T(0.5) * n12;
@@ -263,26 +310,73 @@ __device__ __forceinline__ T solve_sz_opt_default(T V, T n1, T n2, T n3) {
 
 template <typename T, bool FAITHFUL>
 __device__ __forceinline__ T solve_sz_opt(T V, T n1, T n2, T n3) {
-    if (FAITHFUL) return solve_sz_opt_listing<T>(V, n1, n2, n3);
-    return solve_sz_opt_default<T>(V, n1, n2, n3);
+    return solve_sz_opt_default<T, !FAITHFUL>(V, n1, n2, n3);
 }
 
 // ----------------------------------------------------------------------------
-// Sec. 2.5: Newton-Raphson.  Cases (5) and (2) in closed form; case (1) by
-// Newton on d^3 = 6 V n1 n2 n3; cases (3) and (4) by Newton on the cubic of
-// Eq. 10 from the midpoints of [n2, n1+n2] and [n3, L/2].
-// Faithful: 7 steps from n1/2 (case 1), 4 steps (cases 3, 4), the cubic as
-// printed.  Default: the cancellation-free cubic g of reduced_residual(), a
-// start for case (1) from the exponent of 6 V n1 n2 n3, steps until
-// |dd| <= 4 ulp (at most 16) and a bracket safeguard (see newton_bracketed).
+// Sec. 2.5: the iterative solvers.  Both take the closed forms for cases (5)
+// and (2), then iterate on the volume of Eq. 10 inside the bracket of a case:
+// [0, n1] for case (1) (Newton only; nested intervals use the cube root),
+// [n2, n1 + n2] for case (3) and, when the case-(3) result passes n3,
+// [n3, L/2] for case (4).
+//
+// The paper-literal forms (FAITHFUL) run on Eq. 10 as printed: with k
+// corners cut off (none in case (1), two in case (3), three in case (4)),
+//   P(d) = d^3 - sum_{j <= k} (d - n_j)^3 = 6 n1 n2 n3 V,
+// plain Newton steps from the middle of the bracket (7 in case (1), 4 in
+// cases (3)/(4)), and k + 1 halvings for nested intervals, k the binary
+// exponent of the bracket width times 2^24 (2^53 in FP64; k at least 0): the
+// counts the paper uses, with no convergence test.
 // ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void eq10_printed(T d, int corners, T n1, T n2, T n3, T& P, T& dP) {
+    P = d * d * d;
+    dP = T(3) * d * d;
+    const T nk[3] = {n1, n2, n3};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j < corners) {
+            const T e = d - nk[j];
+            P -= e * e * e;
+            dP -= T(3) * e * e;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T newton_printed(T lo, T hi, int corners, int steps, T rhs6, T n1, T n2,
+                                            T n3) {
+    T d = T(0.5) * (lo + hi);
+    for (int i = 0; i < steps; ++i) {
+        T P, dP;
+        eq10_printed<T>(d, corners, n1, n2, n3, P, dP);
+        d -= (P - rhs6) / dP;
+    }
+    return d;
+}
+
+template <typename T>
+__device__ __forceinline__ T halve_printed(T lo, T hi, int corners, T rhs6, T n1, T n2, T n3) {
+    int k = Fm<T>::ilogb_(hi - lo) + (sizeof(T) == 4 ? 24 : 53);
+    k = k < 0 ? 0 : (k > 1100 ? 1100 : k);
+    T d = T(0.5) * (lo + hi);
+    for (int i = 0; i <= k; ++i) {
+        T P, dP;
+        eq10_printed<T>(d, corners, n1, n2, n3, P, dP);
+        if (P < rhs6) lo = d; else hi = d;
+        d = T(0.5) * (lo + hi);
+    }
+    return d;
+}
+
+// Default Newton: the cancellation-free residual of reduced_residual(), steps
+// until |dd| <= 4 ulp (at most 16).  A step that leaves the bracket is clamped
+// to the end it crossed (the root can sit exactly at an end, e.g. d = L/2 for
+// V0 = 1/2); crossing the same end again bisects.  From the bracket midpoint
+// this converges in at most 7 steps on the paper-shaped inputs.
 template <typename T>
 __device__ __forceinline__ T newton_bracketed(T d, T lo, T hi, T rhs, T n1, T n2, T n3,
                                               T inv_n1) {
-    // A step that leaves the bracket is clamped to the bracket end it crossed
-    // (the root can sit exactly at an end, e.g. d = L/2 for V0 = 1/2); a second
-    // crossing of the same end bisects.  From the bracket midpoint this
-    // converges in at most 7 steps on the paper-shaped inputs; 16 bounds it.
     for (int it = 0; it < 16; ++it) {
         T g, gp;
         reduced_residual<T>(d, rhs, n1, n2, n3, inv_n1, g, gp);
@@ -297,106 +391,62 @@ __device__ __forceinline__ T newton_bracketed(T d, T lo, T hi, T rhs, T n1, T n2
     return d;
 }
 
-template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T solve_newton(T V, T n1, T n2, T n3) {
-    typedef Fm<T> F;
-    typedef Kc<T> K;
-    const T n1pn2 = n1 + n2, n3xV = n3 * V;
-    if (n1pn2 <= T(2) * n3xV) return n3xV + T(0.5) * n1pn2;                     // case (5)
-    const T V6n2n3 = T(6) * n2 * n3xV, sqn1 = n1 * n1;
-    if (V6n2n3 >= sqn1 && T(3) * n2 * (T(2) * n3xV + n1 - n2) <= sqn1)          // case (2)
-        return T(0.5) * n1 + K::inv_sqrt12 * F::sqrt_(T(24) * n2 * n3xV - sqn1);
-    const T V6n1n2n3 = V6n2n3 * n1;
-    if (FAITHFUL) {
-        T d;
-        if (V6n2n3 < sqn1) {                                                     // case (1)
-            d = T(0.5) * n1;
-            for (int i = 0; i < 7; ++i) d -= (cb(d) - V6n1n2n3) / (T(3) * sq(d));
-            return d;
-        }
-        d = T(0.5) * (n2 + n1pn2);                                               // case (3)
-        for (int i = 0; i < 4; ++i) {
-            const T f = cb(d) - cb(d - n1) - cb(d - n2) - V6n1n2n3;
-            const T fs = T(3) * (sq(d) - sq(d - n1) - sq(d - n2));
-            d -= f / fs;
-        }
-        if (d <= n3) return d;
-        d = T(0.5) * (n3 + T(0.5) * (n1pn2 + n3));                               // case (4)
-        for (int i = 0; i < 4; ++i) {
-            const T f = cb(d) - cb(d - n1) - cb(d - n2) - cb(d - n3) - V6n1n2n3;
-            const T fs = T(3) * (sq(d) - sq(d - n1) - sq(d - n2) - sq(d - n3));
-            d -= f / fs;
-        }
-        return d;
-    }
-    const T inv_n1 = T(1) / n1;                                                  // n1 > 0 here
-    const T rhs = V6n2n3;
-    if (V6n2n3 < sqn1) {                                                         // case (1)
-        // start within a factor 2^(2/3) of the root from the binary exponent of
-        // X = 6 V n1 n2 n3 (the "log2 hack" of the nested-interval listing)
-        const T X = V6n1n2n3;
-        if (!(X > T(0))) return T(0);
-        const int e = F::log2_halvings(X) - (sizeof(T) == 4 ? 24 : 53);
-        const T d0 = fmin(ldexp(T(1), e / 3), n1);
-        return newton_bracketed<T>(d0, T(0), n1, rhs, n1, n2, n3, inv_n1);
-    }
-    T d = newton_bracketed<T>(T(0.5) * (n2 + n1pn2), n2, n1pn2, rhs, n1, n2, n3, inv_n1);
-    if (d <= n3) return d;                                                       // case (3)
-    const T hl = T(0.5) * (n1pn2 + n3);
-    return newton_bracketed<T>(T(0.5) * (n3 + hl), n3, hl, rhs, n1, n2, n3, inv_n1);  // (4)
-}
-
-// ----------------------------------------------------------------------------
-// Sec. 2.5: nested intervals.  Cases (5), (2), (1) in closed form; case (3) by
-// halving [n2, n1+n2] and, if the result exceeds n3, case (4) by halving
-// [n3, L/2].  Faithful: the printed predicate (cubes of Eq. 10) and
-// floor(log2(width * 2^24)) + 1 halvings (2^53 in double), with the count
-// clamped at 0 (the listing's unsigned count would wrap for widths below the
-// unit roundoff).  Default: the cancellation-free predicate and halving until
-// the ends are adjacent floating-point numbers (at most 128 halvings).
-// ----------------------------------------------------------------------------
-template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T bisect(T dmin, T dmax, T n1, T n2, T n3, bool with_n3, T V6n1n2n3,
-                                    T rhs, T inv_n1) {
-    T d = T(0.5) * (dmin + dmax);
-    if (FAITHFUL) {
-        int k = Fm<T>::log2_halvings(dmax - dmin);
-        k = k < 0 ? 0 : (k > 1100 ? 1100 : k);
-        for (int i = 0; i <= k; ++i) {
-            T f = cb(d) - cb(d - n1) - cb(d - n2);
-            if (with_n3) f -= cb(d - n3);
-            if (f < V6n1n2n3) dmin = d; else dmax = d;
-            d = T(0.5) * (dmin + dmax);
-        }
-        return d;
-    }
+// Default nested intervals: halve on the sign of the cancellation-free
+// residual until the two ends are adjacent floating-point numbers (at most
+// 128 halvings).
+template <typename T>
+__device__ __forceinline__ T halve_to_adjacent(T lo, T hi, T rhs, T n1, T n2, T n3, T inv_n1) {
+    T d = T(0.5) * (lo + hi);
     for (int i = 0; i < 128; ++i) {
         T g, gp;
         reduced_residual<T>(d, rhs, n1, n2, n3, inv_n1, g, gp);
-        if (g < T(0)) dmin = d; else dmax = d;
-        const T m = T(0.5) * (dmin + dmax);
-        if (m <= dmin || m >= dmax) break;
+        if (g < T(0)) lo = d; else hi = d;
+        const T m = T(0.5) * (lo + hi);
+        if (m <= lo || m >= hi) break;
         d = m;
     }
     return d;
 }
 
 template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T solve_nested(T V, T n1, T n2, T n3) {
-    typedef Fm<T> F;
-    typedef Kc<T> K;
-    const T n1pn2 = n1 + n2, n3xV = n3 * V;
-    if (n1pn2 <= T(2) * n3xV) return n3xV + T(0.5) * n1pn2;                     // case (5)
-    const T V6n2n3 = T(6) * n2 * n3xV, sqn1 = n1 * n1;
-    if (V6n2n3 >= sqn1 && T(3) * n2 * (T(2) * n3xV + n1 - n2) <= sqn1)          // case (2)
-        return T(0.5) * n1 + K::inv_sqrt12 * F::sqrt_(T(24) * n2 * n3xV - sqn1);
-    if (V6n2n3 < sqn1) return F::cbrt_(V6n2n3 * n1);                             // case (1)
-    const T V6n1n2n3 = V6n2n3 * n1;
+__device__ __forceinline__ T solve_newton(T V, T n1, T n2, T n3) {
+    const Cases<T> k = classify<T>(V, n1, n2, n3);
+    if (k.c == 5 || k.c == 2) return closed_form<T>(k, n1);
+    const T half = T(0.5) * (k.n12 + n3);                 // L/2
+    if (FAITHFUL) {
+        const T rhs6 = k.w * n1;                           // 6 V n1 n2 n3
+        if (k.c == 1) return newton_printed<T>(T(0), n1, 0, 7, rhs6, n1, n2, n3);
+        const T d = newton_printed<T>(n2, k.n12, 2, 4, rhs6, n1, n2, n3);
+        return d <= n3 ? d : newton_printed<T>(n3, half, 3, 4, rhs6, n1, n2, n3);
+    }
     const T inv_n1 = T(1) / n1;
-    T d = bisect<T, FAITHFUL>(n2, n1pn2, n1, n2, n3, false, V6n1n2n3, V6n2n3, inv_n1);
-    if (d <= n3) return d;                                                       // case (3)
-    return bisect<T, FAITHFUL>(n3, T(0.5) * (n1pn2 + n3), n1, n2, n3, true, V6n1n2n3,
-                               V6n2n3, inv_n1);                                  // case (4)
+    if (k.c == 1) {
+        // start within a factor 2^(2/3) of the root (d1^3 = X) from the binary
+        // exponent of X = 6 V n1 n2 n3
+        const T X = k.w * n1;
+        if (!(X > T(0))) return T(0);
+        const T d0 = fmin(ldexp(T(1), Fm<T>::ilogb_(X) / 3), n1);
+        return newton_bracketed<T>(d0, T(0), n1, k.w, n1, n2, n3, inv_n1);
+    }
+    const T d = newton_bracketed<T>(T(0.5) * (n2 + k.n12), n2, k.n12, k.w, n1, n2, n3, inv_n1);
+    if (d <= n3) return d;
+    return newton_bracketed<T>(T(0.5) * (n3 + half), n3, half, k.w, n1, n2, n3, inv_n1);
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_nested(T V, T n1, T n2, T n3) {
+    const Cases<T> k = classify<T>(V, n1, n2, n3);
+    if (k.c != 0) return closed_form<T>(k, n1);
+    const T half = T(0.5) * (k.n12 + n3);
+    if (FAITHFUL) {
+        const T rhs6 = k.w * n1;
+        const T d = halve_printed<T>(n2, k.n12, 2, rhs6, n1, n2, n3);
+        return d <= n3 ? d : halve_printed<T>(n3, half, 3, rhs6, n1, n2, n3);
+    }
+    const T inv_n1 = T(1) / n1;
+    const T d = halve_to_adjacent<T>(n2, k.n12, k.w, n1, n2, n3, inv_n1);
+    if (d <= n3) return d;
+    return halve_to_adjacent<T>(n3, half, k.w, n1, n2, n3, inv_n1);
 }
 
 // ----------------------------------------------------------------------------
