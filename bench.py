@@ -140,25 +140,172 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# operation counts of the solvers (compute side of their rooflines)
+# ---------------------------------------------------------------------------
+# Operation counts of the PLIC solvers per cell and intersection case, for the
+# compute side of their rooflines (measurement only; nothing here runs a solver).
+#
+# Units: an FP add, multiply, fused multiply-add, compare or min/max is one
+# operation.  Calls are counted apart: ``div``, ``sqrt``, ``rsqrt``, ``cbrt``,
+# ``sin``, ``cos``, ``asin``, ``acos``, ``atan2``.  In FP32 each call is the
+# fast form of the kernels (MUFU operations plus a few FP32 operations, see
+# ``FP32_CALL``); in FP64 each is a library call whose cost is measured by the
+# pipe probes in FP64-FMA equivalents (the FMA rate divided by the call rate).
+#
+# Counts follow the solver source (plic_solvers.cuh, default mode) case by case:
+#
+# * front end (sort of |n|, L, the validity tests, V = min(V0, 1 - V0), the
+#   final offset): 18; the optimised and Kawano SZ solutions add the L1
+#   normalisation (4 and a division);
+# * the a-priori tests of Eq. 24 with their shared products: 14;
+# * closed forms: case (5) 1, case (2) 3 + sqrt, case (1) 1 + cbrt;
+# * FP32-polished: the Newton step on Eq. 10 for cases (1)-(4), 22 + 2 div
+#   (2 in case (5));
+# * analytic, cases (3)/(4): the case test from the residual at d = n3
+#   (21 + div), the coefficients (11 in case (3), 15 in case (4)) and the root
+#   of Eq. 11 (10 + cbrt, rsqrt, sqrt, atan2, sin);
+# * optimised SZ: 28 for the division-free case tests, then 1 / 3 + sqrt /
+#   1 + cbrt for cases (5) / (2) / (1), or 18 + rsqrt, asin, sin for (3)/(4);
+# * Kawano's SZ: its thresholds (10 + 2 div; 16 + 2 div more where cases
+#   (3)-(5) are told apart), the closed forms, and for (3)/(4) Viete's root
+#   (12 + sqrt, div, acos, cos);
+# * Newton: the paper's printed step counts (7 in case (1), 4 per bracket in
+#   cases (3) and (4); case (4) first runs the case-(3) bracket), each step of
+#   the default mode 30 + div (the residual of Eq. 10, the bracket update and
+#   the convergence test; 13 + div in case (1));
+# * nested intervals: halvings until the bracket ends are adjacent
+#   (about 23 per bracket in FP32, 52 in FP64 for brackets of width ~0.3),
+#   24 each; case (4) first halves the case-(3) bracket.
+#
+# The FP32 paired kernels (optimised SZ, analytic) evaluate every case for
+# every cell; their counts here are the method's (case-weighted), so the
+# fraction against them measures how close the kernel comes to doing only the
+# method's work at the pipe's peak.
+FE, FE_L1 = 18, 4
+CLASSIFY = 14
+CLOSED = {5: (1, {}), 2: (3, {"sqrt": 1}), 1: (1, {"cbrt": 1})}
+POLISH = (22, {"div": 2})
+POLISH5 = (2, {})
+NEWTON_STEPS = {1: 7, 3: 4, 4: 8}
+NESTED_HALVINGS = {"fp32": 23, "fp64": 52}
+
+# fast FP32 forms of the calls: (FP32 operations, MUFU operations)
+FP32_CALL = {"div": (1, 1), "sqrt": (2, 1), "rsqrt": (0, 1), "cbrt": (6, 3), "sin": (1, 1),
+             "cos": (1, 1), "asin": (14, 1), "acos": (15, 1), "atan2": (18, 1)}
+
+
+def _add(a, b):
+    ops = a[0] + b[0]
+    calls = dict(a[1])
+    for k, v in b[1].items():
+        calls[k] = calls.get(k, 0) + v
+    return ops, calls
+
+
+def ops_per_case(method: str, prec: str):
+    """{case: (operations, {call: count})} for one cell of the given case
+    (1-5), method and precision ('fp32', 'fp32p', 'fp64')."""
+    out = {}
+    for c in (1, 2, 3, 4, 5):
+        base = (FE, {})
+        if method in ("sz_opt", "sz_orig"):
+            base = _add(base, (FE_L1, {"div": 1}))
+        if method == "sz_opt":
+            cost = (28, {})
+            cost = _add(cost, CLOSED[c] if c in CLOSED else (18, {"rsqrt": 1, "asin": 1, "sin": 1}))
+        elif method == "sz_orig":
+            cost = (10, {"div": 2})
+            if c in (3, 4, 5):
+                cost = _add(cost, (16, {"div": 2}))
+            cost = _add(cost, CLOSED[c] if c in CLOSED else
+                        (12, {"sqrt": 1, "div": 1, "acos": 1, "cos": 1}))
+        elif method == "analytic":
+            cost = (CLASSIFY, {})
+            if c in CLOSED:
+                cost = _add(cost, CLOSED[c])
+            else:
+                cost = _add(cost, (21, {"div": 1}))
+                cost = _add(cost, (11 if c == 3 else 15, {}))
+                cost = _add(cost, (10, {"cbrt": 1, "rsqrt": 1, "sqrt": 1, "atan2": 1, "sin": 1}))
+        elif method == "newton":
+            cost = (CLASSIFY, {})
+            if c in (5, 2):
+                cost = _add(cost, CLOSED[c])
+            elif c == 1:
+                cost = _add(cost, (13 * NEWTON_STEPS[1] + 4, {"div": NEWTON_STEPS[1] + 1}))
+            else:
+                cost = _add(cost, (30 * NEWTON_STEPS[c] + 4, {"div": NEWTON_STEPS[c] + 1}))
+        elif method == "nested":
+            cost = (CLASSIFY, {})
+            if c in CLOSED:
+                cost = _add(cost, CLOSED[c])
+            else:
+                h = NESTED_HALVINGS["fp64" if prec == "fp64" else "fp32"] * (1 if c == 3 else 2)
+                cost = _add(cost, (24 * h + 4, {"div": 1}))
+        else:
+            raise ValueError(method)
+        tot = _add(base, cost)
+        if prec == "fp32p":
+            tot = _add(tot, POLISH5 if c == 5 else POLISH)
+        out[c] = tot
+    return out
+
+
+def ops_weighted(method: str, prec: str, hist):
+    """Case-weighted counts: hist = {case: share}.  Returns (ops, calls)."""
+    pc = ops_per_case(method, prec)
+    ops = sum(hist.get(c, 0.0) * pc[c][0] for c in pc)
+    calls = {}
+    for c in pc:
+        for k, v in pc[c][1].items():
+            calls[k] = calls.get(k, 0.0) + hist.get(c, 0.0) * v
+    return ops, calls
+
+
+def fp32_pipes(method: str, prec: str, hist):
+    """(FP32 operations, MUFU operations) per cell for the FP32 kernels."""
+    ops, calls = ops_weighted(method, prec, hist)
+    fp, mufu = ops, 0.0
+    for k, v in calls.items():
+        f, m = FP32_CALL[k]
+        fp += v * f
+        mufu += v * m
+    return fp, mufu
+
+
+def fp64_equivalents(method: str, hist, call_cost):
+    """FP64-FMA equivalents per cell: the operations plus each library call
+    at its measured cost (``call_cost``: {call: FMA equivalents})."""
+    ops, calls = ops_weighted(method, "fp64", hist)
+    return ops + sum(v * call_cost[k] for k, v in calls.items())
+
+
+# ---------------------------------------------------------------------------
 # inputs
 # ---------------------------------------------------------------------------
-def make_cells_gpu(cells, seed, dtype, dev, vertex_frac=0.1, edge_frac=0.0):
-    """The 2^28-cell workload, generated chunkwise (seeded) straight into device
-    tensors.  Vertex cells get V0 from the GPU forward volume of their offset."""
+C2_EDGE, C2_BOUNDARY = 0.02, 0.1
+
+
+def make_cells_gpu(cells, seed, dtype, dev, edge_frac=C2_EDGE, boundary_frac=C2_BOUNDARY):
+    """The 2^28-cell throughput workload, generated chunkwise (seeded) straight
+    into device tensors: Gaussian unit normals, V0 ~ U[0,1], 2 % edge cases
+    and 10 % cells within 1e-6 (in V) of the case-(3)/(4)/(5) boundaries of
+    their normal, whose boundary volume comes from the GPU forward volume."""
     import torch
     from paper_2006_12838_gb300 import plic, synth
     out = [torch.empty(cells, dtype=dtype, device=dev) for _ in range(4)]
-    for start, c in synth.plic_cells_chunks(cells, seed, vertex_frac=vertex_frac,
-                                            edge_frac=edge_frac):
+    for start, c in synth.plic_cells_chunks(cells, seed, edge_frac=edge_frac,
+                                            boundary_frac=boundary_frac):
         k = c["V0"].size
         n = torch.from_numpy(c["n"]).to(dev, dtype)
         V0 = torch.from_numpy(c["V0"]).to(dev, dtype)
-        vm = torch.from_numpy(c["vertex"]).to(dev)
-        if bool(vm.any()):
-            d0v = torch.from_numpy(c["d0_vertex"]).to(dev, dtype)
-            Vv = plic.volume(n[0].contiguous(), n[1].contiguous(), n[2].contiguous(),
-                             torch.nan_to_num(d0v).contiguous())
-            V0 = torch.where(vm, Vv, V0)
+        bm = torch.from_numpy(c["boundary"]).to(dev)
+        if bool(bm.any()):
+            d0b = torch.from_numpy(np.nan_to_num(c["d0_boundary"])).to(dev, dtype)
+            Vb = plic.volume(n[0].contiguous(), n[1].contiguous(), n[2].contiguous(), d0b)
+            V = (Vb + torch.from_numpy(c["dV"]).to(dev, dtype)).clamp(0.0, 0.5)
+            Vm = torch.where(torch.from_numpy(c["mirror"]).to(dev), 1.0 - V, V)
+            V0 = torch.where(bm, Vm, V0)
         for j in range(3):
             out[j][start:start + k] = n[j]
         out[3][start:start + k] = V0
@@ -213,6 +360,106 @@ def frac(x, p):
     return None if x is None or p in (None, 0) else x / p
 
 
+def case_of(n, d0):
+    """Intersection case (Eq. 10) of each cell from its normal (3, m) and
+    offset: the reduced offset d = L/2 - |d0| against the sorted |n|
+    (a workload statistic for the op-count rooflines)."""
+    a = np.sort(np.abs(n), 0)
+    n1, n2, n3 = a
+    d = 0.5 * a.sum(0) - np.abs(d0)
+    c = np.full(d.size, 4, np.int64)
+    c[d <= np.minimum(n1 + n2, n3)] = 3
+    c[(d >= n1 + n2) & (d <= n3)] = 5
+    c[d <= n2] = 2
+    c[d < n1] = 1
+    return c
+
+
+def take_sample(t, d0, samples=1 << 17):
+    """Every k-th cell of a timed run: its float inputs and the kernel's d0
+    (numpy, FP64), and the case shares of the sample (classified on the
+    kernel's own offsets; a workload statistic)."""
+    import torch
+    n = t[0].numel()
+    step = max(1, n // samples)
+    sel = torch.arange(0, n, step, device=t[0].device)[:samples]
+    f = lambda x: x[sel].double().cpu().numpy()  # noqa: E731
+    smp = {"n": np.stack([f(t[0]), f(t[1]), f(t[2])]), "V0": f(t[3]), "d0": f(d0),
+           "what": "every %d-th cell of the timed output" % step}
+    ok = ~np.isnan(smp["d0"])
+    cases = case_of(smp["n"][:, ok], smp["d0"][ok])
+    smp["case_share"] = {int(c): float(np.mean(cases == c)) for c in (1, 2, 3, 4, 5)}
+    return smp
+
+
+def oracle_errors(smp):
+    """|d0 - d0_ref| of a sample against the FP64 oracle on the same inputs
+    (CPU leg)."""
+    import oracle
+    ref = oracle.offset(smp["n"][0], smp["n"][1], smp["n"][2], smp["V0"])
+    nan = np.isnan(smp["d0"])
+    err = np.abs(smp["d0"] - ref)[~nan]
+    return {"cells": int(ref.size), "sample": smp["what"], "d0_err_max": float(err.max()),
+            "d0_err_p999": float(np.percentile(err, 99.9)), "d0_err_mean": float(err.mean()),
+            "nan": int(nan.sum()), "nan_ref": int(np.isnan(ref).sum())}
+
+
+def measure_peaks(dev):
+    """Pipe rates from the library's probes (CUDA events around one launch,
+    best of three), with the SM clock sampled meanwhile.  FP64 library calls
+    are also given as FP64-FMA equivalents (FMA rate / call rate, minus the
+    one add or multiply each probe adds)."""
+    import torch
+    from paper_2006_12838_gb300 import plic
+    sink = torch.zeros(1, device=dev)
+    s = torch.cuda.current_stream()
+    rates = {}
+    with ClockSampler(dev.index or 0) as clk:
+        for kind in plic.PROBES:
+            iters = 512 if kind.startswith("d_") else (4096 if kind == "dfma" else 16384)
+            plic.pipe_probe(kind, 16, sink)
+            best = float("inf")
+            for _ in range(3):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                ops = plic.pipe_probe(kind, iters, sink)
+                b.record(s)
+                torch.cuda.synchronize()
+                best = min(best, a.elapsed_time(b) / 1e3)
+            rates[kind] = ops / best
+    extra = {"d_sqrt": 1, "d_div": 1, "d_cbrt": 1, "d_asin": 1, "d_acos": 1}
+    cost = {k[2:]: rates["dfma"] / rates[k] - extra.get(k, 0) for k in rates if k.startswith("d_")}
+    cost["rsqrt"] = cost["sqrt"]
+    return {"fp32_tops": max(rates["ffma"], rates["ffma2"]) / 1e12,
+            "ffma_tops": rates["ffma"] / 1e12, "ffma2_tops": rates["ffma2"] / 1e12,
+            "dfma_tops": rates["dfma"] / 1e12,
+            "mufu_tops": max(rates["mufu_sin"], rates["mufu_rsqrt"]) / 1e12,
+            "mufu_rates_tops": {k: rates[k] / 1e12 for k in ("mufu_ex2_lg2", "mufu_rsqrt", "mufu_sin")},
+            "fp64_call_fma_equiv": {k: round(v, 2) for k, v in cost.items()},
+            "clocks": clk.summary(),
+            "how": "plic_pipe_probe: one wave of 256-thread blocks, 8 independent chains per "
+                   "thread, CUDA events, best of 3"}
+
+
+def op_roofline(sec_per_cell, bytes_per_cell, pk, pp, fp32=0.0, mufu=0.0, fp64=0.0):
+    """Fraction of the roofline set by the slowest of bytes at HBM peak and
+    the operations at their pipes' measured peaks (per cell)."""
+    t = {"hbm": bytes_per_cell / (pk["hbm_gbs"] * 1e9)}
+    if pp:
+        if fp32:
+            t["fp32"] = fp32 / (pp["fp32_tops"] * 1e12)
+        if mufu:
+            t["mufu"] = mufu / (pp["mufu_tops"] * 1e12)
+        if fp64:
+            t["fp64"] = fp64 / (pp["dfma_tops"] * 1e12)
+    bound = max(t, key=t.get)
+    return {"bound": bound, "frac": t[bound] / sec_per_cell,
+            "roof_g_cells_s": 1e-9 / t[bound],
+            "ops_per_cell": {k: round(v, 1) for k, v in (("fp32", fp32), ("mufu", mufu),
+                                                         ("fp64_fma_equiv", fp64)) if v}}
+
+
 # Curvature roofline (bound "alu"): the FP32 arithmetic of the method per
 # interface cell with m interface neighbours (PY normal, SZ-opt solves with the
 # per-normal constants computed once per cell, foot points, 5x5 LDL^T), an FMA,
@@ -231,9 +478,14 @@ CURV_XU_CELL, CURV_XU_SOLVE = 20, 6
 N_SM, FP32_PER_SM, XU_PER_SM = 152, 128, 16
 
 
-def curvature_roofline(cells_per_s, m_mean, pk):
+def curvature_roofline(cells_per_s, m_mean, pk, pp=None):
     clk = float(pk.get("sm_max_mhz") or 2070.0) * 1e6
-    fp_peak, xu_peak = N_SM * FP32_PER_SM * clk, N_SM * XU_PER_SM * clk
+    if pp:
+        fp_peak, xu_peak = pp["fp32_tops"] * 1e12, pp["mufu_tops"] * 1e12
+        src = "measured (plic_pipe_probe: FP32 FMA and MUFU rates)"
+    else:
+        fp_peak, xu_peak = N_SM * FP32_PER_SM * clk, N_SM * XU_PER_SM * clk
+        src = "152 SMs x 128 FP32 / 16 MUFU lanes x %.0f MHz (sm_max_mhz)" % (clk / 1e6)
     fp = CURV_FP_CELL + CURV_FP_SOLVE * (m_mean + 1) + CURV_FP_NEIGHBOUR * m_mean
     xu = CURV_XU_CELL + CURV_XU_SOLVE * (m_mean + 1)
     roof = 1.0 / max(fp / fp_peak, xu / xu_peak)          # cells/s at the busier pipe's peak
@@ -241,8 +493,7 @@ def curvature_roofline(cells_per_s, m_mean, pk):
             "achieved": cells_per_s * fp / 1e12, "peak": fp_peak / 1e12, "unit": "T FP32 op/s",
             "frac": cells_per_s / roof, "fp32_ops_per_cell": round(fp, 1),
             "mufu_ops_per_cell": round(xu, 1), "mean_interface_neighbours": round(m_mean, 3),
-            "roof_g_cells_s": roof / 1e9,
-            "peak_src": "152 SMs x 128 FP32 lanes x %.0f MHz (sm_max_mhz)" % (clk / 1e6)}
+            "roof_g_cells_s": roof / 1e9, "peak_src": src}
 
 
 def mean_interface_neighbours(fields):
@@ -268,7 +519,7 @@ def mean_interface_neighbours(fields):
 # ---------------------------------------------------------------------------
 # sections (each returns a dict)
 # ---------------------------------------------------------------------------
-def section_solvers(t32, dev, pk, steps):
+def section_solvers(t32, dev, pk, steps, hist=None, pp=None):
     import torch
     from paper_2006_12838_gb300 import plic
     s = torch.cuda.current_stream()
@@ -279,9 +530,12 @@ def section_solvers(t32, dev, pk, steps):
         for prec in ("fp32p", "fp32"):
             sec = timed(lambda: plic.offset(*t32, method=m, precision=prec, out=d0), steps, 2, s)
             gbs = 20.0 * n * steps / sec / 1e9
-            out["offset_%s_%s" % (m, prec)] = {"g_solves_s": n * steps / sec / 1e9,
-                                              "ms": sec / steps * 1e3, "hbm_gbs": gbs,
-                                              "hbm_frac": frac(gbs, pk["hbm_gbs"])}
+            r = {"g_solves_s": n * steps / sec / 1e9, "ms": sec / steps * 1e3, "hbm_gbs": gbs,
+                 "hbm_frac": frac(gbs, pk["hbm_gbs"])}
+            if hist:
+                fp, mu = fp32_pipes(m, prec, hist)
+                r["roofline"] = op_roofline(sec / steps / n, 20.0, pk, pp, fp32=fp, mufu=mu)
+            out["offset_%s_%s" % (m, prec)] = r
     sec = timed(lambda: plic.volume(*t32[:3], t32[3], out=d0), steps, 2, s)
     gbs = 20.0 * n * steps / sec / 1e9
     out["volume_fp32"] = {"g_cells_s": n * steps / sec / 1e9, "ms": sec / steps * 1e3,
@@ -298,7 +552,14 @@ def section_solvers(t32, dev, pk, steps):
     return out
 
 
-def section_fp64(dev, pk, steps, cells):
+# FP64_REFINED adds to the FP32-polished solve two Newton steps on Eq. 10 in
+# double-float arithmetic (about 8 double-float products at ~10 FP32
+# operations and 8 sums at ~15 per step) and the integer front end on the
+# doubles' bits (~60): an estimate of 460 FP32/ALU operations per cell.
+REFINE_FP32 = 460
+
+
+def section_fp64(dev, pk, steps, cells, hist=None, pp=None, samples=None):
     import torch
     from paper_2006_12838_gb300 import plic
     t64 = make_cells_gpu(cells, 2, torch.float64, dev)
@@ -309,9 +570,21 @@ def section_fp64(dev, pk, steps, cells):
         for prec in ("fp64", "fp64r"):
             sec = timed(lambda: plic.offset(*t64, method=m, precision=prec, out=d0), steps, 1, s)
             gbs = 40.0 * cells * steps / sec / 1e9
-            out["offset_%s_%s" % (m, prec)] = {"g_solves_s": cells * steps / sec / 1e9,
-                                               "ms": sec / steps * 1e3, "hbm_gbs": gbs,
-                                               "hbm_frac": frac(gbs, pk["hbm_gbs"]), "cells": cells}
+            r = {"g_solves_s": cells * steps / sec / 1e9, "ms": sec / steps * 1e3, "hbm_gbs": gbs,
+                 "hbm_frac": frac(gbs, pk["hbm_gbs"]), "cells": cells}
+            if hist and pp:
+                spc = sec / steps / cells
+                if prec == "fp64":
+                    eq = fp64_equivalents(m, hist, pp["fp64_call_fma_equiv"])
+                    r["roofline"] = op_roofline(spc, 40.0, pk, pp, fp64=eq)
+                else:
+                    fp, mu = fp32_pipes(m, "fp32p", hist)
+                    r["roofline"] = op_roofline(spc, 40.0, pk, pp, fp32=fp + REFINE_FP32, mufu=mu)
+            out["offset_%s_%s" % (m, prec)] = r
+        if m == "sz_opt" and samples is not None:
+            for prec in ("fp64", "fp64r"):
+                smp = take_sample(t64, plic.offset(*t64, method=m, precision=prec, out=d0), 1 << 15)
+                samples["sz_opt_" + prec] = smp
     del t64
     torch.cuda.empty_cache()
     return out
@@ -340,7 +613,27 @@ def section_adjoint(t32, dev, pk, steps):
                                      "cells": n}}
 
 
-def section_curvature(dev, pk, steps):
+def timed_cold(fn, steps, stream, flush):
+    """Device time of fn() with L2 cold: before each call a 512 MiB buffer
+    (four times the L2) is written, then fn() runs between CUDA events.  The
+    flush keeps the GPU busy while the host queues the call, so the events
+    bracket the kernels alone.  Returns mean seconds per call."""
+    import torch
+    fn()
+    tot = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b) / 1e3
+    return tot / steps
+
+
+def section_curvature(dev, pk, steps, pp=None):
     import torch
     from paper_2006_12838_gb300 import plic, synth
     phi, _ = synth.curvature_field(seed=3, edge=256, device=dev)
@@ -351,20 +644,30 @@ def section_curvature(dev, pk, steps):
     s = torch.cuda.current_stream()
     ws = torch.empty(plic.workspace_bytes(plic.WS_COMPACT, phi.numel()), dtype=torch.uint8, device=dev)
     cnt2 = torch.empty(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(128 << 20, device=dev)
     out = {"interface_cells": k, "field": "256^3 f32, 8 spheres R~U[6,40]",
-           "timing": "CUDA graph of the timed calls (device time, no per-call Python time)"}
-    sec, how = timed_graph(lambda: plic.interface_compact(phi, idx=idx, count=cnt2, workspace=ws), steps, 3, s)
+           "timing": "warm: CUDA graph of the timed calls (device time, no per-call Python time); "
+                     "cold: 512 MiB written before each call, CUDA events around the call"}
+    compact = lambda: plic.interface_compact(phi, idx=idx, count=cnt2, workspace=ws)  # noqa: E731
+    sec, how = timed_graph(compact, steps, 3, s)
     out["timing_mode"] = how
-    out["compact"] = {"ms": sec / steps * 1e3,
-                      "hbm_gbs": (phi.numel() * 4 + k * 4) * steps / sec / 1e9}
+    cbytes = phi.numel() * 4 + k * 4
+    out["compact"] = {"ms": sec / steps * 1e3, "hbm_gbs": cbytes * steps / sec / 1e9,
+                      "hbm_frac": frac(cbytes * steps / sec / 1e9, pk["hbm_gbs"])}
+    secc = timed_cold(compact, steps, s, flush)
+    out["compact_cold"] = {"ms": secc * 1e3, "hbm_gbs": cbytes / secc / 1e9,
+                           "hbm_frac": frac(cbytes / secc / 1e9, pk["hbm_gbs"])}
     m_mean = mean_interface_neighbours([(phi, it, k)])
     for fit, name in FITS:
         sec, _ = timed_graph(lambda: plic.curvature(phi, it, kappa=kap, flags=fit), steps, 3, s)
         out["curvature_sz_opt_" + name] = {"ms": sec / steps * 1e3,
                                             "m_cells_s": k * steps / sec / 1e6}
         if fit == 0:
-            out["roofline"] = curvature_roofline(k * steps / sec, m_mean, pk)
+            out["roofline"] = curvature_roofline(k * steps / sec, m_mean, pk, pp)
             out["roofline"]["of"] = "curvature_sz_opt_auto"
+    secc = timed_cold(lambda: plic.curvature(phi, it, kappa=kap), steps, s, flush)
+    out["curvature_cold"] = {"ms": secc * 1e3, "m_cells_s": k / secc / 1e6,
+                             "frac": curvature_roofline(k / secc, m_mean, pk, pp)["frac"]}
     for m in plic.METHODS:
         if m == "sz_opt":
             continue                                  # the default: timed above
@@ -388,6 +691,24 @@ def section_curvature(dev, pk, steps):
         plic.curvature(phi, idx, n_iface=k, count=cnt2, kappa=kap)
     sec, _ = timed_graph(pipeline, steps, 3, s)
     out["compact_plus_curvature"] = {"ms": sec / steps * 1e3, "m_cells_s": k * steps / sec / 1e6}
+    secc = timed_cold(pipeline, steps, s, flush)
+    out["compact_plus_curvature_cold"] = {"ms": secc * 1e3, "m_cells_s": k / secc / 1e6}
+    del ws, idx
+    # compaction of a field larger than L2: the 256^3 field tiled to 512 x 512 x 1024 (1 GiB)
+    big = phi.repeat(2, 2, 4)
+    kb_max = 16 * k + (1 << 20)
+    idxb = torch.empty(kb_max, dtype=torch.int32, device=dev)
+    wsb = torch.empty(plic.workspace_bytes(plic.WS_COMPACT, big.numel()), dtype=torch.uint8, device=dev)
+    cb = lambda: plic.interface_compact(big, idx=idxb, count=cnt2, workspace=wsb)  # noqa: E731
+    cb()
+    kb = int(cnt2.item())
+    secb = timed(cb, steps, 2, s) / steps
+    bb = big.numel() * 4 + kb * 4
+    out["compact_1GiB"] = {"field": "512 x 512 x 1024 (the 256^3 field tiled)", "interface_cells": kb,
+                           "ms": secb * 1e3, "hbm_gbs": bb / secb / 1e9,
+                           "hbm_frac": frac(bb / secb / 1e9, pk["hbm_gbs"])}
+    del big, idxb, wsb, flush
+    torch.cuda.empty_cache()
     return out
 
 
@@ -439,7 +760,7 @@ def section_curvature_adjoint(dev, pk, steps):
     return out
 
 
-def section_batched(dev, pk, steps):
+def section_batched(dev, pk, steps, pp=None):
     import torch
     from paper_2006_12838_gb300 import plic, synth
     fields = synth.batched_fields(seed=5, n_fields=64, device=dev)
@@ -466,7 +787,7 @@ def section_batched(dev, pk, steps):
         sec = timed(lambda: plic.curvature_batched(batch, flags=fit, tuning=shape), steps, 2, s)
         out["batched_" + name] = {"ms": sec / steps * 1e3, "m_cells_s": tot * steps / sec / 1e6}
         if fit == 0:
-            out["roofline"] = curvature_roofline(tot * steps / sec, m_mean, pk)
+            out["roofline"] = curvature_roofline(tot * steps / sec, m_mean, pk, pp)
             out["roofline"]["of"] = "batched_auto"
     # the other layout at its best tuning, for comparison
     if times:
@@ -518,19 +839,20 @@ def section_paper(dev, pk, steps, normals=1 << 26, normals64=1 << 20, L=256):
 # ---------------------------------------------------------------------------
 def oracle_sample(cells, seed=2):
     """A bounded sample of the headline workload for the CPU oracle: the
-    first `cells` cells of the same seeded chunk stream, with vertex-cell V0
-    from the oracle's own forward volume."""
+    first `cells` cells of the same seeded chunk stream, with the boundary
+    cells' V0 from the oracle's own forward volume."""
     import oracle
     from paper_2006_12838_gb300 import synth
     nx, ny, nz, V0 = [], [], [], []
     got = 0
-    for _, c in synth.plic_cells_chunks(CELLS, seed, vertex_frac=0.1):
+    for _, c in synth.plic_cells_chunks(CELLS, seed, edge_frac=C2_EDGE, boundary_frac=C2_BOUNDARY):
         n = c["n"].astype(np.float32).astype(np.float64)
         v = c["V0"].copy()
-        vm = c["vertex"]
-        if vm.any():
-            v[vm] = oracle.volume(n[0][vm], n[1][vm], n[2][vm],
-                                  c["d0_vertex"][vm].astype(np.float32).astype(np.float64))
+        bm = c["boundary"]
+        if bm.any():
+            d0b = c["d0_boundary"][bm].astype(np.float32).astype(np.float64)
+            Vb = oracle.volume(n[0][bm], n[1][bm], n[2][bm], d0b)
+            v[bm] = synth.boundary_fill(Vb, c["dV"][bm], c["mirror"][bm])
         v = v.astype(np.float32).astype(np.float64)
         take = min(cells - got, v.size)
         nx.append(n[0][:take]); ny.append(n[1][:take]); nz.append(n[2][:take]); V0.append(v[:take])
@@ -549,7 +871,8 @@ def oracle_step(sample):
 def headline_config():
     return {"workload": "plic_offset_roundtrip: sz_opt offset (fp32 + 1 Newton polish) "
                         "and the forward volume of the result, one fused kernel, "
-                        "2^28 SoA f32 cells per GPU, 10% within 1e-6 of a cube vertex",
+                        "2^28 SoA f32 cells per GPU: Gaussian unit normals, V0~U[0,1], "
+                        "2% edge cases, 10% within 1e-6 in V of a case-(3)/(4)/(5) boundary",
             "cells_per_gpu": CELLS, "method": "sz_opt", "precision": "fp32_polished",
             "l2": "inputs 4 GiB per step > 129 MB L2 (no flush needed)"}
 
@@ -578,6 +901,14 @@ def cpu_baseline(cells=1 << 24, cells_1core=1 << 20):
     t0 = time.perf_counter()
     oracle.curvature(p, idx)
     secc = time.perf_counter() - t0
+    # the batched workload on 4 of its 64 fields (the first four of the seeded set)
+    fields = synth.batched_fields(seed=5, n_fields=64)[:4]
+    lists = [(f.numpy(), oracle.interface_cells(f.numpy())) for f, _ in fields]
+    t0 = time.perf_counter()
+    for q, ii in lists:
+        oracle.curvature(q, ii)
+    sec5 = time.perf_counter() - t0
+    k5 = sum(int(ii.size) for _, ii in lists)
     return {"value": cells / sec / 1e9, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": "first %d cells of the 2^28-cell workload (same seeded stream), FP64 bisection "
@@ -585,7 +916,10 @@ def cpu_baseline(cells=1 << 24, cells_1core=1 << 20):
             "seconds": sec,
             "value_1core": cells_1core / sec1 / 1e9, "sample_1core": "first %d cells, 1 thread" % cells_1core,
             "curvature_256_cells_s": idx.size / secc, "curvature_256_seconds": secc,
-            "curvature_256_interface_cells": int(idx.size)}
+            "curvature_256_interface_cells": int(idx.size),
+            "batched_4_of_64_fields_cells_s": k5 / sec5, "batched_4_fields_seconds": sec5,
+            "batched_4_fields_interface_cells": k5,
+            "batched_4_fields_edges": [int(f.shape[0]) for f, _ in fields]}
 
 
 def run_reference(args):
@@ -667,6 +1001,42 @@ def run_case(args):
     print("case %s done" % args.case)
 
 
+def summary(line, sec):
+    """The figures the line is read for, compact and last in the line (so that
+    a record keeping only the end of the output still holds them)."""
+    def g(d, *path):
+        for p in path:
+            if not isinstance(d, dict) or p not in d:
+                return None
+            d = d[p]
+        return round(d, 4) if isinstance(d, float) else d
+    out = {"step_g_solves_s": g(line, "value"), "step_hbm_frac": g(line, "roofline", "frac"),
+           "e2e_g_solves_s": g(line, "e2e", "value")}
+    acc = line.get("accuracy", {}).get("vs_oracle_sz_opt_fp32p", {})
+    out["d0_err_max"] = acc.get("d0_err_max")
+    out["d0_err_p999"] = acc.get("d0_err_p999")
+    c = sec.get("curvature_256", {})
+    out["curv256_m_cells_s"] = g(c, "curvature_sz_opt_auto", "m_cells_s")
+    out["curv256_frac"] = g(c, "roofline", "frac")
+    out["curv256_cold_us"] = None if g(c, "curvature_cold", "ms") is None else round(c["curvature_cold"]["ms"] * 1e3, 2)
+    out["compact256_cold_hbm_frac"] = g(c, "compact_cold", "hbm_frac")
+    out["compact1GiB_hbm_frac"] = g(c, "compact_1GiB", "hbm_frac")
+    out["compact_plus_curv_cold_us"] = (None if g(c, "compact_plus_curvature_cold", "ms") is None
+                                        else round(c["compact_plus_curvature_cold"]["ms"] * 1e3, 2))
+    bt = sec.get("batched_64_fields", {})
+    out["batched64_m_cells_s"] = g(bt, "batched_auto", "m_cells_s")
+    out["batched64_frac"] = g(bt, "roofline", "frac")
+    for m in ("sz_opt", "analytic", "sz_orig", "newton", "nested"):
+        for p in ("fp32p", "fp64", "fp64r"):
+            r = sec.get("offset_%s_%s" % (m, p), {})
+            if r:
+                out["%s_%s" % (m, p)] = [g(r, "g_solves_s"), g(r, "roofline", "frac"),
+                                         g(r, "roofline", "bound")]
+    pp = line.get("peaks") or {}
+    out["peaks_tops"] = {k: g(pp, k) for k in ("fp32_tops", "dfma_tops", "mufu_tops")}
+    return out
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -741,10 +1111,13 @@ def main():
     D.barrier()
     kern_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
     value = D.weak_scaling_value(CELLS, world, args.steps, sec) / 1e9
-    # accuracy of the timed result: round trip on a sample of the output
+    # accuracy of the timed result: round trip on every output, and a sample of
+    # the output kept for the CPU leg's comparison with the oracle
     rt = (Vrt - t32[3]).abs()
     rt_max = float(rt.max().item())
     rt_mean = float(rt.double().mean().item())
+    samples = {"sz_opt_fp32p": take_sample(t32, d0)}
+    hist = samples["sz_opt_fp32p"]["case_share"]
 
     # e2e: same step through the ABI from pinned host buffers (H2D + D2H in the timed region).
     # Two ways: zero copy (the kernel reads the pinned host arrays and writes the
@@ -839,21 +1212,25 @@ def main():
             "roofline": roof, "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
-            "accuracy": {"roundtrip_max": rt_max, "roundtrip_mean": rt_mean}}
+            "accuracy": {"roundtrip_max": rt_max, "roundtrip_mean": rt_mean,
+                         "case_share": hist}}
 
+    sec_out = {}
+    pp = None
     if rank == 0 and world == 1 and not args.no_sections:
         steps = 3 if args.quick else 5
-        sec_out = {}
         try:
-            sec_out.update(section_solvers(t32, dev, pk, steps))
+            pp = measure_peaks(dev)
+            line["peaks"] = pp
+            sec_out.update(section_solvers(t32, dev, pk, steps, hist, pp))
             sec_out.update(section_adjoint(t32, dev, pk, steps))
             del t32, d0, Vrt
             torch.cuda.empty_cache()
-            sec_out.update(section_fp64(dev, pk, 2 if args.quick else 3, CELLS))
+            sec_out.update(section_fp64(dev, pk, 2 if args.quick else 3, CELLS, hist, pp, samples))
             sec_out["sphere"] = section_sphere(dev, pk, steps)
-            sec_out["curvature_256"] = section_curvature(dev, pk, steps)
+            sec_out["curvature_256"] = section_curvature(dev, pk, steps, pp)
             sec_out["curvature_adjoint_128"] = section_curvature_adjoint(dev, pk, steps)
-            sec_out["batched_64_fields"] = section_batched(dev, pk, steps)
+            sec_out["batched_64_fields"] = section_batched(dev, pk, steps, pp)
             sec_out["paper_harness"] = section_paper(dev, pk, 2)
         except Exception as ex:
             sec_out["error"] = repr(ex)[:300]
@@ -863,7 +1240,13 @@ def main():
             line["cpu_baseline"] = cpu_baseline()
         except Exception as ex:
             line["cpu_baseline"] = {"value": None, "error": repr(ex)[:200]}
+        try:
+            for key, smp in samples.items():
+                line["accuracy"]["vs_oracle_" + key] = oracle_errors(smp)
+        except Exception as ex:
+            line["accuracy"]["error"] = repr(ex)[:200]
     if rank == 0:
+        line["summary"] = summary(line, sec_out)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -364,6 +364,21 @@ int plic_abi_version(void);
  * only (cudaPointerGetAttributes); no launch, no synchronisation. */
 plic_status plic_host_device_pointer(const void *host_ptr, void **dev_ptr);
 
+/* plic_pipe_probe -- a throughput probe of one execution pipe, for the
+ * compute side of the kernels' rooflines (the paper has no counterpart).
+ * kind: 0 FP32 FMA, 1 paired FP32 FMA (FFMA2, two operations), 2 FP64 FMA,
+ * 3 MUFU ex2 + lg2 (two operations), 4 MUFU rsqrt, 5 MUFU sin; FP64 library
+ * calls: 6 sqrt(x+1), 7 1/(x+1), 8 cbrt(x+1) (each with one FP64 add),
+ * 9 sin, 10 cos, 11 asin(x/2), 12 acos(x/2) (each with one FP64 multiply),
+ * 13 atan2.  Launches one wave of resident blocks on `stream`, every thread
+ * running 8 independent chains of `iters` operations; *ops (host) receives
+ * the number of operations (or calls) the launch performs, so that the
+ * caller's CUDA-event time of the launch gives the rate.  d_sink: a device
+ * float that is written only in the impossible event that keeps the chains
+ * alive.  Errors: PLIC_ERR_ARG (unknown kind, iters < 1, null pointers),
+ * PLIC_ERR_ALIGN, PLIC_ERR_CUDA. */
+plic_status plic_pipe_probe(int kind, int iters, float *d_sink, int64_t *ops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ def load():
             "plic_sphere_volume": [P, P, I64, I32, P],
             "plic_offset_roundtrip": [P, P, P, P, P, P, I64, I32, I32, U32, P, P],
             "plic_sphere_offset": [P, P, I64, I32, P],
+            "plic_pipe_probe": [I32, I32, P, ctypes.POINTER(I64), P],
         }
         for name, args in sigs.items():
             f = getattr(L, name, None)
@@ -419,3 +420,20 @@ def sphere_offset(V0, precision=None, out=None, stream=None):
     _check(load().plic_sphere_offset(_ptr(V0), _ptr(out), V0.numel(), p, _stream(V0, stream)),
            "plic_sphere_offset")
     return out
+
+
+PROBES = {"ffma": 0, "ffma2": 1, "dfma": 2, "mufu_ex2_lg2": 3, "mufu_rsqrt": 4, "mufu_sin": 5,
+          "d_sqrt": 6, "d_div": 7, "d_cbrt": 8, "d_sin": 9, "d_cos": 10, "d_asin": 11,
+          "d_acos": 12, "d_atan2": 13}
+
+
+def pipe_probe(kind, iters, sink, stream=None) -> int:
+    """Launch the pipe-throughput probe ``kind`` (a key of PROBES) on the
+    current device; returns the number of operations (or calls) the launch
+    performs.  ``sink``: a CUDA float tensor of at least one element."""
+    L = load()
+    _cuda(sink, dtype=torch.float32)
+    ops = ctypes.c_int64(0)
+    _check(L.plic_pipe_probe(PROBES[kind], int(iters), _ptr(sink), ctypes.byref(ops),
+                             _stream(sink, stream)), "plic_pipe_probe")
+    return int(ops.value)

@@ -92,7 +92,7 @@ def edge_case_cells(rng: np.random.Generator, m: int):
 
 
 def plic_cells(m: int, seed, edge_frac: float = 0.0, vertex_frac: float = 0.0,
-               vertex_eps: float = 1e-6):
+               vertex_eps: float = 1e-6, boundary_frac: float = 0.0, boundary_eps: float = 1e-6):
     """Normals and fill fractions for m PLIC cells (FP64 numpy arrays).
 
     Returns dict(n=(3, m) [rows nx, ny, nz], V0=(m,), vertex=(m,) bool,
@@ -101,7 +101,20 @@ def plic_cells(m: int, seed, edge_frac: float = 0.0, vertex_frac: float = 0.0,
     than the two extreme vertices where V0 is 0 or 1); the caller computes
     V0 = V0(n, d0_vertex) with its own forward volume.  Edge cases occupy the
     last ``edge_frac`` share; each other cell is a vertex cell with probability
-    ``vertex_frac``."""
+    ``vertex_frac``.
+
+    ``boundary`` cells (probability ``boundary_frac`` among the cells that are
+    neither edge nor vertex cells) sit at the boundaries of cases (3), (4) and
+    (5) in V rather than in d: with the components of |n| sorted,
+    n1 <= n2 <= n3, the plane through the cube corner at the far end of the
+    n2 axis ends case (2) and starts case (3); the one at the end of the n3
+    axis ends case (3) and starts case (4) when n3 < n1 + n2, else the plane
+    through the corner n1 + n2 ends case (3) and starts case (5).  One of the
+    two boundaries is drawn with probability 1/2; ``d0_boundary`` is that
+    plane's offset, ``dV`` ~ U[-boundary_eps, boundary_eps] and ``mirror`` a
+    fair coin.  The caller forms V = V0(n, d0_boundary) with its own forward
+    volume, then V0 = clip(V + dV, 0, 1/2), mirrored to 1 - V0 where
+    ``mirror`` is set; V0 of these cells is NaN here."""
     rng = np.random.default_rng(seed)
     n = gaussian_normals(rng, m)
     V0 = rng.random(m)
@@ -125,7 +138,43 @@ def plic_cells(m: int, seed, edge_frac: float = 0.0, vertex_frac: float = 0.0,
         s = sgn_n * (1.0 - 2.0 * flips)
         d0v[pick] = 0.5 * (npk * s).sum(0) + rng.uniform(-vertex_eps, vertex_eps, k)
         V0[pick] = np.nan
-    return {"n": n, "V0": V0, "vertex": vertex, "d0_vertex": d0v}
+    boundary = np.zeros(m, bool)
+    d0b = np.full(m, np.nan)
+    dV = np.zeros(m)
+    mirror = np.zeros(m, bool)
+    if boundary_frac > 0:
+        pool = m - m_edge
+        boundary[:pool] = (~vertex[:pool]) & (rng.random(pool) < boundary_frac)
+        pick = np.flatnonzero(boundary)
+        k = pick.size
+        a = np.abs(n[:, pick])
+        order = np.argsort(a, axis=0, kind="stable")        # axes of n1, n2, n3
+        srt = np.take_along_axis(a, order, 0)
+        cols = np.arange(k)
+        # vertex offsets from the corner -sign(n)/2 (where V0 = 0): a corner
+        # reached by moving along the chosen axes
+        upper = rng.random(k) < 0.5
+        tall = srt[2] >= srt[0] + srt[1]
+        move = np.zeros((3, k), bool)
+        move[order[1], cols] = ~upper                        # case (2)/(3): the n2 axis
+        move[order[2], cols] = upper & ~tall                 # case (3)/(4): the n3 axis
+        move[order[0], cols] |= upper & tall                 # case (3)/(5): n1 and n2
+        move[order[1], cols] |= upper & tall
+        sgn = np.where(n[:, pick] >= 0, 1.0, -1.0)
+        x = -0.5 * sgn + np.where(move, sgn, 0.0)
+        d0b[pick] = (n[:, pick] * x).sum(0)
+        dV[pick] = rng.uniform(-boundary_eps, boundary_eps, k)
+        mirror[pick] = rng.random(k) < 0.5
+        V0[pick] = np.nan
+    return {"n": n, "V0": V0, "vertex": vertex, "d0_vertex": d0v,
+            "boundary": boundary, "d0_boundary": d0b, "dV": dV, "mirror": mirror}
+
+
+def boundary_fill(Vb, dV, mirror):
+    """V0 of boundary cells from the forward volume Vb of their plane
+    (see :func:`plic_cells`): clip(Vb + dV, 0, 1/2), mirrored where asked."""
+    V = np.clip(Vb + dV, 0.0, 0.5)
+    return np.where(mirror, 1.0 - V, V)
 
 
 def plic_cells_chunks(m: int, seed: int, chunk: int = 1 << 22, **kw):

@@ -44,7 +44,7 @@ def test_every_declared_symbol_is_exported(lib):
 # entry points with no counterpart in the paper (sizes, status text, version,
 # host-memory addressing)
 PLUMBING = {"plic_workspace_bytes", "plic_curv_bwd_workspace_bytes", "plic_status_string",
-            "plic_last_error", "plic_abi_version", "plic_host_device_pointer"}
+            "plic_last_error", "plic_abi_version", "plic_host_device_pointer", "plic_pipe_probe"}
 
 
 # deployment variants of a compute entry: no passage of the paper defines

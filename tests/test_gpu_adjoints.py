@@ -9,9 +9,11 @@ Finite-difference step: the stated step of 1e-4 is in its asymptotic range
 only away from the clamp -- near fills of 2e-4 the offset d0 ~ V^(1/3) bends
 so fast that central differences with h = 1e-4 are off by ~5 % in norm on this
 field (h = 1e-5: 4e-4; h = 1e-6 and 1e-7 agree to 4e-6).  The oracle is FP64,
-so the gate uses h = 1e-6 and h = 1e-7 (entries where these two disagree by
-more than 1e-4 of the gradient scale are left out and counted); the h = 1e-4
-difference is printed beside it.
+so the gate uses h = 1e-6 and h = 1e-7, per entry: where the two agree to
+1e-4 of the gradient scale the GPU entry must match to 1e-3 relative (with a
+floor of 1e-2 of the scale); where they disagree (counted and bounded) it must
+lie between them, widened by the same tolerance.  The h = 1e-4 difference is
+printed beside it.
 """
 import numpy as np
 import pytest
@@ -33,21 +35,33 @@ def dev():
     return torch.device("cuda:0")
 
 
-def _compare(g_gpu, g1, g2, label, tol_rel=1e-3, g_coarse=None):
+def _compare(g_gpu, g1, g2, label, tol_rel=1e-3, g_coarse=None, max_unconverged=0.01):
+    """Per-entry gate: every entry where the two FD steps agree (FD converged)
+    must satisfy |g_gpu - g_fd| <= tol_rel max(|g_fd|, 1e-2 max|g_fd|); the
+    entries where they disagree are counted and bounded (a share of the
+    non-zero entries), and on them the GPU value must lie within the spread
+    of the two FD values widened by the same tolerance."""
     scale = np.abs(g1).max()
-    ok = np.abs(g1 - g2) <= 1e-4 * scale          # FD converged here
-    err = np.abs(g_gpu - g1)
-    nz = np.abs(g1) > 0
-    glob = np.linalg.norm((g_gpu - g1)[ok]) / np.linalg.norm(g1[ok])
-    rel = err[ok & nz] / np.maximum(np.abs(g1[ok & nz]), 1e-2 * scale)
+    conv = np.abs(g1 - g2) <= 1e-4 * scale          # FD converged here
+    nz = (np.abs(g1) > 0) | (np.abs(g2) > 0)
+    floor = np.maximum(np.abs(g1), 1e-2 * scale)
+    rel = np.abs(g_gpu - g1) / floor
+    glob = np.linalg.norm((g_gpu - g1)[conv]) / np.linalg.norm(g1[conv])
+    unc = ~conv & nz
     print("%s: entries %d (FD-unconverged %d), global rel %.3e, max rel %.3e, p99.9 %.3e" % (
-        label, nz.sum(), (~ok & nz).sum(), glob, rel.max(), np.percentile(rel, 99.9)))
+        label, nz.sum(), unc.sum(), glob, rel[conv & nz].max(), np.percentile(rel[conv & nz], 99.9)))
     if g_coarse is not None:
         print("   vs FD h=1e-4: global rel %.3e" % (np.linalg.norm(g_gpu - g_coarse) / np.linalg.norm(g_coarse)))
-    assert glob <= tol_rel
-    assert np.percentile(rel, 99.9) <= 10 * tol_rel
+    worst = np.argsort(np.where(conv & nz, rel, 0))[::-1][:5]
+    for i in worst:
+        print("   entry %d: gpu %.6e fd %.6e fd2 %.6e" % (i, g_gpu.flat[i], g1.flat[i], g2.flat[i]))
+    assert rel[conv & nz].max() <= tol_rel, label
+    assert unc.sum() <= max_unconverged * nz.sum(), label
+    lo, hi = np.minimum(g1, g2), np.maximum(g1, g2)
+    slack = tol_rel * floor
+    assert np.all((g_gpu[unc] >= lo[unc] - slack[unc]) & (g_gpu[unc] <= hi[unc] + slack[unc])), label
     # nothing outside the union of the stencils
-    assert np.all(g_gpu[~nz & (np.abs(g2) == 0)] == 0)
+    assert np.all(g_gpu[~nz] == 0)
 
 
 @pytest.mark.parametrize("fit", [0, plic.FLAG_FIT_DF32])
