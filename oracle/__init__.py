@@ -98,7 +98,7 @@ def _load():
         lib.oracle_sphere_offset.argtypes = [D]
         lib.oracle_sphere_volume_batch.argtypes = [P, P, I64]
         lib.oracle_sphere_offset_batch.argtypes = [P, P, I64]
-        lib.oracle_curvature_batch.argtypes = [P, I32, I32, I32, P, I64, U, P, P, P]
+        lib.oracle_curvature_batch.argtypes = [P, I32, I32, I32, P, I64, U, P, P, P, P]
         lib.oracle_curvature_grad_fd.argtypes = [P, I32, I32, I32, P, I64, P, D, U, P]
         _lib = lib
         return lib
@@ -277,20 +277,24 @@ def interface_cells(phi) -> np.ndarray:
     return np.flatnonzero(mask.ravel()).astype(np.int32)
 
 
-def curvature(phi, idx, flags: int = 0):
+def curvature(phi, idx, flags: int = 0, with_cond: bool = False):
     """kappa (FP64) for the curvature cells ``idx`` of the FP32 field ``phi``
     (the curvature step of Sec. 4.2 and Appendix B).
 
-    ``phi`` has shape (nz, ny, nx).  Returns (kappa, fit_dim, n_points)."""
+    ``phi`` has shape (nz, ny, nx).  Returns (kappa, fit_dim, n_points), and
+    with ``with_cond`` also the fit's conditioning: the smallest leading pivot
+    of its normal matrix divided by the matrix's trace (1 without a fit)."""
     phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float32))
     nz, ny, nx = phi.shape
     idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
     kappa = np.empty(idx.size, np.float64)
     dim = np.empty(idx.size, np.int32)
     npt = np.empty(idx.size, np.int32)
+    cond = np.empty(idx.size, np.float64) if with_cond else None
     _load().oracle_curvature_batch(_ptr(phi), nx, ny, nz, _ptr(idx), idx.size, flags,
-                                   _ptr(kappa), _ptr(dim), _ptr(npt))
-    return kappa, dim, npt
+                                   _ptr(kappa), _ptr(dim), _ptr(npt),
+                                   None if cond is None else _ptr(cond))
+    return (kappa, dim, npt, cond) if with_cond else (kappa, dim, npt)
 
 
 def curvature_grad_fd(phi, idx, w, h: float = 1e-4, flags: int = 0):

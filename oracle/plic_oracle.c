@@ -401,10 +401,23 @@ static double gauss_solve(int k, const double ain[5][5], const double *bin, doub
  * while a leading pivot det(M_j)/det(M_{j-1}) is below ORC_FIT_TAU * trace(M);
  * the leading block is solved by Gaussian elimination with partial pivoting,
  * the remaining parameters stay 0.  Returns the dimension used. */
+static int lsq_fit(int m, const double *px, const double *py, const double *pz, double *x5,
+                   double *minpiv);
+
 ORC_EXPORT int oracle_lsq_paraboloid(int m, const double *px, const double *py,
                                      const double *pz, double *x5)
 {
-    double M[5][5], b[5], tr = 0.0, detprev = 1.0;
+    return lsq_fit(m, px, py, pz, x5, NULL);
+}
+
+/* The fit of oracle_lsq_paraboloid; *minpiv (nullable) receives the smallest
+ * leading pivot of the dimension used, divided by trace(M) (1 when no
+ * parameter is fitted): a measure of the fit's conditioning, reported beside
+ * kappa. */
+static int lsq_fit(int m, const double *px, const double *py, const double *pz, double *x5,
+                   double *minpiv)
+{
+    double M[5][5], b[5], tr = 0.0, detprev = 1.0, pmin = 1.0;
     int i, j, p, dim;
     memset(M, 0, sizeof M);
     memset(b, 0, sizeof b);
@@ -421,9 +434,11 @@ ORC_EXPORT int oracle_lsq_paraboloid(int m, const double *px, const double *py,
     for (j = 1; j <= dim; ++j) {
         double det = gauss_solve(j, (const double (*)[5])M, NULL, NULL);
         if (!(det / detprev > ORC_FIT_TAU * tr)) { dim = j - 1; break; }
+        if (det / detprev / tr < pmin) pmin = det / detprev / tr;
         detprev = det;
     }
     if (dim > 0) gauss_solve(dim, (const double (*)[5])M, b, x5);
+    if (minpiv) *minpiv = pmin;
     return dim;
 }
 
@@ -455,9 +470,20 @@ ORC_EXPORT double oracle_paraboloid_kappa(const double *x5)
  * is NULL the test 0 < phi_i < 1 is applied to phi27 itself.
  * Writes the fit dimension and the number of neighbour points; returns kappa
  * (-(Eq. 42) unless ORC_KAPPA_PAPER_SIGN). */
+static double curvature_cell(const double *phi27, const int *iface27, const double *nn81,
+                             unsigned flags, int *dim_out, int *npts_out, double *minpiv);
+
 ORC_EXPORT double oracle_curvature_cell(const double *phi27, const int *iface27,
                                         const double *nn81, unsigned flags,
                                         int *dim_out, int *npts_out)
+{
+    return curvature_cell(phi27, iface27, nn81, flags, dim_out, npts_out, NULL);
+}
+
+/* oracle_curvature_cell, with the fit's conditioning (lsq_fit) in *minpiv
+ * (nullable; 1 when no fit is made). */
+static double curvature_cell(const double *phi27, const int *iface27, const double *nn81,
+                             unsigned flags, int *dim_out, int *npts_out, double *minpiv)
 {
     static const double R[3] = {0.56270900, 0.32704452, 0.75921047};
     double n[3], by[3], bx[3], r[3], len, d00, c0[3] = {0, 0, 0}, x5[5];
@@ -466,6 +492,7 @@ ORC_EXPORT double oracle_curvature_cell(const double *phi27, const int *iface27,
 
     if (dim_out) *dim_out = 0;
     if (npts_out) *npts_out = 0;
+    if (minpiv) *minpiv = 1.0;
     ok = (flags & ORC_NORMAL_CM) ? oracle_cm_normal(phi27, n) : oracle_py_normal(phi27, n);
     if (!ok) return 0.0;
     r[0] = R[0]; r[1] = R[1]; r[2] = R[2];
@@ -509,7 +536,7 @@ ORC_EXPORT double oracle_curvature_cell(const double *phi27, const int *iface27,
         pz[m] = q[0] * n[0] + q[1] * n[1] + q[2] * n[2];
         ++m;
     }
-    dim = oracle_lsq_paraboloid(m, px, py, pz, x5);
+    dim = lsq_fit(m, px, py, pz, x5, minpiv);
     if (dim_out) *dim_out = dim;
     if (npts_out) *npts_out = m;
     if (dim == 0) return 0.0;
@@ -555,7 +582,8 @@ static void neighbour_normals(const float *phi, int nx, int ny, int nz, int64_t 
  * interface cells (linear indices x + nx*(y + ny*z)). */
 ORC_EXPORT void oracle_curvature_batch(const float *phi, int nx, int ny, int nz,
                                        const int32_t *idx, int64_t n_iface, unsigned flags,
-                                       double *kappa, int32_t *dim, int32_t *npts)
+                                       double *kappa, int32_t *dim, int32_t *npts,
+                                       double *minpiv)
 {
     int64_t k;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -564,8 +592,8 @@ ORC_EXPORT void oracle_curvature_batch(const float *phi, int nx, int ny, int nz,
         int dm, np;
         gather27(phi, nx, ny, idx[k], s);
         if (flags & ORC_NEIGHBOR_NORMAL) neighbour_normals(phi, nx, ny, nz, idx[k], s, flags, nn);
-        kappa[k] = oracle_curvature_cell(s, NULL, (flags & ORC_NEIGHBOR_NORMAL) ? nn : NULL, flags,
-                                         &dm, &np);
+        kappa[k] = curvature_cell(s, NULL, (flags & ORC_NEIGHBOR_NORMAL) ? nn : NULL, flags,
+                                  &dm, &np, minpiv ? minpiv + k : NULL);
         if (dim) dim[k] = dm;
         if (npts) npts[k] = np;
     }

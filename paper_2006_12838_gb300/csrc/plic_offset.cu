@@ -62,6 +62,120 @@ k_plic_offset(const T* __restrict__ nx, const T* __restrict__ ny, const T* __res
     count_invalid(bad, invalid);
 }
 
+// Work-compacted form of k_plic_offset for the default (non-literal) solvers:
+// the warp runs the symmetry front end and the closed-form cases (Eqs. 24-25)
+// on its 32 x W cells, then gathers the cells that need the heavy part (the
+// trigonometric root of cases (3)/(4), or the Newton / nested-interval
+// iterations) into a dense per-warp task list -- one warp vote per cell slot
+// and a popcount prefix give each task its place -- and runs the heavy part
+// on those tasks only, 32 at a time; the owners then take their results
+// back.  Without this every lane of the warp would pass through the heavy
+// part whenever any lane needed it (about every time: 40-60 % of random cells
+// are in cases (3)/(4)), and lanes with closed-form cells would idle through
+// it.  The task list lives in shared memory (4 values per task).
+template <int METHOD, typename T, bool POLISH>
+__global__ void __launch_bounds__(256)
+k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const T* __restrict__ nz,
+                      const T* __restrict__ V0, T* __restrict__ d0, int64_t n, int vec_ok,
+                      unsigned long long* invalid, void* /* round trip: not fused here */) {
+    typedef typename Vec16<T>::type VT;
+    constexpr int W = Vec16<T>::W;
+    constexpr bool SZ = METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT;
+    typedef Solver<METHOD, T, false> S;
+    __shared__ T task[8][32 * W][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    const int64_t nvec = vec_ok ? n / W : 0;
+    // the loop bound is the same for the 32 lanes of a warp (votes below)
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + warp * 32; i0 < nvec; i0 += wstride) {
+        const int64_t i = i0 + lane;
+        const bool have = i < nvec;
+        T a[W], b[W], c[W], v[W];
+        if (have) {
+            to_arr(ld_stream(reinterpret_cast<const VT*>(nx) + i), a);
+            to_arr(ld_stream(reinterpret_cast<const VT*>(ny) + i), b);
+            to_arr(ld_stream(reinterpret_cast<const VT*>(nz) + i), c);
+            to_arr(ld_stream(reinterpret_cast<const VT*>(V0) + i), v);
+        }
+        // front end (Sec. 2.1) and the closed-form cases
+        T red[W][4], scale[W], res[W];
+        unsigned need = 0u;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            res[j] = T(0);
+            scale[j] = T(0);
+            if (!have) continue;
+            T n1, n2, n3;
+            reduce_normal<T, false>(a[j], b[j], c[j], n1, n2, n3);
+            const T L = fabs(a[j]) + fabs(b[j]) + fabs(c[j]);
+            const bool ok = (v[j] >= T(0)) && (v[j] <= T(1)) && (L > T(0)) && (L <= T(3));
+            if (!ok) {
+                bad += 1;
+                res[j] = T(NAN);
+                continue;
+            }
+            const T V = reduce_volume<T, false>(v[j]);
+            if (SZ) {
+                const T il = Fm<T>::rcp_(L);
+                n1 *= il;
+                n3 *= il;
+                n2 = Fm<T>::fdim_(T(1), n1 + n3);
+                scale[j] = L;
+            } else {
+                scale[j] = T(1);
+            }
+            red[j][0] = V; red[j][1] = n1; red[j][2] = n2; red[j][3] = n3;
+            T d;
+            if (S::easy(V, n1, n2, n3, d)) res[j] = d;
+            else need |= 1u << j;
+        }
+        // the heavy part on the packed task list of the warp
+        unsigned m[W];
+        int pre[W + 1];
+        pre[0] = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            m[j] = __ballot_sync(0xffffffffu, (need >> j) & 1u);
+            pre[j + 1] = pre[j] + __popc(m[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if ((need >> j) & 1u) {
+                T* q = task[warp][pre[j] + __popc(m[j] & lt)];
+                q[0] = red[j][0]; q[1] = red[j][1]; q[2] = red[j][2]; q[3] = red[j][3];
+            }
+        __syncwarp();
+        for (int t = lane; t < pre[W]; t += 32) {
+            T* q = task[warp][t];
+            q[0] = S::hard(q[0], q[1], q[2], q[3]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if ((need >> j) & 1u) res[j] = task[warp][pre[j] + __popc(m[j] & lt)][0];
+        __syncwarp();
+        // polish and the symmetry back to d0 (Eqs. 5-8)
+        T r[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            if (!(scale[j] > T(0))) {
+                r[j] = res[j];                       // invalid cell: NaN
+                continue;
+            }
+            T x = res[j];
+            if (POLISH) x = polish<T>(x, red[j][0], red[j][1], red[j][2], red[j][3]);
+            if (SZ) r[j] = scale[j] * copysign(T(0.5) - x, v[j] - T(0.5));
+            else r[j] = copysign(T(0.5) * (red[j][1] + red[j][2] + red[j][3]) - x, v[j] - T(0.5));
+        }
+        if (have) st_stream(reinterpret_cast<VT*>(d0) + i, from_arr(r));
+    }
+    for (int64_t i = nvec * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += wstride)
+        d0[i] = offset_cell<METHOD, T, POLISH, false>(nx[i], ny[i], nz[i], V0[i], bad);
+    count_invalid(bad, invalid);
+}
+
 // The optimised SZ solution in FP32 (the paper's recommended solver, Sec.
 // 2.5) on paired FP32 instructions: each thread takes 4 cells per step as two
 // pairs.  Tail and unaligned cells go through the same pair code with the
@@ -136,14 +250,29 @@ static const void* kptr() {
     return reinterpret_cast<const void*>(&k_plic_offset<METHOD, T, POLISH, FAITHFUL>);
 }
 
+template <int METHOD, typename T, bool POLISH>
+static const void* cptr() {
+    return reinterpret_cast<const void*>(&k_plic_offset_compact<METHOD, T, POLISH>);
+}
+
+// The default solvers run work-compacted (k_plic_offset_compact); the
+// paper-literal ones keep one cell after the other per lane.
+// Kawano's SZ in FP32 stays one cell after the other: its heavy part (one
+// arccosine and one cosine on the FP32 pipes) is too short to repay the
+// packing (measured 102 against 130 G solves/s on 2^26 cells); in FP64, and
+// for the iterative solvers, packing wins (e.g. nested intervals FP32 27 ->
+// 40, FP64 SZ-opt 3.3 -> 4.5 G solves/s).
 template <int METHOD>
 static const void* pick(plic_precision p, bool faithful) {
     if (p == PLIC_FP64_REFINED) return reinterpret_cast<const void*>(&k_plic_offset_refined<METHOD>);
     if (p == PLIC_FP64)
-        return faithful ? kptr<METHOD, double, false, true>() : kptr<METHOD, double, false, false>();
+        return faithful ? kptr<METHOD, double, false, true>() : cptr<METHOD, double, false>();
+    const bool packed = !faithful && METHOD != M_SZ_ORIG;
     if (p == PLIC_FP32_POLISHED)
-        return faithful ? kptr<METHOD, float, true, true>() : kptr<METHOD, float, true, false>();
-    return faithful ? kptr<METHOD, float, false, true>() : kptr<METHOD, float, false, false>();
+        return packed ? cptr<METHOD, float, true>()
+                      : (faithful ? kptr<METHOD, float, true, true>() : kptr<METHOD, float, true, false>());
+    return packed ? cptr<METHOD, float, false>()
+                  : (faithful ? kptr<METHOD, float, false, true>() : kptr<METHOD, float, false, false>());
 }
 
 // The paired FP32 kernels (optimised SZ, analytic); *fused is set when the

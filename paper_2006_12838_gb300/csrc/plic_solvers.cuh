@@ -185,16 +185,34 @@ __device__ __forceinline__ T analytic_case4(T V, T n1, T n2, T n3) {
                         T(0.5) * L);
 }
 
+// Every solver comes in two parts (struct Solver below): easy() settles the
+// closed-form cases and returns false for the cells that need the heavy part,
+// hard() (the trigonometric root or the iterations); solve_<method> is one
+// after the other.  The work-compacted kernel runs easy() on every cell and
+// hard() only on the cells that need it, packed densely over the lanes.
 template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T solve_analytic(T V, T n1, T n2, T n3) {
+__device__ __forceinline__ bool analytic_easy(T V, T n1, T n2, T n3, T& d) {
     const Cases<T> k = classify<T>(V, n1, n2, n3);
-    if (k.c != 0) return closed_form<T>(k, n1);
+    if (k.c == 0) return false;
+    d = closed_form<T>(k, n1);
+    return true;
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T analytic_hard(T V, T n1, T n2, T n3) {
+    const Cases<T> k = classify<T>(V, n1, n2, n3);
     if (FAITHFUL) {
         const T d3 = analytic_case3<T>(V, n1, n2, n3, k.n12);
         return d3 <= n3 ? d3 : analytic_case4<T>(V, n1, n2, n3);
     }
     return offset_in_case3<T>(k, n1, n2, n3) ? analytic_case3<T>(V, n1, n2, n3, k.n12)
                                              : analytic_case4<T>(V, n1, n2, n3);
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_analytic(T V, T n1, T n2, T n3) {
+    T d;
+    return analytic_easy<T, FAITHFUL>(V, n1, n2, n3, d) ? d : analytic_hard<T, FAITHFUL>(V, n1, n2, n3);
 }
 
 // ----------------------------------------------------------------------------
@@ -222,22 +240,36 @@ __device__ __forceinline__ T solve_analytic(T V, T n1, T n2, T n3) {
 // reports; this reproduces it.
 // ----------------------------------------------------------------------------
 template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T solve_sz_orig(T w, T m1, T m2, T m3) {
+__device__ __forceinline__ bool sz_orig_easy(T w, T m1, T m2, T m3, T& a) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T m12 = m1 + m2;
+    const T vb1 = F::div_(m1 * m1, T(6) * m2 * m3 + T(1e-25));
+    if (w < vb1) {                                                                // (1)
+        a = F::cbrt_(T(6) * m1 * m2 * m3 * w);
+        return true;
+    }
+    if (w < vb1 + F::div_(T(0.5) * (m2 - m1), m3)) {                               // (2)
+        a = T(0.5) * m1 + F::sqrt_(T(2) * m2 * m3 * w - K::twelfth * m1 * m1);
+        return true;
+    }
+    if (!(m3 < m12) && !(w < F::div_(T(0.5) * m12, m3))) {
+        a = m3 * w + T(0.5) * m12;                                                 // (5)
+        return a != T(0);
+    }
+    return false;
+}
+
+// Cases (3)/(4) (and the zero case-(5) offset that implementation sends here).
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T sz_orig_hard(T w, T m1, T m2, T m3) {
     typedef Fm<T> F;
     typedef Kc<T> K;
     const T m12 = m1 + m2, e3 = m1 * m2 * m3;
-    const T vb1 = F::div_(m1 * m1, T(6) * m2 * m3 + T(1e-25));
-    if (w < vb1) return F::cbrt_(T(6) * e3 * w);                                   // (1)
-    if (w < vb1 + F::div_(T(0.5) * (m2 - m1), m3))
-        return T(0.5) * m1 + F::sqrt_(T(2) * m2 * m3 * w - K::twelfth * m1 * m1);    // (2)
     const bool tall = !(m3 < m12);
     const T vb3 = tall ? F::div_(T(0.5) * m12, m3)
                        : F::div_(cb(m3) - cb(m3 - m1) - cb(m3 - m2), T(6) * e3);
-    bool case3 = w < vb3;
-    if (!case3 && tall) {
-        const T a5 = m3 * w + T(0.5) * m12;                                         // (5)
-        if (a5 != T(0)) return a5;
-    }
+    const bool case3 = w < vb3;
     T s2, mq2, shift;                     // s^2, -q/2, -a2/3
     if (FAITHFUL) {
         const T w6 = T(6) * e3 * w;
@@ -258,6 +290,12 @@ __device__ __forceinline__ T solve_sz_orig(T w, T m1, T m2, T m3) {
     T r = F::div_(mq2, s2 * s);
     if (!FAITHFUL) r = fmin(fmax(r, T(-1)), T(1));
     return shift + T(2) * s * F::cos_(K::third * (F::acos_(r) + K::four_pi));
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_sz_orig(T w, T m1, T m2, T m3) {
+    T a;
+    return sz_orig_easy<T, FAITHFUL>(w, m1, m2, m3, a) ? a : sz_orig_hard<T, FAITHFUL>(w, m1, m2, m3);
 }
 
 // ----------------------------------------------------------------------------
@@ -311,6 +349,39 @@ __device__ __forceinline__ T solve_sz_opt_default(T V, T n1, T n2, T n3) {
 template <typename T, bool FAITHFUL>
 __device__ __forceinline__ T solve_sz_opt(T V, T n1, T n2, T n3) {
     return solve_sz_opt_default<T, !FAITHFUL>(V, n1, n2, n3);
+}
+
+// The two parts of the optimised SZ solution (the FP64 path branches on the
+// cases; the FP32 path selects and has its own paired kernel).
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ bool sz_opt_easy(T V, T n1, T n2, T n3, T& d) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T n12 = n1 + n2, n3V = n3 * V;
+    const T V6n2n3 = T(6) * n2 * n3V, sqn1 = n1 * n1;
+    if (n12 <= T(2) * n3V) { d = n3V + T(0.5) * n12; return true; }
+    if (V6n2n3 < sqn1) { d = F::cbrt_(V6n2n3 * n1); return true; }
+    if (T(3) * n2 * (T(2) * n3V + n1 - n2) < sqn1) {
+        d = T(0.5) * (n1 + F::sqrt_(T(8) * n2 * n3V - K::third * sqn1));
+        return true;
+    }
+    return false;
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T sz_opt_hard(T V, T n1, T n2, T n3) {
+    typedef Fm<T> F;
+    typedef Kc<T> K;
+    const T n12 = n1 + n2, n3V = n3 * V, n1n2 = n1 * n2;
+    const T num3 = sq(n3) * (T(3) * n12 - n3) + n1 * n1 * (n1 - T(3) * n3) + sq(n2) * (n2 - T(3) * n3);
+    const bool c3 = !(n3 < n12) || T(6) * n2 * n3V * n1 < num3;
+    const T q = c3 ? T(1.5) * n1n2 * (n12 - T(2) * n3V) : T(0.75) * n1n2 * n3 * (T(1) - T(2) * V);
+    const T t2 = c3 ? T(2) * n1n2 : T(0.25) * (n1 * (T(2) * (n2 + n3) - n1) - sq(n3 - n2));
+    const T c = c3 ? n12 : T(0.5);
+    const T rt = F::rsqrt_(t2);
+    T arg = q * (rt * rt * rt);
+    if (!FAITHFUL) arg = fmin(fmax(arg, T(-1)), T(1));
+    return c - T(2) * (t2 * rt) * F::sin_(K::third * F::asin_(arg));
 }
 
 // ----------------------------------------------------------------------------
@@ -409,9 +480,16 @@ __device__ __forceinline__ T halve_to_adjacent(T lo, T hi, T rhs, T n1, T n2, T 
 }
 
 template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T solve_newton(T V, T n1, T n2, T n3) {
+__device__ __forceinline__ bool newton_easy(T V, T n1, T n2, T n3, T& d) {
     const Cases<T> k = classify<T>(V, n1, n2, n3);
-    if (k.c == 5 || k.c == 2) return closed_form<T>(k, n1);
+    if (k.c != 5 && k.c != 2) return false;
+    d = closed_form<T>(k, n1);
+    return true;
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T newton_hard(T V, T n1, T n2, T n3) {
+    const Cases<T> k = classify<T>(V, n1, n2, n3);
     const T half = T(0.5) * (k.n12 + n3);                 // L/2
     if (FAITHFUL) {
         const T rhs6 = k.w * n1;                           // 6 V n1 n2 n3
@@ -434,9 +512,19 @@ __device__ __forceinline__ T solve_newton(T V, T n1, T n2, T n3) {
 }
 
 template <typename T, bool FAITHFUL>
-__device__ __forceinline__ T solve_nested(T V, T n1, T n2, T n3) {
+__device__ __forceinline__ T solve_newton(T V, T n1, T n2, T n3) {
+    T d;
+    return newton_easy<T, FAITHFUL>(V, n1, n2, n3, d) ? d : newton_hard<T, FAITHFUL>(V, n1, n2, n3);
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ bool nested_easy(T V, T n1, T n2, T n3, T& d) {
+    return analytic_easy<T, FAITHFUL>(V, n1, n2, n3, d);
+}
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T nested_hard(T V, T n1, T n2, T n3) {
     const Cases<T> k = classify<T>(V, n1, n2, n3);
-    if (k.c != 0) return closed_form<T>(k, n1);
     const T half = T(0.5) * (k.n12 + n3);
     if (FAITHFUL) {
         const T rhs6 = k.w * n1;
@@ -448,6 +536,36 @@ __device__ __forceinline__ T solve_nested(T V, T n1, T n2, T n3) {
     if (d <= n3) return d;
     return halve_to_adjacent<T>(n3, half, k.w, n1, n2, n3, inv_n1);
 }
+
+template <typename T, bool FAITHFUL>
+__device__ __forceinline__ T solve_nested(T V, T n1, T n2, T n3) {
+    T d;
+    return nested_easy<T, FAITHFUL>(V, n1, n2, n3, d) ? d : nested_hard<T, FAITHFUL>(V, n1, n2, n3);
+}
+
+// The split parts by method, for the work-compacted kernel (reduced inputs:
+// the L1-normalised m for the SZ solutions, the unit-normal n otherwise).
+template <int METHOD, typename T, bool FAITHFUL> struct Solver;
+template <typename T, bool F> struct Solver<M_ANALYTIC, T, F> {
+    static __device__ __forceinline__ bool easy(T V, T a, T b, T c, T& d) { return analytic_easy<T, F>(V, a, b, c, d); }
+    static __device__ __forceinline__ T hard(T V, T a, T b, T c) { return analytic_hard<T, F>(V, a, b, c); }
+};
+template <typename T, bool F> struct Solver<M_SZ_ORIG, T, F> {
+    static __device__ __forceinline__ bool easy(T V, T a, T b, T c, T& d) { return sz_orig_easy<T, F>(V, a, b, c, d); }
+    static __device__ __forceinline__ T hard(T V, T a, T b, T c) { return sz_orig_hard<T, F>(V, a, b, c); }
+};
+template <typename T, bool F> struct Solver<M_SZ_OPT, T, F> {
+    static __device__ __forceinline__ bool easy(T V, T a, T b, T c, T& d) { return sz_opt_easy<T, F>(V, a, b, c, d); }
+    static __device__ __forceinline__ T hard(T V, T a, T b, T c) { return sz_opt_hard<T, F>(V, a, b, c); }
+};
+template <typename T, bool F> struct Solver<M_NEWTON, T, F> {
+    static __device__ __forceinline__ bool easy(T V, T a, T b, T c, T& d) { return newton_easy<T, F>(V, a, b, c, d); }
+    static __device__ __forceinline__ T hard(T V, T a, T b, T c) { return newton_hard<T, F>(V, a, b, c); }
+};
+template <typename T, bool F> struct Solver<M_NESTED, T, F> {
+    static __device__ __forceinline__ bool easy(T V, T a, T b, T c, T& d) { return nested_easy<T, F>(V, a, b, c, d); }
+    static __device__ __forceinline__ T hard(T V, T a, T b, T c) { return nested_hard<T, F>(V, a, b, c); }
+};
 
 // ----------------------------------------------------------------------------
 // Whole cell: d0(V0, n) (Sec. 2, Eq. 1) for one method and precision.

@@ -91,7 +91,9 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
         if (ex != 0) gx = fmaf(w * (float)ex, v, gx);
         if (ey != 0) gy = fmaf(w * (float)ey, v, gy);
         if (ez != 0) gz = fmaf(w * (float)ez, v, gz);
-        if (v > 0.0f && v < 1.0f) mask |= 1u << i;
+        // 0 < v < 1 as one unsigned compare of the bits: the positive floats
+        // below 1.0f are the patterns 1 .. 0x3F7FFFFF
+        if (__float_as_uint(v) - 1u < 0x3F7FFFFFu) mask |= 1u << i;
     });
     // 2. normal and frame (Sec. 4.2)
     const float gl2 = gx * gx + gy * gy + gz * gz;
@@ -207,12 +209,22 @@ k_vof_curvature_batched_tpc(const vof_field* __restrict__ fields, const int64_t*
         const int64_t start = (int64_t)__shfl_sync(0xffffffffu, t, 0);
         if (start >= total) break;
         const int64_t end = start + chunk < total ? start + chunk : total;
-        for (int64_t gi = start + lane; gi < end; gi += 32) {
+        // the field of the ticket's first cell, found once per ticket (lane 0,
+        // binary search over the list prefix); each lane then steps forward
+        // from it to its own cell's field (the lists are long: rarely a step)
+        int f0 = 0;
+        if (lane == 0) {
             int lo = 0, hi = n_fields - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(prefix + mid) <= gi) lo = mid; else hi = mid - 1;
+                if (__ldg(prefix + mid) <= start) lo = mid; else hi = mid - 1;
             }
+            f0 = lo;
+        }
+        f0 = __shfl_sync(0xffffffffu, f0, 0);
+        for (int64_t gi = start + lane; gi < end; gi += 32) {
+            int lo = f0;
+            while (lo + 1 < n_fields && __ldg(prefix + lo + 1) <= gi) ++lo;
             const int64_t kk = gi - __ldg(prefix + lo);
             const vof_field& F = fields[lo];
             const float k = tpc_kappa<METHOD, FIT>(F.phi, F.nx, (int64_t)F.nx * F.ny,

@@ -10,9 +10,10 @@ only away from the clamp -- near fills of 2e-4 the offset d0 ~ V^(1/3) bends
 so fast that central differences with h = 1e-4 are off by ~5 % in norm on this
 field (h = 1e-5: 4e-4; h = 1e-6 and 1e-7 agree to 4e-6).  The oracle is FP64,
 so the gate uses h = 1e-6 and h = 1e-7, per entry: where the two agree to
-1e-4 of the gradient scale the GPU entry must match to 1e-3 relative (with a
-floor of 1e-2 of the scale); where they disagree (counted and bounded) it must
-lie between them, widened by the same tolerance.  The h = 1e-4 difference is
+1e-4 of the gradient scale the GPU entry must match to 2e-4 relative (with a
+floor of 1e-2 of the scale; the FP32 adjoint reaches 3.4e-5 on the ellipsoid);
+where they disagree (counted and bounded) it must lie between them, widened
+by the same tolerance.  The h = 1e-4 difference is
 printed beside it.
 """
 import numpy as np
@@ -35,7 +36,7 @@ def dev():
     return torch.device("cuda:0")
 
 
-def _compare(g_gpu, g1, g2, label, tol_rel=1e-3, g_coarse=None, max_unconverged=0.01):
+def _compare(g_gpu, g1, g2, label, tol_rel=2e-4, g_coarse=None, max_unconverged=0.01):
     """Per-entry gate: every entry where the two FD steps agree (FD converged)
     must satisfy |g_gpu - g_fd| <= tol_rel max(|g_fd|, 1e-2 max|g_fd|); the
     entries where they disagree are counted and bounded (a share of the
@@ -52,7 +53,7 @@ def _compare(g_gpu, g1, g2, label, tol_rel=1e-3, g_coarse=None, max_unconverged=
         label, nz.sum(), unc.sum(), glob, rel[conv & nz].max(), np.percentile(rel[conv & nz], 99.9)))
     if g_coarse is not None:
         print("   vs FD h=1e-4: global rel %.3e" % (np.linalg.norm(g_gpu - g_coarse) / np.linalg.norm(g_coarse)))
-    worst = np.argsort(np.where(conv & nz, rel, 0))[::-1][:5]
+    worst = np.argsort(np.where(conv & nz, rel, 0).ravel())[::-1][:5]
     for i in worst:
         print("   entry %d: gpu %.6e fd %.6e fd2 %.6e" % (i, g_gpu.flat[i], g1.flat[i], g2.flat[i]))
     assert rel[conv & nz].max() <= tol_rel, label

@@ -72,36 +72,36 @@ def test_compaction_edge_fields(dev, orc, field):
     np.testing.assert_array_equal(small.cpu().numpy(), idx[:100])
 
 
-def _check(kappa, kref, dim, tol, label):
-    return gate_kappa(kappa, kref, dim, label, tol)
+def _check(kappa, kref, dim, tol, label, cond=None):
+    return gate_kappa(kappa, kref, dim, label, tol, cond)
 
 
 @pytest.mark.parametrize("method", list(plic.METHODS))
 def test_curvature_methods_default_fit(dev, orc, field, method):
     p, idx = field
-    kref, dim, _ = orc.curvature(p, idx)
+    kref, dim, _, cond = orc.curvature(p, idx, with_cond=True)
     phid = torch.tensor(p, device=dev)
     k = plic.curvature(phid, torch.tensor(idx, device=dev), method=method).cpu().numpy()
-    _check(k.astype(np.float64), kref, dim, TOL, method + " adaptive fit")
+    _check(k.astype(np.float64), kref, dim, TOL, method + " adaptive fit", cond)
 
 
 @pytest.mark.parametrize("fit,tol", [(plic.FLAG_FIT_DF32, TOL), (plic.FLAG_FIT_FP64, TOL),
                                      (plic.FLAG_FIT_FP32, 1e-3)])
 def test_curvature_fit_precisions(dev, orc, field, fit, tol):
     p, idx = field
-    kref, dim, _ = orc.curvature(p, idx)
+    kref, dim, _, cond = orc.curvature(p, idx, with_cond=True)
     phid = torch.tensor(p, device=dev)
     k = plic.curvature(phid, torch.tensor(idx, device=dev), flags=fit).cpu().numpy()
-    _check(k.astype(np.float64), kref, dim, tol, "fit flag %d" % fit)
+    _check(k.astype(np.float64), kref, dim, tol, "fit flag %d" % fit, cond)
 
 
 def test_curvature_flags(dev, orc, field):
     p, idx = field
     phid = torch.tensor(p, device=dev)
     it = torch.tensor(idx, device=dev)
-    kref, dim, _ = orc.curvature(p, idx, orc.POINT_CENTROID)
+    kref, dim, _, cond = orc.curvature(p, idx, orc.POINT_CENTROID, with_cond=True)
     k = plic.curvature(phid, it, flags=plic.FLAG_POINT_CENTROID).cpu().numpy()
-    _check(k.astype(np.float64), kref, dim, TOL, "centroid points")
+    _check(k.astype(np.float64), kref, dim, TOL, "centroid points", cond)
     k0 = plic.curvature(phid, it)
     k1 = plic.curvature(phid, it, flags=plic.FLAG_KAPPA_PAPER_SIGN)
     assert torch.equal(k0, -k1)
@@ -136,7 +136,7 @@ def test_batched_matches_single(dev, orc):
         args.append((phid, it, k, kap))
         singles.append(plic.curvature(phid, it).cpu().numpy() if k else np.zeros(0, np.float32))
     big = max(range(len(args)), key=lambda i: args[i][2])
-    kref, dim, _ = orc.curvature(args[big][0].cpu().numpy(), args[big][1].cpu().numpy())
+    kref, dim, _, cond = orc.curvature(args[big][0].cpu().numpy(), args[big][1].cpu().numpy(), with_cond=True)
     # one thread per cell (the default and lanes_per_cell = 1): the single-field
     # kernel's arithmetic, so the same values
     for tuning in (None, (128, 64, 1), (128, 7, 2), (128, 1000, 0), (128, 96, 0, 1), (128, 32, 3, 0)):
@@ -145,16 +145,17 @@ def test_batched_matches_single(dev, orc):
             np.testing.assert_array_equal(kap[:k].cpu().numpy(), s)
     # eight lanes per cell: other summation orders; against the oracle, per
     # cell, on every field
-    refs = [orc.curvature(a[0].cpu().numpy(), a[1].cpu().numpy()) if a[2] else None for a in args]
+    refs = [orc.curvature(a[0].cpu().numpy(), a[1].cpu().numpy(), with_cond=True) if a[2] else None
+            for a in args]
     for tuning in ((128, 64, 1, 8), (128, 7, 2, 8), (128, 1000, 0, 8)):
         plic.curvature_batched(args, tuning=tuning)
         for j, ((phid, it, k, kap), r) in enumerate(zip(args, refs)):
             if k:
                 _check(kap[:k].cpu().numpy().astype(np.float64), r[0], r[1], TOL,
-                       "batched, 8 lanes %s, field %d" % (tuning, j))
+                       "batched, 8 lanes %s, field %d" % (tuning, j), r[3])
     plic.curvature_batched(args)
     phid, it, k, kap = args[big]
-    _check(kap[:k].cpu().numpy().astype(np.float64), kref, dim, TOL, "batched")
+    _check(kap[:k].cpu().numpy().astype(np.float64), kref, dim, TOL, "batched", cond)
     # the prepared descriptor table, reused: same values
     batch = plic.BatchedFields(args)
     for _ in range(2):
@@ -214,10 +215,10 @@ def _reduced_stencils(orc, rng):
 def test_reduced_and_near_singular_fits(dev, orc, fit):
     rng = np.random.default_rng(61)
     phi, idx = _stencil_field(_reduced_stencils(orc, rng))
-    kref, dim, npt = orc.curvature(phi, idx)
+    kref, dim, npt, cond = orc.curvature(phi, idx, with_cond=True)
     print("oracle fit dimensions:", np.bincount(dim, minlength=6))
     for d in (1, 2, 3, 4):
         assert (dim == d).any(), d
     k = plic.curvature(torch.tensor(phi, device=dev), torch.tensor(idx, device=dev),
                        flags=fit).cpu().numpy()
-    _check(k.astype(np.float64), kref, dim, TOL, "reduced / near-singular fits, flag %d" % fit)
+    _check(k.astype(np.float64), kref, dim, TOL, "reduced / near-singular fits, flag %d" % fit, cond)

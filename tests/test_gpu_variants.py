@@ -41,8 +41,8 @@ def field(orc):
     return p, orc.interface_cells(p)
 
 
-def _rel(kappa, kref, dim, label, tol=TOL):
-    gate_kappa(kappa, kref, dim, label, tol)
+def _rel(kappa, kref, dim, label, tol=TOL, cond=None):
+    gate_kappa(kappa, kref, dim, label, tol, cond)
 
 
 @pytest.mark.parametrize("flags", [0, 64])
@@ -84,10 +84,10 @@ def test_curvature_variants(dev, orc, field, flags):
     phid = torch.tensor(p, device=dev)
     it = torch.tensor(idx, device=dev)
     oflags = flags & (2 | 64 | 128)
-    kref, dim, _ = orc.curvature(p, idx, oflags)
+    kref, dim, _, cond = orc.curvature(p, idx, oflags, with_cond=True)
     k = plic.curvature(phid, it, flags=flags).cpu().numpy().astype(np.float64)
     tol = 1e-3 if flags & 8 else TOL
-    _rel(k, kref, dim, "variant flags %d" % flags, tol)
+    _rel(k, kref, dim, "variant flags %d" % flags, tol, cond)
 
 
 @pytest.mark.parametrize("method", list(plic.METHODS))
@@ -95,9 +95,9 @@ def test_neighbour_normal_methods(dev, orc, field, method):
     p, idx = field
     phid = torch.tensor(p, device=dev)
     it = torch.tensor(idx, device=dev)
-    kref, dim, _ = orc.curvature(p, idx, 128)
+    kref, dim, _, cond = orc.curvature(p, idx, 128, with_cond=True)
     k = plic.curvature(phid, it, method=method, flags=128).cpu().numpy().astype(np.float64)
-    _rel(k, kref, dim, "neighbour normals %s" % method)
+    _rel(k, kref, dim, "neighbour normals %s" % method, TOL, cond)
 
 
 def test_laplace_pressure_is_two_sigma_kappa(dev, field):

@@ -69,3 +69,27 @@ def test_fill_fields_exact_quantised():
     np.testing.assert_array_equal(phi, p2)       # union with itself
     e = synth.fill_ellipsoid((40, 40, 40), (20, 20, 20), (6, 9, 12)).numpy()
     assert abs(e.sum() - 4 / 3 * math.pi * 6 * 9 * 12) < 1.0
+
+
+def test_boundary_cells_sit_on_case_boundaries(orc):
+    # the throughput workload's boundary cells: the plane through the corner
+    # that ends case (2) or starts case (4) / (5), whose volume must equal the
+    # closed-form boundary volumes of the configuration (Eq. 10 at d = n2,
+    # n3 and n1 + n2)
+    from paper_2006_12838_gb300 import synth
+    c = synth.plic_cells(40_000, seed=2, edge_frac=0.02, boundary_frac=0.1)
+    b = c["boundary"]
+    assert 0.08 < b.mean() < 0.12 and not b[-800:].any()
+    n = c["n"][:, b]
+    Vb = orc.volume(n[0], n[1], n[2], c["d0_boundary"][b])
+    n1, n2, n3 = np.sort(np.abs(n), 0)
+    V23 = (3 * n2 ** 2 - 3 * n1 * n2 + n1 ** 2) / (6 * n2 * n3)
+    V34 = (n3 ** 3 - (n3 - n1) ** 3 - (n3 - n2) ** 3) / (6 * n1 * n2 * n3)
+    V35 = (n1 + n2) / (2 * n3)
+    other = np.where(n3 >= n1 + n2, V35, V34)
+    at23 = np.abs(Vb - V23) < 1e-12
+    assert np.all(at23 | (np.abs(Vb - other) < 1e-12))
+    assert 0.4 < at23.mean() < 0.6
+    V0 = synth.boundary_fill(Vb, c["dV"][b], c["mirror"][b])
+    V = np.minimum(V0, 1 - V0)
+    assert np.all(np.abs(V - np.clip(Vb, 0, 0.5)) <= 1e-6 + 1e-15)
