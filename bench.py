@@ -1198,7 +1198,7 @@ def main():
     # 24 B/cell: nx, ny, nz, V0 in (16) + d0, V0_rt out (8)
     alg_bytes = 24.0 * CELLS
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_plic_offset_pair<METHOD=M_SZ_OPT,POLISH=1,ROUNDTRIP=1>",
+    roof = {"bound": "hbm", "kernel": "k_plic_offset_pair<METHOD=M_SZ_OPT,POLISH=1,ROUNDTRIP=1,COUNT=0>",
             "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": profile_traffic("plic_offset_roundtrip_sz_opt_fp32p"),

@@ -181,8 +181,10 @@ k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const 
 // pairs.  Tail and unaligned cells go through the same pair code with the
 // cell duplicated in both lanes, so every cell sees identical arithmetic.
 // With ROUNDTRIP the forward volume of each stored d0 is written to vrt in
-// the same pass (plic_offset_roundtrip).
-template <int METHOD, bool POLISH, bool ROUNDTRIP>
+// the same pass (plic_offset_roundtrip); COUNT (an invalid-cell counter was
+// given) keeps the per-cell count of invalid inputs, which otherwise costs
+// instructions for nothing.
+template <int METHOD, bool POLISH, bool ROUNDTRIP, bool COUNT>
 __global__ void __launch_bounds__(256)
 k_plic_offset_pair(const float* __restrict__ nx, const float* __restrict__ ny,
                    const float* __restrict__ nz, const float* __restrict__ V0,
@@ -198,10 +200,10 @@ k_plic_offset_pair(const float* __restrict__ nx, const float* __restrict__ ny,
         const float4 c = __ldcs(reinterpret_cast<const float4*>(nz) + i);
         const float4 v = __ldcs(reinterpret_cast<const float4*>(V0) + i);
         float2 w0, w1;
-        const float2 r0 = p2::offset_pair<METHOD, POLISH, ROUNDTRIP>(
+        const float2 r0 = p2::offset_pair<METHOD, POLISH, ROUNDTRIP, COUNT>(
             make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y), make_float2(v.x, v.y),
             bad, &w0);
-        const float2 r1 = p2::offset_pair<METHOD, POLISH, ROUNDTRIP>(
+        const float2 r1 = p2::offset_pair<METHOD, POLISH, ROUNDTRIP, COUNT>(
             make_float2(a.z, a.w), make_float2(b.z, b.w), make_float2(c.z, c.w), make_float2(v.z, v.w),
             bad, &w1);
         __stcs(reinterpret_cast<float4*>(d0) + i, make_float4(r0.x, r0.y, r1.x, r1.y));
@@ -210,14 +212,14 @@ k_plic_offset_pair(const float* __restrict__ nx, const float* __restrict__ ny,
     for (int64_t i = nvec * 4 + tid; i < n; i += stride) {
         int bad2 = 0;
         float2 w;
-        const float2 r = p2::offset_pair<METHOD, POLISH, ROUNDTRIP>(
+        const float2 r = p2::offset_pair<METHOD, POLISH, ROUNDTRIP, COUNT>(
             make_float2(nx[i], nx[i]), make_float2(ny[i], ny[i]), make_float2(nz[i], nz[i]),
             make_float2(V0[i], V0[i]), bad2, &w);
         bad += bad2 >> 1;
         d0[i] = r.x;
         if (ROUNDTRIP) vrt[i] = w.x;
     }
-    count_invalid(bad, invalid);
+    if (COUNT) count_invalid(bad, invalid);
 }
 
 // PLIC_FP64_REFINED: double in/out, FP32 solve + two FP64 Newton steps.
@@ -277,14 +279,19 @@ static const void* pick(plic_precision p, bool faithful) {
 
 // The paired FP32 kernels (optimised SZ, analytic); *fused is set when the
 // round-trip volume comes out of the same kernel.
-template <int METHOD>
-static const void* pick_pair(bool polish, bool roundtrip, bool* fused) {
-    *fused = roundtrip;
+template <int METHOD, bool COUNT>
+static const void* pick_pair_c(bool polish, bool roundtrip) {
     if (polish)
-        return roundtrip ? reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, true, true>)
-                         : reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, true, false>);
-    return roundtrip ? reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, false, true>)
-                     : reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, false, false>);
+        return roundtrip ? reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, true, true, COUNT>)
+                         : reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, true, false, COUNT>);
+    return roundtrip ? reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, false, true, COUNT>)
+                     : reinterpret_cast<const void*>(&k_plic_offset_pair<METHOD, false, false, COUNT>);
+}
+
+template <int METHOD>
+static const void* pick_pair(bool polish, bool roundtrip, bool count, bool* fused) {
+    *fused = roundtrip;
+    return count ? pick_pair_c<METHOD, true>(polish, roundtrip) : pick_pair_c<METHOD, false>(polish, roundtrip);
 }
 
 static plic_status offset_entry(const void* nx, const void* ny, const void* nz, const void* V0,
@@ -310,12 +317,14 @@ static plic_status offset_entry(const void* nx, const void* ny, const void* nz, 
     const void* k = nullptr;
     switch (m) {
         case PLIC_ANALYTIC:
-            k = (!dbl && !faithful) ? pick_pair<M_ANALYTIC>(p == PLIC_FP32_POLISHED, vrt != nullptr, fused)
+            k = (!dbl && !faithful) ? pick_pair<M_ANALYTIC>(p == PLIC_FP32_POLISHED, vrt != nullptr,
+                                                            d_invalid_count != nullptr, fused)
                                     : pick<M_ANALYTIC>(p, faithful);
             break;
         case PLIC_SZ_ORIG: k = pick<M_SZ_ORIG>(p, faithful); break;
         case PLIC_SZ_OPT:
-            k = (!dbl && !faithful) ? pick_pair<M_SZ_OPT>(p == PLIC_FP32_POLISHED, vrt != nullptr, fused)
+            k = (!dbl && !faithful) ? pick_pair<M_SZ_OPT>(p == PLIC_FP32_POLISHED, vrt != nullptr,
+                                                          d_invalid_count != nullptr, fused)
                                     : pick<M_SZ_OPT>(p, faithful);
             break;
         case PLIC_NEWTON: k = pick<M_NEWTON>(p, faithful); break;

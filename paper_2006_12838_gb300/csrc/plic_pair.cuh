@@ -30,7 +30,7 @@ __device__ __forceinline__ b2 lt(f2 a, f2 b) { return {a.x < b.x, a.y < b.y}; }
 __device__ __forceinline__ b2 le(f2 a, f2 b) { return {a.x <= b.x, a.y <= b.y}; }
 
 __device__ __forceinline__ f2 rsqrt(f2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
-__device__ __forceinline__ f2 rcp(f2 a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
+__device__ __forceinline__ f2 rcp(f2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
 __device__ __forceinline__ f2 sqrt_(f2 a) {
     return make_float2(Fm<float>::sqrt_(a.x), Fm<float>::sqrt_(a.y));
 }
@@ -251,8 +251,8 @@ __device__ __forceinline__ f2 volume_reduced(f2 d0, f2 il, f2 m1, f2 m2, f2 m3) 
 // Whole cells: two (n, V0) -> d0 in FP32 by the optimised SZ solution
 // (METHOD = M_SZ_OPT, in L1 units) or the analytic solution (M_ANALYTIC, in
 // the unit normal's units); with ROUNDTRIP, also the forward volume of the
-// returned d0 into *vrt.
-template <int METHOD, bool POLISH, bool ROUNDTRIP = false>
+// returned d0 into *vrt; with COUNT, invalid cells are added to `bad`.
+template <int METHOD, bool POLISH, bool ROUNDTRIP = false, bool COUNT = true>
 __device__ __forceinline__ f2 offset_pair(f2 nx, f2 ny, f2 nz, f2 V0, int& bad,
                                           f2* vrt = nullptr) {
     const f2 ax = make_float2(fabsf(nx.x), fabsf(nx.y));
@@ -267,7 +267,7 @@ __device__ __forceinline__ f2 offset_pair(f2 nx, f2 ny, f2 nz, f2 V0, int& bad,
     const f2 V = make_float2(fminf(V0.x, W.x), fminf(V0.y, W.y));
     const bool okx = V.x >= 0.0f && L.x > 0.0f && L.x <= 3.0f;
     const bool oky = V.y >= 0.0f && L.y > 0.0f && L.y <= 3.0f;
-    bad += (int)!okx + (int)!oky;
+    if (COUNT) bad += (int)!okx + (int)!oky;
     const f2 il = rcp(L);
     const f2 m1 = mul(n1, il), m3 = mul(n3, il);
     const f2 m2 = fmax0(sub(mk(1.0f), add(m1, m3)));

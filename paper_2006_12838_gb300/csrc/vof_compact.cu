@@ -4,22 +4,21 @@
 // Two or three launches, no atomics and no inter-block waiting, so the list
 // is in ascending cell order and identical run to run.  A tile is a run of
 // whole x-rows (about 8192 cells):
-//   1. k_compact_count : each block counts the interface cells of its tile
-//                        (one warp vote per 32 cells of a row), stores the
-//                        interface bits of every row and each row's offset
-//                        within the tile in the workspace, and the tile count.
+//   1. k_compact_count : each block counts the interface cells of its tile and,
+//                        with room in the workspace, stores every row's
+//                        interface bits and count.
 //   2. k_compact_scan  : one block turns the per-tile counts into exclusive
 //                        offsets (in place) and writes the total to *d_count;
 //                        only for fields of more than 4096 tiles (about 33 M
-//                        cells): below, each block of pass 3 sums the counts
-//                        of the tiles before its own, and the last writes the
-//                        total.
-//   3. k_compact_emit  : each warp writes the indices of its tile's non-empty
-//                        rows from the stored bits at the stored row offsets.
-//                        Without room for the bits (rows shorter than 32
-//                        cells) or without a workspace (the allocation-free
-//                        entry), k_compact_write recounts each row from the
-//                        field and scans the row counts itself.
+//                        cells): below, pass 3 sums the counts of the tiles
+//                        before each block, and the warp of the last tile
+//                        writes the total.
+//   3. k_compact_emit  : one warp per tile writes the indices of the tile's
+//                        non-empty rows from the stored bits.  Without room for
+//                        the bits (rows shorter than 32 cells) or without a
+//                        workspace (the allocation-free entry), k_compact_write
+//                        recounts each row from the field and scans the row
+//                        counts itself.
 // HBM roofline: 4 B per field cell read once + 1/8 B per cell of bits written
 // and read back for the non-empty rows, plus 4 B per interface cell written.
 #include <mutex>
@@ -90,257 +89,110 @@ __device__ __forceinline__ int row_bits(const float* __restrict__ row, int nx, b
 // unsigned compare of u - 1 decides it.
 __device__ __forceinline__ bool iface_bits(unsigned u) { return u - 1u < 0x3F7FFFFFu; }
 
-constexpr int CT_U = 8;                  // 32-cell words of a row loaded per warp and step
+// Vector path helpers: the 4-bit interface mask of the float4 at column x of
+// a row (boundary columns cleared), and the gather of the nibbles of 8 lanes
+// into the row's 32-bit word (x0 / 32 + lane / 8), stored by `fn`.
+__device__ __forceinline__ unsigned nib4(float4 v, int x, int nx) {
+    unsigned m = (unsigned)iface_bits(__float_as_uint(v.x)) |
+                 ((unsigned)iface_bits(__float_as_uint(v.y)) << 1) |
+                 ((unsigned)iface_bits(__float_as_uint(v.z)) << 2) |
+                 ((unsigned)iface_bits(__float_as_uint(v.w)) << 3);
+    if (x == 0) m &= ~1u;
+    if (x + 3 == nx - 1) m &= ~8u;
+    return x < nx ? m : 0u;
+}
 
-// Pass 1.  Warp w of a block takes rows w, w + 8, ... of the block's tile, two
-// rows at a time.  Each lane loads one float of every 32-cell word of the
-// row (coalesced 128-byte rows of loads, 8 words per step issued before any
-// is used), and one warp vote per word gives the word's interface bits in
-// cell order; the boundary columns x = 0 and x = nx - 1 are masked out of the
-// first and last word.  Rows with y or z on the field boundary are not read.
-// The row counts (warp-uniform popcounts) go to shared memory; warp 0 then
-// writes the tile's count and, with `row_off` given, each row's offset
-// within the tile (exclusive scan); with `bits` given each word is stored
-// (wpr = ceil(nx/32) words per row) so that pass 3 need not read the field
-// again.  Rows of a tile: R <= CT_MAX_ROWS.
+template <typename F>
+__device__ __forceinline__ void emit_nibbles(unsigned m, int x0, int nx, F fn) {
+    const int lane = threadIdx.x & 31;
+    unsigned w = m << (4 * (lane & 7));
+    w |= __shfl_xor_sync(0xffffffffu, w, 1);
+    w |= __shfl_xor_sync(0xffffffffu, w, 2);
+    w |= __shfl_xor_sync(0xffffffffu, w, 4);
+    if ((lane & 7) == 0 && x0 + 4 * lane < nx) fn((x0 >> 5) + (lane >> 3), w);
+}
+
+__device__ __forceinline__ float4 ld_row4(const float* __restrict__ row, bool ok, int x, int nx) {
+    return (ok && x < nx) ? __ldg(reinterpret_cast<const float4*>(row + x))
+                          : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// Pass 1.  Work is split by rows: warp w of a block takes rows w, w + 8, ...
+// of the block's tile.  A row's (y, z) is computed once per warp, rows on the
+// field boundary are skipped without reading them.  The per-tile count goes
+// to tile_count; with `bits` given, the row's interface bits are stored too
+// (wpr words per row), so that pass 3 need not read the field again.  In the
+// vector path a warp takes two rows at a time and issues the four 16-byte
+// loads per lane of 256 columns of both rows before using any of them, so
+// every lane keeps 64 bytes in flight (the pass is bound by load latency, not
+// by the compare work).
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
                 int* __restrict__ tile_count, unsigned* __restrict__ bits,
-                int* __restrict__ row_off) {
-    __shared__ int rc[CT_MAX_ROWS];
+                int* __restrict__ row_count, int vec) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpr = (nx + 31) >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
-    const int nr = (int)(rbeg + R < rows ? R : rows - rbeg);
-    const unsigned* __restrict__ u32 = reinterpret_cast<const unsigned*>(phi);
-    const int lastw = wpr - 1;
-    const unsigned lastmask = (1u << ((nx - 1) & 31)) - 1u;   // drops x = nx - 1 and beyond
+    const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
     auto interior = [&](int64_t r) {
         const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
         return y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2;
     };
-    for (int k = warp; k < nr; k += 2 * CT_WARPS) {
-        const int kb = k + CT_WARPS;
-        const bool hasb = kb < nr;
-        const int64_t ra = rbeg + k, rb = rbeg + (hasb ? kb : k);
-        const bool oka = interior(ra), okb = hasb && interior(rb);
-        const unsigned* rowa = u32 + ra * nx;
-        const unsigned* rowb = u32 + rb * nx;
-        int ca = 0, cb = 0;
-        for (int w0 = 0; w0 < wpr; w0 += CT_U) {
-            unsigned va[CT_U], vb[CT_U];
-#pragma unroll
-            for (int u = 0; u < CT_U; ++u) {
-                const int x = (w0 + u) * 32 + lane;
-                va[u] = (oka && x < nx) ? __ldg(rowa + x) : 0u;
-                vb[u] = (okb && x < nx) ? __ldg(rowb + x) : 0u;
+    int cnt = 0;
+    if (vec) {
+        for (int64_t ra = rbeg + warp; ra < rend; ra += 2 * CT_WARPS) {
+            const int64_t rb = ra + CT_WARPS;
+            const bool oka = interior(ra), hasb = rb < rend, okb = hasb && interior(rb);
+            const float* rowa = phi + ra * nx;
+            const float* rowb = phi + (hasb ? rb : ra) * nx;
+            unsigned* ba = bits ? bits + ra * wpr : nullptr;
+            unsigned* bb = (bits && hasb) ? bits + rb * wpr : nullptr;
+            int ca = 0, cb = 0;
+            for (int x0 = 0; x0 < nx; x0 += 256) {
+                const int xa = x0 + 4 * lane, xb = xa + 128;
+                const float4 a0 = ld_row4(rowa, oka, xa, nx), a1 = ld_row4(rowa, oka, xb, nx);
+                const float4 b0 = ld_row4(rowb, okb, xa, nx), b1 = ld_row4(rowb, okb, xb, nx);
+                const unsigned ma0 = oka ? nib4(a0, xa, nx) : 0u, ma1 = oka ? nib4(a1, xb, nx) : 0u;
+                const unsigned mb0 = okb ? nib4(b0, xa, nx) : 0u, mb1 = okb ? nib4(b1, xb, nx) : 0u;
+                ca += __popc(ma0) + __popc(ma1);
+                cb += __popc(mb0) + __popc(mb1);
+                emit_nibbles(ma0, x0, nx, [&](int w, unsigned b) { if (ba) ba[w] = b; });
+                emit_nibbles(ma1, x0 + 128, nx, [&](int w, unsigned b) { if (ba) ba[w] = b; });
+                emit_nibbles(mb0, x0, nx, [&](int w, unsigned b) { if (bb) bb[w] = b; });
+                emit_nibbles(mb1, x0 + 128, nx, [&](int w, unsigned b) { if (bb) bb[w] = b; });
             }
-            unsigned mya = 0u, myb = 0u;
-#pragma unroll
-            for (int u = 0; u < CT_U; ++u) {
-                const int w = w0 + u;
-                unsigned ma = __ballot_sync(0xffffffffu, iface_bits(va[u]));
-                unsigned mb = __ballot_sync(0xffffffffu, iface_bits(vb[u]));
-                const unsigned cm = (w == 0 ? ~1u : ~0u) & (w == lastw ? lastmask : ~0u);
-                ma &= cm;
-                mb &= cm;
-                ca += __popc(ma);
-                cb += __popc(mb);
-                mya = lane == u ? ma : mya;
-                myb = lane == u ? mb : myb;
+            ca = __reduce_add_sync(0xffffffffu, ca);
+            cb = __reduce_add_sync(0xffffffffu, cb);
+            if (row_count && lane == 0) {
+                row_count[ra] = ca;
+                if (hasb) row_count[rb] = cb;
             }
-            if (bits && lane < CT_U && w0 + lane < wpr) {
-                if (oka) bits[ra * wpr + w0 + lane] = mya;
-                if (okb) bits[rb * wpr + w0 + lane] = myb;
-            }
+            cnt += ca + cb;
         }
-        if (lane == 0) {
-            rc[k] = ca;
-            if (hasb) rc[kb] = cb;
+    } else {
+        for (int64_t r = rbeg + warp; r < rend; r += CT_WARPS) {
+            unsigned* rb = bits ? bits + r * wpr : nullptr;
+            if (!interior(r)) {
+                if (rb)
+                    for (int w = lane; w < wpr; w += 32) rb[w] = 0u;
+                if (row_count && lane == 0) row_count[r] = 0;
+                continue;
+            }
+            const int c = row_bits(phi + r * nx, nx, false, [&](int w, unsigned b) {
+                if (rb) rb[w] = b;
+            });
+            if (row_count && lane == 0) row_count[r] = c;
+            cnt += c;
         }
     }
+    __shared__ int ws[CT_WARPS];
+    if (lane == 0) ws[warp] = cnt;
     __syncthreads();
-    if (warp == 0) {
-        // exclusive scan of the nr row counts: each lane sums a run of rows
-        const int per = (nr + 31) >> 5;
-        const int k0 = lane * per, k1 = min(k0 + per, nr);
-        int sum = 0;
-        for (int k = k0; k < k1; ++k) sum += rc[k];
-        int incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (row_off) {
-            int run = incl - sum;
-            for (int k = k0; k < k1; ++k) {
-                row_off[rbeg + k] = run;
-                run += rc[k];
-            }
-        }
-        if (lane == 31) tile_count[blockIdx.x] = incl;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Pass 1, streaming form (rows of nx % 4 == 0 cells, at most CT_TILE cells,
-// 16-byte aligned field): a persistent grid of blocks, each taking tiles
-// t = blockIdx.x, + gridDim.x, ...  One thread streams every tile (whole rows,
-// contiguous in memory) into shared memory with a cp.async.bulk copy that
-// completes on the stage's mbarrier, CT_STAGES tiles ahead; all warps count
-// from shared memory (one float per lane and word, one vote per word), warp
-// 0 scans the row counts into row offsets.  Waits on the mbarriers are
-// bounded: after CT_WAIT_LIMIT polls a block marks the count of each tile it
-// has not finished with CT_FAILED (which the scan and the write pass turn
-// into *d_count = -1 and no list), waits (bounded) for its copies in flight
-// and leaves.
-// ---------------------------------------------------------------------------
-constexpr int CT_STAGES = 3;
-constexpr int CT_WAIT_LIMIT = 1 << 16;   // hardware-suspended polls (each up to a few us)
-constexpr int CT_FAILED = -2147483647 - 1;  // tile count of a tile whose copy never arrived
-
-constexpr int CT_STREAM_ROWS = CT_TILE / 4;   // rows of a tile when nx >= 4
-
-struct CountSmem {
-    float buf[CT_STAGES][CT_TILE];           // 3 x 32 KB
-    int rc[2][CT_STREAM_ROWS];               // row counts of two consecutive tiles
-    unsigned long long bar[CT_STAGES];
-};
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// One potentially blocking test of the phase `parity` of an mbarrier: the
-// thread is suspended in hardware until the phase completes or a
-// system-defined time limit passes (then false).
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-    return done != 0u;
-}
-
-// Bounded wait for the phase `parity` of an mbarrier to complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < CT_WAIT_LIMIT; ++it)
-        if (mbar_try(bar, parity)) return true;
-    return false;
-}
-
-// Thread 0: stream tile t (rows rbeg .. rbeg + nr - 1) into stage s.
-__device__ __forceinline__ void issue_tile(CountSmem& sm, int s, const float* phi, int nx,
-                                           int64_t rbeg, int nr) {
-    const uint32_t bytes = (uint32_t)nr * (uint32_t)nx * 4u;
-    const uint32_t bar = smem_addr(&sm.bar[s]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(smem_addr(sm.buf[s])), "l"(phi + rbeg * nx), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__global__ void __launch_bounds__(CT_THREADS)
-k_compact_count_stream(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
-                       int64_t ntiles, int* __restrict__ tile_count, unsigned* __restrict__ bits,
-                       int* __restrict__ row_off) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    CountSmem& sm = *reinterpret_cast<CountSmem*>(smem_raw);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wpr = (nx + 31) >> 5;
-    const int lastw = wpr - 1;
-    const unsigned lastmask = (1u << ((nx - 1) & 31)) - 1u;   // drops x = nx - 1
-    auto tile_rows_of = [&](int64_t t) {
-        const int64_t rb = t * R;
-        return (int)(rb + R < rows ? R : rows - rb);
-    };
     if (threadIdx.x == 0) {
-        for (int s = 0; s < CT_STAGES; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&sm.bar[s])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    // tiles of this block: t_k = blockIdx.x + k gridDim.x
-    const int64_t first = blockIdx.x, step = gridDim.x;
-    const int64_t nmine = first < ntiles ? (ntiles - first + step - 1) / step : 0;
-    if (threadIdx.x == 0)
-        for (int64_t k = 0; k < CT_STAGES && k < nmine; ++k) {
-            const int64_t t = first + k * step;
-            issue_tile(sm, (int)k, phi, nx, t * R, tile_rows_of(t));
-        }
-    int64_t k = 0;
-    bool ok = true;
-    for (; k < nmine; ++k) {
-        const int s = (int)(k % CT_STAGES);
-        const uint32_t parity = (uint32_t)((k / CT_STAGES) & 1);
-        const int64_t t = first + k * step;
-        const int64_t rbeg = t * R;
-        const int nr = tile_rows_of(t);
-        int* rc = sm.rc[k & 1];
-        // one thread waits for the copy, the barrier releases the others
-        if (threadIdx.x == 0) ok = mbar_wait(smem_addr(&sm.bar[s]), parity);
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        const float* tb = sm.buf[s];
-        for (int kk = warp; kk < nr; kk += CT_WARPS) {
-            const int64_t r = rbeg + kk;
-            const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-            int cnt = 0;
-            if (y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2) {
-                const unsigned* row = reinterpret_cast<const unsigned*>(tb + kk * nx);
-                for (int w0 = 0; w0 < wpr; w0 += 32) {
-                    unsigned mine = 0u;
-#pragma unroll 4
-                    for (int u = 0; u < 32 && w0 + u < wpr; ++u) {
-                        const int w = w0 + u;
-                        const int x = 32 * w + lane;
-                        const unsigned v = x < nx ? row[x] : 0u;
-                        unsigned b = __ballot_sync(0xffffffffu, iface_bits(v));
-                        b &= (w == 0 ? ~1u : ~0u) & (w == lastw ? lastmask : ~0u);
-                        cnt += __popc(b);
-                        mine = lane == u ? b : mine;
-                    }
-                    if (bits && w0 + lane < wpr) bits[r * wpr + w0 + lane] = mine;
-                }
-            }
-            if (lane == 0) rc[kk] = cnt;
-        }
-        __syncthreads();                              // stage s and rc[] complete
-        if (threadIdx.x == 0 && k + CT_STAGES < nmine) {
-            const int64_t tn = first + (k + CT_STAGES) * step;
-            issue_tile(sm, s, phi, nx, tn * R, tile_rows_of(tn));
-        }
-        if (warp == 0) {
-            // exclusive scan of the nr row counts: each lane sums a run of rows
-            const int per = (nr + 31) >> 5;
-            const int k0 = lane * per, k1 = min(k0 + per, nr);
-            int sum = 0;
-            for (int q = k0; q < k1; ++q) sum += rc[q];
-            int incl = sum;
+        int t = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            if (row_off) {
-                int run = incl - sum;
-                for (int q = k0; q < k1; ++q) {
-                    row_off[rbeg + q] = run;
-                    run += rc[q];
-                }
-            }
-            if (lane == 31) tile_count[t] = incl;
-        }
-    }
-    if (!ok && threadIdx.x == 0) {
-        // tiles k .. of this block were not counted; their copies (at most
-        // CT_STAGES, tiles k .. k + CT_STAGES - 1) may still be in flight
-        for (int64_t j = k; j < nmine; ++j) tile_count[first + j * step] = CT_FAILED;
-        for (int64_t j = k; j < nmine && j < k + CT_STAGES; ++j)
-            mbar_wait(smem_addr(&sm.bar[j % CT_STAGES]), (uint32_t)((j / CT_STAGES) & 1));
+        for (int w = 0; w < CT_WARPS; ++w) t += ws[w];
+        tile_count[blockIdx.x] = t;
     }
 }
 
@@ -350,15 +202,6 @@ __global__ void __launch_bounds__(1024)
 k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict__ d_count) {
     __shared__ long long wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // a tile that pass 1 could not count (CT_FAILED) voids the list: every
-    // offset becomes -1 and so does the count
-    int neg = 0;
-    for (int64_t i = threadIdx.x; i < ntiles; i += 1024) neg |= tile_count[i] < 0;
-    if (__syncthreads_or(neg)) {
-        for (int64_t i = threadIdx.x; i < ntiles; i += 1024) tile_count[i] = -1;
-        if (threadIdx.x == 0) *d_count = -1;
-        return;
-    }
     long long carry = 0;
     for (int64_t b0 = 0; b0 < ntiles; b0 += 4096) {
         const int64_t i0 = b0 + 4 * (int64_t)threadIdx.x;
@@ -529,30 +372,32 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     }
 }
 
-// Pass 3 with pass 1's interface bits and row offsets: no field reads, no
-// row scan.  The block's base is the sum of the counts of the tiles before
-// its own (fused: few tiles, every block sums them, the last block writes the
-// total) or the exclusive offset written by the scan launch (then the tile's
-// count is the next offset, or the total, minus its own).  Each warp takes
-// rows w, w + 8, ...; a non-empty row is written one 32-cell word per lane:
-// a warp prefix of the word popcounts gives each lane its first slot, and
-// the lane writes its word's cells in ascending order.
+// Pass 3 with pass 1's interface bits and row counts: one warp per tile, a
+// block of CT_WARPS consecutive tiles.  The tile's base is the sum of the
+// counts of the tiles before it (fused: few tiles; the block sums the counts
+// before its first tile, each warp adds those of the block's tiles before
+// its own, and the warp of the last tile writes the total) or the exclusive
+// offset written by the scan launch (then the tile's count is the next
+// offset, or the total, minus its own).  The warp takes its rows 32 at a time,
+// one row per lane: a warp scan of the row counts gives each row its first
+// slot, and each lane with a non-empty row writes that row's cells in
+// ascending order from its bit words.  One barrier, in the fused prefix.
 __global__ void __launch_bounds__(CT_THREADS)
-k_compact_emit(int nx, int R, int64_t rows, const int* __restrict__ tiles,
-               const unsigned* __restrict__ bits, const int* __restrict__ row_off,
+k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restrict__ tiles,
+               const unsigned* __restrict__ bits, const int* __restrict__ row_cnt,
                int32_t* __restrict__ idx, int64_t cap, int fused, int64_t* __restrict__ d_count) {
     __shared__ long long s_part[CT_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int t = blockIdx.x;
-    long long base;
-    int tcount;
+    const int64_t t0 = (int64_t)blockIdx.x * CT_WARPS;
+    const int64_t t = t0 + warp;
+    long long base = 0;
+    int tcount = 0;
     if (fused) {
-        // the counts of the tiles before this one (t <= 4096): four int4
+        // counts of the tiles before the block's first (t0 <= 4096): four int4
         // loads per thread at most, all issued before any is summed
         long long part = 0;
-        int neg = 0;
         const int4* t4 = reinterpret_cast<const int4*>(tiles);
-        const int n4 = t >> 2;
+        const int n4 = (int)(t0 >> 2);
         int4 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -560,93 +405,64 @@ k_compact_emit(int nx, int R, int64_t rows, const int* __restrict__ tiles,
             v[u] = q < n4 ? __ldg(t4 + q) : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            part += (long long)v[u].x + v[u].y + v[u].z + v[u].w;
-            neg |= (v[u].x | v[u].y | v[u].z | v[u].w) < 0;
-        }
-        if (threadIdx.x < (t & 3)) {
-            const int c = __ldg(tiles + 4 * n4 + threadIdx.x);
-            part += c;
-            neg |= c < 0;
-        }
+        for (int u = 0; u < 4; ++u) part += (long long)v[u].x + v[u].y + v[u].z + v[u].w;
+        if (threadIdx.x < (int)(t0 & 3)) part += __ldg(tiles + 4 * n4 + threadIdx.x);
+        // the block's own tiles: lane j < CT_WARPS holds tile t0 + j
+        const int cj = (lane < CT_WARPS && t0 + lane < ntiles) ? __ldg(tiles + t0 + lane) : 0;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if (lane == 0) s_part[warp] = part;
-        tcount = __ldg(tiles + t);
-        neg = __syncthreads_or(neg | (tcount < 0));
-        base = 0;
+        __syncthreads();
 #pragma unroll
         for (int w = 0; w < CT_WARPS; ++w) base += s_part[w];
-        if (t == (int)gridDim.x - 1 && threadIdx.x == 0) *d_count = neg ? -1 : base + tcount;
-        if (neg) return;                            // a tile before (or this one) was not counted
+        base += __reduce_add_sync(0xffffffffu, lane < warp ? cj : 0);
+        tcount = __shfl_sync(0xffffffffu, cj, warp);
+        if (t == ntiles - 1 && lane == 0) *d_count = base + tcount;
     } else {
+        if (t >= ntiles) return;
         base = __ldg(tiles + t);
-        if (base < 0) return;                       // the scan found an uncounted tile
-        const long long next = t + 1 < (int)gridDim.x ? (long long)__ldg(tiles + t + 1) : *d_count;
+        const long long next = t + 1 < ntiles ? (long long)__ldg(tiles + t + 1) : *d_count;
         tcount = (int)(next - base);
     }
-    const int64_t rbeg = (int64_t)t * R;
+    if (t >= ntiles || tcount == 0) return;
+    const int64_t rbeg = t * R;
     const int nr = (int)(rbeg + R < rows ? R : rows - rbeg);
     const int wpr = (nx + 31) >> 5;
-    for (int k = warp; k < nr; k += CT_WARPS) {
-        const int off = __ldg(row_off + rbeg + k);
-        const int end = k + 1 < nr ? __ldg(row_off + rbeg + k + 1) : tcount;
-        if (end == off) continue;                   // most rows hold no interface cell
-        const int64_t r = rbeg + k;
-        int64_t pos = base + off;
-        for (int w0 = 0; w0 < wpr; w0 += 32) {
-            const int w = w0 + lane;
-            unsigned b = w < wpr ? __ldg(bits + r * wpr + w) : 0u;
-            const int c = __popc(b);
-            int incl = c;
+    int rowbase = 0;
+    for (int k0 = 0; k0 < nr; k0 += 32) {
+        // one row per lane: its count, its offset in the tile (warp scan),
+        // then the lane writes the row's cells from its words (loaded four
+        // at a time), so that all non-empty rows of the tile proceed at once
+        const int k = k0 + lane;
+        const int c = k < nr ? __ldg(row_cnt + rbeg + k) : 0;
+        int incl = c;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
-            }
-            int64_t p = pos + incl - c;
-            const int64_t cell0 = r * nx + 32 * (int64_t)w;
-            while (b) {
-                const int j = __ffs(b) - 1;
-                b &= b - 1u;
-                if (p < cap) idx[p] = (int32_t)(cell0 + j);
-                ++p;
-            }
-            pos += __shfl_sync(0xffffffffu, incl, 31);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
-    }
-}
-
-// Grid of the streaming count pass: resident blocks (shared memory allows
-// two per SM) times the SMs, at most one block per tile; 0 when the kernel
-// cannot be given its shared memory.  The attribute is set once per device.
-static int count_stream_grid(int64_t nt) {
-    static std::mutex mu;
-    static int per_sm[256] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 0;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (per_sm[dev] == 0) {
-            const void* k = reinterpret_cast<const void*>(&k_compact_count_stream);
-            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(CountSmem)) != cudaSuccess) {
-                cudaGetLastError();
-                per_sm[dev] = -1;
-            } else {
-                int b = 0;
-                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, CT_THREADS, sizeof(CountSmem)) !=
-                        cudaSuccess || b < 1) {
-                    cudaGetLastError();
-                    b = -1;
+        if (c > 0) {
+            const int64_t r = rbeg + k;
+            const unsigned* rb = bits + r * wpr;
+            int64_t p = base + rowbase + incl - c;
+            for (int w0 = 0; w0 < wpr; w0 += 4) {
+                unsigned b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) b[u] = w0 + u < wpr ? __ldg(rb + w0 + u) : 0u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t cell0 = r * nx + 32 * (int64_t)(w0 + u);
+                    while (b[u]) {
+                        const int q = __ffs(b[u]) - 1;
+                        b[u] &= b[u] - 1u;
+                        if (p < cap) idx[p] = (int32_t)(cell0 + q);
+                        ++p;
+                    }
                 }
-                per_sm[dev] = b;
             }
         }
-        if (per_sm[dev] < 0) return 0;
+        rowbase += __shfl_sync(0xffffffffu, incl, 31);
     }
-    const int64_t g = (int64_t)sm_count() * per_sm[dev];
-    return (int)(g < nt ? g : nt);
 }
 
 // Tiles of a field: whole x-rows, tile_rows(nx) per tile.
@@ -714,23 +530,16 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
         rowc = reinterpret_cast<int*>(reinterpret_cast<char*>(workspace) + tile_bytes + bits_bytes);
     }
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
-    // the streaming count pass needs whole rows of 16-byte multiples that fit
-    // one shared-memory stage, and the bits and row offsets in the workspace
-    const int stream_blocks = (vec && nx <= CT_TILE && bits) ? count_stream_grid(nt) : 0;
-    if (stream_blocks > 0) {
-        k_compact_count_stream<<<(unsigned)stream_blocks, CT_THREADS, sizeof(CountSmem), s>>>(
-            phi, nx, ny, nz, R, rows, nt, tiles, bits, rowc);
-    } else {
-        k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits,
-                                                            rowc);
-    }
-    // up to CT_FUSED_SCAN_TILES tiles each block of pass 3 sums the counts of
-    // the tiles before it (at most that many L2 reads per block); beyond, one
+    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, rowc,
+                                                        vec);
+    // up to CT_FUSED_SCAN_TILES tiles pass 3 sums the counts of the tiles
+    // before each block (at most that many L2 reads per block); beyond, one
     // block scans them first
     const bool fused = nt <= CT_FUSED_SCAN_TILES;
     if (!fused) k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
     if (bits) {
-        k_compact_emit<<<(unsigned)nt, CT_THREADS, 0, s>>>(nx, R, rows, tiles, bits, rowc, idx,
+        const int64_t nb = (nt + CT_WARPS - 1) / CT_WARPS;
+        k_compact_emit<<<(unsigned)nb, CT_THREADS, 0, s>>>(nx, R, rows, nt, tiles, bits, rowc, idx,
                                                            idx_capacity, fused ? 1 : 0, d_count);
     } else {
         k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
@@ -815,7 +624,7 @@ extern "C" plic_status vof_interface_compact_noalloc(const float* phi, int nx, i
     // the built-in scratch holds the tile counts only; pass 3 re-reads the field
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
     k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
-                                                        nullptr);
+                                                        nullptr, vec);
     const bool fused = nt <= CT_FUSED_SCAN_TILES;
     if (!fused) k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
     k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,

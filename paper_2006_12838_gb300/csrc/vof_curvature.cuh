@@ -130,7 +130,7 @@ template <> struct FitReal<FIT_FP32> {
     static __device__ __forceinline__ R mul(R a, R b) { return a * b; }
     // MUFU reciprocal and a multiply (2 ulp): the divisors are the LDL^T pivots,
     // positive and far inside the normal range
-    static __device__ __forceinline__ R div(R a, R b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ R div(R a, R b) { return a * rcp_approx(b); }
     static __device__ __forceinline__ float tof(R a) { return a; }
     static __device__ __forceinline__ bool gt(R a, R b) { return a > b; }
 };
@@ -315,16 +315,16 @@ struct CellPlic<M_SZ_OPT> {
         L = ax + ay + az;
         // MUFU reciprocals (no IEEE division): the thresholds only choose
         // between case formulas that agree at the case boundaries
-        const float il = __fdividef(1.0f, L);
+        const float il = rcp_approx(L);
         m1 = fminf(fminf(ax, ay), az) * il;
         m3 = fmaxf(fmaxf(ax, ay), az) * il;
         m2 = fmaxf(1.0f - (m1 + m3), 0.0f);
         n12 = m1 + m2;
         const float m1m2 = m1 * m2, sq1 = m1 * m1;
         const float k23 = 6.0f * m2 * m3;
-        const float rk = k23 > 0.0f ? __fdividef(1.0f, k23) : 0.0f;
-        inv1 = m1 > 0.0f ? __fdividef(1.0f, m1) : 0.0f;
-        V5 = 0.5f * n12 * __fdividef(1.0f, m3);                  // case (5): V >= V5
+        const float rk = k23 > 0.0f ? rcp_approx(k23) : 0.0f;
+        inv1 = m1 > 0.0f ? rcp_approx(m1) : 0.0f;
+        V5 = 0.5f * n12 * rcp_approx(m3);                  // case (5): V >= V5
         V1 = sq1 * rk;                                           // case (1): V < V1
         V2 = (sq1 - 3.0f * m2 * (m1 - m2)) * rk;                 // case (2): V < V2
         const float num3 = m3 * m3 * (3.0f * n12 - m3) + sq1 * (m1 - 3.0f * m3) + m2 * m2 * (m2 - 3.0f * m3);
@@ -358,7 +358,7 @@ struct CellPlic<M_SZ_OPT> {
         const float e22 = e2 * e2, e33 = e3 * e3;
         const float g = fmaf(3.0f * d, d - m1, m1 * m1) - fmaf(e22, e2, e33 * e3) * inv1 - k6 * V;
         const float gp = fmaf(6.0f, d, -3.0f * m1) - 3.0f * (e22 + e33) * inv1;
-        d = d - __fdividef(g, gp);
+        d = d - g * rcp_approx(gp);
         d = c1 ? d1 : d;
         d = c2 ? d2 : d;
         d = c5 ? d5 : d;
