@@ -134,9 +134,10 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     const int wpr = (nx + 31) >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
     const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
+    // rows < 2^31 (fields of at most 2^31 - 1 cells): 32-bit division
     auto interior = [&](int64_t r) {
-        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-        return y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2;
+        const unsigned z = (unsigned)r / (unsigned)ny, y = (unsigned)r - z * (unsigned)ny;
+        return y >= 1u && y + 2u <= (unsigned)ny && z >= 1u && z + 2u <= (unsigned)nz;
     };
     int cnt = 0;
     if (vec) {
@@ -285,8 +286,8 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
             }
             cnt = __reduce_add_sync(0xffffffffu, cnt);
         } else {
-            const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-            if (y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2) {
+            const unsigned z = (unsigned)r / (unsigned)ny, y = (unsigned)r - z * (unsigned)ny;
+            if (y >= 1u && y + 2u <= (unsigned)ny && z >= 1u && z + 2u <= (unsigned)nz) {
                 cnt = row_bits(phi + r * nx, nx, vec != 0, [&](int w, unsigned b) {
                     if (in_smem) bal[k * wpr + w] = b;
                 });
@@ -344,8 +345,8 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
                 } else {
                     // recompute this word (rare: tiles of very long rows)
                     const float* row = phi + r * nx;
-                    const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
-                    if (y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2)
+                    const unsigned z = (unsigned)r / (unsigned)ny, y = (unsigned)r - z * (unsigned)ny;
+                    if (y >= 1u && y + 2u <= (unsigned)ny && z >= 1u && z + 2u <= (unsigned)nz)
                         for (int j = 0; j < 32; ++j) {
                             const int x = 32 * w + j;
                             if (x >= 1 && x <= nx - 2 && iface(__ldg(row + x))) b |= 1u << j;

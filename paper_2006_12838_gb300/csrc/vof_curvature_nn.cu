@@ -39,7 +39,9 @@ k_vof_curvature_nn(const float* __restrict__ phi, int nx, int ny, int nz,
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lim;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = __ldg(idx + k);
-        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / nxy);
+        // 32-bit arithmetic: list entries are int32 cell indices
+        const unsigned cu = (unsigned)c, zu = cu / (unsigned)nxy, ru = cu - zu * (unsigned)nxy;
+        const int z = (int)zu, y = (int)(ru / (unsigned)nx), x = (int)(ru - (unsigned)y * (unsigned)nx);
         float nx_, ny_, nz_;
         if (!stencil_normal(phi, c, nx, nxy, cm, nx_, ny_, nz_)) { out[k] = 0.0f; continue; }
         // frame (Sec. 4.2)
