@@ -964,7 +964,7 @@ def run_case(args):
         vr = torch.empty_like(t[0])
         for _ in range(args.steps):
             if args.case == "offset":
-                plic.offset(*t, method="sz_opt", precision="fp32p", out=d0)
+                plic.offset(*t, method=args.method, precision=args.precision, out=d0)
             elif args.case == "roundtrip":
                 plic.offset_roundtrip(*t, method="sz_opt", precision="fp32p", out=d0, out_rt=vr)
             else:
@@ -980,6 +980,13 @@ def run_case(args):
             idx, cnt = plic.interface_compact(phi)
             k = int(cnt.item())
             plic.curvature(phi, idx[:k].contiguous())
+    elif args.case == "compact":
+        # the 256^3 curvature field tiled to 256 x 512 x 512 (256 MiB, twice L2)
+        phi, _ = synth.curvature_field(seed=3, edge=256, device=dev)
+        big = phi.repeat(1, 2, 2)
+        idx = torch.empty(big.numel() // 8, dtype=torch.int32, device=dev)
+        for _ in range(args.steps):
+            plic.interface_compact(big, idx=idx)
     elif args.case == "curv_bwd":
         phi, w = synth.adjoint_field(seed=4, device=dev)
         idx, cnt = plic.interface_compact(phi)
@@ -1049,9 +1056,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default=None,
                     help="profiling case: run only one kernel on --cells cells "
-                         "(offset | roundtrip | volume | offset_fp64 | offset_fp64r | curvature | curv_bwd | "
-                         "batched)")
+                         "(offset | roundtrip | volume | offset_fp64 | offset_fp64r | curvature | compact | "
+                         "curv_bwd | batched)")
     ap.add_argument("--cells", type=int, default=1 << 24)
+    ap.add_argument("--method", default="sz_opt", help="solver of --case offset")
+    ap.add_argument("--precision", default="fp32p", help="precision of --case offset")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

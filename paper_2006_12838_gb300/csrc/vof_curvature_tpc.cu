@@ -162,14 +162,21 @@ __device__ __forceinline__ float tpc_kappa(const float* __restrict__ phi, int nx
             const float y = w * (qx[j] * byx + qy[j] * byy + qz[j] * byz);
             const float zz = w * z[j];
             const float Q[5] = {x * x, y * y, x * y, x, y};
+            // the 12 distinct moments of the normal matrix: the entries
+            // (xy, xy), (xy, x), (xy, y) equal (x^2, y^2), (x^2, y), (y^2, x)
+            // and are copied after the loop
 #pragma unroll
             for (int a = 0; a < 5; ++a) {
 #pragma unroll
-                for (int b = a; b < 5; ++b) rec[uidx(a, b)] = fmaf(Q[a], Q[b], rec[uidx(a, b)]);
+                for (int b = a; b < 5; ++b)
+                    if (a != 2) rec[uidx(a, b)] = fmaf(Q[a], Q[b], rec[uidx(a, b)]);
                 rec[15 + a] = fmaf(zz, Q[a], rec[15 + a]);
             }
         }
     }
+    rec[uidx(2, 2)] = rec[uidx(0, 1)];
+    rec[uidx(2, 3)] = rec[uidx(0, 4)];
+    rec[uidx(2, 4)] = rec[uidx(1, 3)];
     // 5. fit and Eq. 42
     return co_solve<FIT>(rec, flags);
 }

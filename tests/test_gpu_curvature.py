@@ -46,7 +46,12 @@ def _compact(dev, p):
 
 @pytest.mark.parametrize("shape", [(96, 96, 96), (29, 41, 37), (3, 3, 3), (5, 70, 13), (7, 9, 100),
                                    (5, 6, 260), (6, 5, 4), (4, 33, 8), (3, 17, 516),
-                                   (520, 256, 256)])   # > 4096 tiles: the separate scan launch
+                                   # rows of 32 cells (one bit word), of 8192 cells (one row
+                                   # per tile) and beyond, a 44-cell row (two words)
+                                   (6, 7, 32), (3, 4, 8192), (3, 3, 8196), (3, 40, 44),
+                                   # > 4096 tiles: the separate scan launch, with the vector
+                                   # loads and with the scalar ones (odd nx)
+                                   (520, 256, 256), (500, 257, 257)])
 def test_compaction_bit_exact(dev, orc, shape):
     rng = np.random.default_rng(sum(shape))
     p = rng.random(shape).astype(np.float32)
