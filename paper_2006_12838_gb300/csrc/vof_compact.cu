@@ -5,8 +5,8 @@
 // is in ascending cell order and identical run to run.  A tile is a run of
 // whole x-rows (about 8192 cells):
 //   1. k_compact_count : each block counts the interface cells of its tile and,
-//                        with room in the workspace, stores every row's
-//                        interface bits and count.
+//                        with room in the workspace, stores the tile's
+//                        interface bits (one word per 32 cells of a row).
 //   2. k_compact_scan  : one block turns the per-tile counts into exclusive
 //                        offsets (in place) and writes the total to *d_count;
 //                        only for fields of more than 4096 tiles (about 33 M
@@ -14,13 +14,14 @@
 //                        before each block, and the warp of the last tile
 //                        writes the total.
 //   3. k_compact_emit  : one warp per tile writes the indices of the tile's
-//                        non-empty rows from the stored bits.  Without room for
-//                        the bits (rows shorter than 32 cells) or without a
-//                        workspace (the allocation-free entry), k_compact_write
-//                        recounts each row from the field and scans the row
-//                        counts itself.
+//                        cells from the stored bits.  Without room for the bits
+//                        (rows shorter than 32 cells) or without a workspace
+//                        (the allocation-free entry), k_compact_write recounts
+//                        each row from the field and scans the row counts
+//                        itself.
 // HBM roofline: 4 B per field cell read once + 1/8 B per cell of bits written
-// and read back for the non-empty rows, plus 4 B per interface cell written.
+// and read back for the tiles holding interface cells, plus 4 B per interface
+// cell written.
 #include <mutex>
 #include <stdio.h>
 
@@ -128,8 +129,7 @@ __device__ __forceinline__ float4 ld_row4(const float* __restrict__ row, bool ok
 // by the compare work).
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
-                int* __restrict__ tile_count, unsigned* __restrict__ bits,
-                int* __restrict__ row_count, int vec) {
+                int* __restrict__ tile_count, unsigned* __restrict__ bits, int vec) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpr = (nx + 31) >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
@@ -162,27 +162,20 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
                 emit_nibbles(mb0, x0, nx, [&](int w, unsigned b) { if (bb) bb[w] = b; });
                 emit_nibbles(mb1, x0 + 128, nx, [&](int w, unsigned b) { if (bb) bb[w] = b; });
             }
-            ca = __reduce_add_sync(0xffffffffu, ca);
-            cb = __reduce_add_sync(0xffffffffu, cb);
-            if (row_count && lane == 0) {
-                row_count[ra] = ca;
-                if (hasb) row_count[rb] = cb;
-            }
-            cnt += ca + cb;
+            cnt += ca + cb;                       // the lane's share
         }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
     } else {
         for (int64_t r = rbeg + warp; r < rend; r += CT_WARPS) {
             unsigned* rb = bits ? bits + r * wpr : nullptr;
             if (!interior(r)) {
                 if (rb)
                     for (int w = lane; w < wpr; w += 32) rb[w] = 0u;
-                if (row_count && lane == 0) row_count[r] = 0;
                 continue;
             }
             const int c = row_bits(phi + r * nx, nx, false, [&](int w, unsigned b) {
                 if (rb) rb[w] = b;
             });
-            if (row_count && lane == 0) row_count[r] = c;
             cnt += c;
         }
     }
@@ -240,14 +233,12 @@ k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict
     if (threadIdx.x == 0) *d_count = carry;
 }
 
-// Pass 3: each warp takes its rows' interface bits (from pass 1's bit array,
-// or recomputed from the field when none was kept), the block scans the row
-// counts, and every warp writes its rows' indices at the row offsets, in
-// ascending cell order.
+// Pass 3 without stored bits: each warp recomputes its rows' interface bits
+// from the field, the block scans the row counts, and every warp writes its
+// rows' indices at the row offsets, in ascending cell order.
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
-                const int* __restrict__ tile_offset, const unsigned* __restrict__ bits,
-                const int* __restrict__ row_count, int32_t* __restrict__ idx, int64_t cap, int vec,
+                const int* __restrict__ tile_offset, int32_t* __restrict__ idx, int64_t cap, int vec,
                 int64_t* __restrict__ d_count) {
     __shared__ unsigned bal[CT_MAX_WORDS];
     __shared__ int rowoff[CT_MAX_ROWS + 1];
@@ -268,32 +259,19 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     const int64_t rend = rbeg + R < rows ? rbeg + R : rows;
     const int nr = (int)(rend - rbeg);
     const int wpr = (nx + 31) >> 5;                 // words per row
-    // with pass 1's row counts the rows need not be recounted here, and their
-    // bits are read from global memory only for the non-empty rows
-    const bool in_smem = !row_count && (int64_t)nr * wpr <= CT_MAX_WORDS;
-    if (row_count) {
-        for (int k = threadIdx.x; k < nr; k += CT_THREADS) rowoff[k] = rowcnt[k] = __ldg(row_count + rbeg + k);
-    }
-    for (int k = warp; k < (row_count ? 0 : nr); k += CT_WARPS) {
+    // the tile's bits are kept in shared memory when they fit, else each
+    // word is recomputed when it is written
+    const bool in_smem = (int64_t)nr * wpr <= CT_MAX_WORDS;
+    for (int k = warp; k < nr; k += CT_WARPS) {
         const int64_t r = rbeg + k;
         int cnt = 0;
-        if (bits) {
-            const unsigned* rb = bits + r * wpr;
-            for (int w = lane; w < wpr; w += 32) {
-                const unsigned b = __ldg(rb + w);
-                cnt += __popc(b);
+        const unsigned z = (unsigned)r / (unsigned)ny, y = (unsigned)r - z * (unsigned)ny;
+        if (y >= 1u && y + 2u <= (unsigned)ny && z >= 1u && z + 2u <= (unsigned)nz) {
+            cnt = row_bits(phi + r * nx, nx, vec != 0, [&](int w, unsigned b) {
                 if (in_smem) bal[k * wpr + w] = b;
-            }
-            cnt = __reduce_add_sync(0xffffffffu, cnt);
-        } else {
-            const unsigned z = (unsigned)r / (unsigned)ny, y = (unsigned)r - z * (unsigned)ny;
-            if (y >= 1u && y + 2u <= (unsigned)ny && z >= 1u && z + 2u <= (unsigned)nz) {
-                cnt = row_bits(phi + r * nx, nx, vec != 0, [&](int w, unsigned b) {
-                    if (in_smem) bal[k * wpr + w] = b;
-                });
-            } else if (in_smem) {
-                for (int w = lane; w < wpr; w += 32) bal[k * wpr + w] = 0u;
-            }
+            });
+        } else if (in_smem) {
+            for (int w = lane; w < wpr; w += 32) bal[k * wpr + w] = 0u;
         }
         if (lane == 0) rowoff[k] = rowcnt[k] = cnt;
     }
@@ -340,8 +318,6 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
             if (w < wpr) {
                 if (in_smem) {
                     b = bal[k * wpr + w];
-                } else if (bits) {
-                    b = __ldg(bits + r * wpr + w);
                 } else {
                     // recompute this word (rare: tiles of very long rows)
                     const float* row = phi + r * nx;
@@ -373,20 +349,21 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     }
 }
 
-// Pass 3 with pass 1's interface bits and row counts: one warp per tile, a
-// block of CT_WARPS consecutive tiles.  The tile's base is the sum of the
-// counts of the tiles before it (fused: few tiles; the block sums the counts
-// before its first tile, each warp adds those of the block's tiles before
-// its own, and the warp of the last tile writes the total) or the exclusive
-// offset written by the scan launch (then the tile's count is the next
-// offset, or the total, minus its own).  The warp takes its rows 32 at a time,
-// one row per lane: a warp scan of the row counts gives each row its first
-// slot, and each lane with a non-empty row writes that row's cells in
-// ascending order from its bit words.  One barrier, in the fused prefix.
+// Pass 3 with pass 1's interface bits: one warp per tile, a block of CT_WARPS
+// consecutive tiles.  The tile's base is the sum of the counts of the tiles
+// before it (fused: few tiles; the block sums the counts before its first
+// tile, each warp adds those of the block's tiles before its own, and the
+// warp of the last tile writes the total) or the exclusive offset written by
+// the scan launch (then the tile's count is the next offset, or the total,
+// minus its own).  A tile's words are contiguous (its rows, wpr words each):
+// each lane takes 8 consecutive words (two int4 loads when aligned), one warp
+// scan of the lane counts gives each lane its first slot, and the lane writes
+// its words' cells in ascending order.  One dependent load per tile (the
+// words, issued with the tile counts) and one barrier, in the fused prefix.
 __global__ void __launch_bounds__(CT_THREADS)
 k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restrict__ tiles,
-               const unsigned* __restrict__ bits, const int* __restrict__ row_cnt,
-               int32_t* __restrict__ idx, int64_t cap, int fused, int64_t* __restrict__ d_count) {
+               const unsigned* __restrict__ bits, int32_t* __restrict__ idx, int64_t cap,
+               int fused, int64_t* __restrict__ d_count) {
     __shared__ long long s_part[CT_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t t0 = (int64_t)blockIdx.x * CT_WARPS;
@@ -394,8 +371,6 @@ k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restric
     long long base = 0;
     int tcount = 0;
     if (fused) {
-        // counts of the tiles before the block's first (t0 <= 4096): four int4
-        // loads per thread at most, all issued before any is summed
         long long part = 0;
         const int4* t4 = reinterpret_cast<const int4*>(tiles);
         const int n4 = (int)(t0 >> 2);
@@ -408,7 +383,6 @@ k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restric
 #pragma unroll
         for (int u = 0; u < 4; ++u) part += (long long)v[u].x + v[u].y + v[u].z + v[u].w;
         if (threadIdx.x < (int)(t0 & 3)) part += __ldg(tiles + 4 * n4 + threadIdx.x);
-        // the block's own tiles: lane j < CT_WARPS holds tile t0 + j
         const int cj = (lane < CT_WARPS && t0 + lane < ntiles) ? __ldg(tiles + t0 + lane) : 0;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -428,41 +402,49 @@ k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restric
     if (t >= ntiles || tcount == 0) return;
     const int64_t rbeg = t * R;
     const int nr = (int)(rbeg + R < rows ? R : rows - rbeg);
-    const int wpr = (nx + 31) >> 5;
-    int rowbase = 0;
-    for (int k0 = 0; k0 < nr; k0 += 32) {
-        // one row per lane: its count, its offset in the tile (warp scan),
-        // then the lane writes the row's cells from its words (loaded four
-        // at a time), so that all non-empty rows of the tile proceed at once
-        const int k = k0 + lane;
-        const int c = k < nr ? __ldg(row_cnt + rbeg + k) : 0;
+    const unsigned wpr = ((unsigned)nx + 31u) >> 5;
+    const int nw = nr * (int)wpr;
+    const unsigned* tb = bits + rbeg * (int64_t)wpr;
+    const bool al = ((rbeg * (int64_t)wpr) & 3) == 0;
+    const unsigned invw = wpr > 1u ? 0xFFFFFFFFu / wpr + 1u : 0u;
+    long long pos = base;
+    for (int w0 = 0; w0 < nw; w0 += 256) {
+        const int wl = w0 + 8 * lane;
+        unsigned b[8];
+        if (al && wl + 8 <= nw) {
+            const int4 x = __ldg(reinterpret_cast<const int4*>(tb + wl));
+            const int4 y = __ldg(reinterpret_cast<const int4*>(tb + wl + 4));
+            b[0] = x.x; b[1] = x.y; b[2] = x.z; b[3] = x.w;
+            b[4] = y.x; b[5] = y.y; b[6] = y.z; b[7] = y.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) b[k] = wl + k < nw ? __ldg(tb + wl + k) : 0u;
+        }
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c += __popc(b[k]);
         int incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += u;
         }
-        if (c > 0) {
-            const int64_t r = rbeg + k;
-            const unsigned* rb = bits + r * wpr;
-            int64_t p = base + rowbase + incl - c;
-            for (int w0 = 0; w0 < wpr; w0 += 4) {
-                unsigned b[4];
+        long long p = pos + incl - c;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) b[u] = w0 + u < wpr ? __ldg(rb + w0 + u) : 0u;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int64_t cell0 = r * nx + 32 * (int64_t)(w0 + u);
-                    while (b[u]) {
-                        const int q = __ffs(b[u]) - 1;
-                        b[u] &= b[u] - 1u;
-                        if (p < cap) idx[p] = (int32_t)(cell0 + q);
-                        ++p;
-                    }
-                }
+        for (int k = 0; k < 8; ++k) {
+            unsigned bb = b[k];
+            if (!bb) continue;
+            const unsigned w = (unsigned)(wl + k);
+            const unsigned r = wpr > 1u ? __umulhi(w, invw) : w, wr = w - r * wpr;
+            const int64_t cell0 = (rbeg + r) * (int64_t)nx + 32 * (int64_t)wr;
+            while (bb) {
+                const int q = __ffs(bb) - 1;
+                bb &= bb - 1u;
+                if (p < cap) idx[p] = (int32_t)(cell0 + q);
+                ++p;
             }
         }
-        rowbase += __shfl_sync(0xffffffffu, incl, 31);
+        pos += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 
@@ -482,12 +464,10 @@ extern "C" size_t plic_workspace_bytes(int op, int64_t arg) {
             // field of arg cells has at most 2 arg / CT_TILE + 1 tiles; interface
             // bits: one word per 32 cells of each row, at most arg / 16 words
             // for rows of >= 32 cells (shorter rows keep no bits)
-            // row counts: one int per row of >= 32 cells, at most arg / 32 + 1
             const int64_t t = (arg + plic::CT_TILE - 1) / plic::CT_TILE * 2 + 1;
             const size_t a = ((size_t)t * sizeof(int) + 255) / 256 * 256;
             const size_t b = ((size_t)(arg / 16 + 1) * sizeof(unsigned) + 255) / 256 * 256;
-            const size_t c = ((size_t)(arg / 32 + 1) * sizeof(int) + 255) / 256 * 256;
-            return a + b + c;
+            return a + b;
         }
         case PLIC_WS_BATCHED: {
             // descriptor table + per-field cell prefix + the ticket counter
@@ -525,14 +505,10 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
     const int64_t words = rows * ((nx + 31) / 32);
     const size_t bits_bytes = ((size_t)words * sizeof(unsigned) + 255) / 256 * 256;
     unsigned* bits = nullptr;
-    int* rowc = nullptr;
-    if (nx >= 32 && tile_bytes + bits_bytes + (size_t)rows * sizeof(int) <= ws_bytes) {
+    if (nx >= 32 && tile_bytes + bits_bytes <= ws_bytes)
         bits = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + tile_bytes);
-        rowc = reinterpret_cast<int*>(reinterpret_cast<char*>(workspace) + tile_bytes + bits_bytes);
-    }
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
-    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, rowc,
-                                                        vec);
+    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, vec);
     // up to CT_FUSED_SCAN_TILES tiles pass 3 sums the counts of the tiles
     // before each block (at most that many L2 reads per block); beyond, one
     // block scans them first
@@ -540,12 +516,11 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
     if (!fused) k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
     if (bits) {
         const int64_t nb = (nt + CT_WARPS - 1) / CT_WARPS;
-        k_compact_emit<<<(unsigned)nb, CT_THREADS, 0, s>>>(nx, R, rows, nt, tiles, bits, rowc, idx,
+        k_compact_emit<<<(unsigned)nb, CT_THREADS, 0, s>>>(nx, R, rows, nt, tiles, bits, idx,
                                                            idx_capacity, fused ? 1 : 0, d_count);
     } else {
-        k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
-                                                            nullptr, idx, idx_capacity, vec,
-                                                            fused ? d_count : nullptr);
+        k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, idx,
+                                                            idx_capacity, vec, fused ? d_count : nullptr);
     }
     return check_launch("vof_interface_compact");
 }
@@ -624,12 +599,10 @@ extern "C" plic_status vof_interface_compact_noalloc(const float* phi, int nx, i
     }
     // the built-in scratch holds the tile counts only; pass 3 re-reads the field
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
-    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
-                                                        nullptr, vec);
+    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr, vec);
     const bool fused = nt <= CT_FUSED_SCAN_TILES;
     if (!fused) k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
-    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr,
-                                                        nullptr, idx, idx_capacity, vec,
-                                                        fused ? d_count : nullptr);
+    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, idx,
+                                                        idx_capacity, vec, fused ? d_count : nullptr);
     return check_launch("vof_interface_compact_noalloc");
 }

@@ -80,10 +80,10 @@ def test_status_strings_and_version(lib):
 def test_workspace_sizes(lib):
     # one int per tile (tiles of whole rows, >= 8192 cells each) + 1 bit per cell, 256-byte rounded
     r256 = lambda b: (b + 255) // 256 * 256  # noqa: E731
-    # tile counts + interface bits + row counts
+    # tile counts + interface bits
     assert lib.plic_workspace_bytes(plic.WS_COMPACT, 256 ** 3) == (
-        r256((2 * 2048 + 1) * 4) + r256((256 ** 3 // 16 + 1) * 4) + r256((256 ** 3 // 32 + 1) * 4))
-    assert lib.plic_workspace_bytes(plic.WS_COMPACT, 1) == 768
+        r256((2 * 2048 + 1) * 4) + r256((256 ** 3 // 16 + 1) * 4))
+    assert lib.plic_workspace_bytes(plic.WS_COMPACT, 1) == 512
     assert lib.plic_workspace_bytes(plic.WS_BATCHED, 64) >= 64 * (ctypes.sizeof(plic.VofField) + 8)
     assert lib.plic_workspace_bytes(77, 10) == 0
     assert lib.plic_curv_bwd_workspace_bytes(128 ** 3, 1000) == 128 ** 3 * 4 + (27 * 4 * 1000 + 255) // 256 * 256
