@@ -169,13 +169,13 @@ class ClockSampler:
 # * Kawano's SZ: its thresholds (10 + 2 div; 16 + 2 div more where cases
 #   (3)-(5) are told apart), the closed forms, and for (3)/(4) Viete's root
 #   (12 + sqrt, div, acos, cos);
-# * Newton: the paper's printed step counts (7 in case (1), 4 per bracket in
-#   cases (3) and (4); case (4) first runs the case-(3) bracket), each step of
+# * Newton: the paper's printed step counts (7 in case (1), 4 in cases (3)
+#   and (4), which the default mode iterates in one bracket), each step of
 #   the default mode 30 + div (the residual of Eq. 10, the bracket update and
 #   the convergence test; 13 + div in case (1));
 # * nested intervals: halvings until the bracket ends are adjacent
-#   (about 23 per bracket in FP32, 52 in FP64 for brackets of width ~0.3),
-#   24 each; case (4) first halves the case-(3) bracket.
+#   (about 23 in FP32, 52 in FP64 for brackets of width ~0.3), 24 each, one
+#   bracket for cases (3) and (4).
 #
 # The FP32 paired kernels (optimised SZ, analytic) evaluate every case for
 # every cell; their counts here are the method's (case-weighted), so the
@@ -186,7 +186,7 @@ CLASSIFY = 14
 CLOSED = {5: (1, {}), 2: (3, {"sqrt": 1}), 1: (1, {"cbrt": 1})}
 POLISH = (22, {"div": 2})
 POLISH5 = (2, {})
-NEWTON_STEPS = {1: 7, 3: 4, 4: 8}
+NEWTON_STEPS = {1: 7, 3: 4, 4: 4}
 NESTED_HALVINGS = {"fp32": 23, "fp64": 52}
 
 # fast FP32 forms of the calls: (FP32 operations, MUFU operations)
@@ -240,7 +240,7 @@ def ops_per_case(method: str, prec: str):
             if c in CLOSED:
                 cost = _add(cost, CLOSED[c])
             else:
-                h = NESTED_HALVINGS["fp64" if prec == "fp64" else "fp32"] * (1 if c == 3 else 2)
+                h = NESTED_HALVINGS["fp64" if prec == "fp64" else "fp32"]
                 cost = _add(cost, (24 * h + 4, {"div": 1}))
         else:
             raise ValueError(method)

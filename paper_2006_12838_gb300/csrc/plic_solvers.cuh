@@ -388,8 +388,13 @@ __device__ __forceinline__ T sz_opt_hard(T V, T n1, T n2, T n3) {
 // Sec. 2.5: the iterative solvers.  Both take the closed forms for cases (5)
 // and (2), then iterate on the volume of Eq. 10 inside the bracket of a case:
 // [0, n1] for case (1) (Newton only; nested intervals use the cube root),
-// [n2, n1 + n2] for case (3) and, when the case-(3) result passes n3,
-// [n3, L/2] for case (4).
+// [n2, n1 + n2] for case (3) and, in the paper's order, [n3, L/2] for case
+// (4) when the case-(3) result passes n3.  The default forms iterate on the
+// residual of reduced_residual(), which is Eq. 10 for every d < n1 + n2 (its
+// (d - n3)_+ term covers case (4)); since the case-(4) range [n3, L/2] lies
+// inside [n2, n1 + n2] (L/2 < n1 + n2 when n3 < n1 + n2), one bracket
+// [n2, n1 + n2] holds the offset of both cases and is iterated once.  The
+// bracket is chosen by selects, so all lanes of a warp run one loop.
 //
 // The paper-literal forms (FAITHFUL) run on Eq. 10 as printed: with k
 // corners cut off (none in case (1), two in case (3), three in case (4)),
@@ -498,17 +503,16 @@ __device__ __forceinline__ T newton_hard(T V, T n1, T n2, T n3) {
         return d <= n3 ? d : newton_printed<T>(n3, half, 3, 4, rhs6, n1, n2, n3);
     }
     const T inv_n1 = T(1) / n1;
-    if (k.c == 1) {
-        // start within a factor 2^(2/3) of the root (d1^3 = X) from the binary
-        // exponent of X = 6 V n1 n2 n3
-        const T X = k.w * n1;
-        if (!(X > T(0))) return T(0);
-        const T d0 = fmin(ldexp(T(1), Fm<T>::ilogb_(X) / 3), n1);
-        return newton_bracketed<T>(d0, T(0), n1, k.w, n1, n2, n3, inv_n1);
-    }
-    const T d = newton_bracketed<T>(T(0.5) * (n2 + k.n12), n2, k.n12, k.w, n1, n2, n3, inv_n1);
-    if (d <= n3) return d;
-    return newton_bracketed<T>(T(0.5) * (n3 + half), n3, half, k.w, n1, n2, n3, inv_n1);
+    // case (1): [0, n1], starting within a factor 2^(2/3) of the root
+    // (d1^3 = X) from the binary exponent of X = 6 V n1 n2 n3; cases (3)/(4):
+    // [n2, n1 + n2] from its middle
+    const bool c1 = k.c == 1;
+    const T X = k.w * n1;
+    if (c1 && !(X > T(0))) return T(0);
+    const T d1 = fmin(ldexp(T(1), Fm<T>::ilogb_(c1 ? X : T(1)) / 3), n1);
+    const T lo = c1 ? T(0) : n2, hi = c1 ? n1 : k.n12;
+    const T d0 = c1 ? d1 : T(0.5) * (n2 + k.n12);
+    return newton_bracketed<T>(d0, lo, hi, k.w, n1, n2, n3, inv_n1);
 }
 
 template <typename T, bool FAITHFUL>
@@ -532,9 +536,7 @@ __device__ __forceinline__ T nested_hard(T V, T n1, T n2, T n3) {
         return d <= n3 ? d : halve_printed<T>(n3, half, 3, rhs6, n1, n2, n3);
     }
     const T inv_n1 = T(1) / n1;
-    const T d = halve_to_adjacent<T>(n2, k.n12, k.w, n1, n2, n3, inv_n1);
-    if (d <= n3) return d;
-    return halve_to_adjacent<T>(n3, half, k.w, n1, n2, n3, inv_n1);
+    return halve_to_adjacent<T>(n2, k.n12, k.w, n1, n2, n3, inv_n1);
 }
 
 template <typename T, bool FAITHFUL>
