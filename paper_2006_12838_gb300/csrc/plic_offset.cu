@@ -82,15 +82,22 @@ k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const 
     constexpr int W = Vec16<T>::W;
     constexpr bool SZ = METHOD == M_SZ_ORIG || METHOD == M_SZ_OPT;
     typedef Solver<METHOD, T, false> S;
+    // FP64: one task list for the block's 8 warps (heavy parts long enough
+    // to repay the barriers; only the block's last round is partly empty);
+    // FP32: one list per warp, no barriers
+    constexpr bool POOL = sizeof(T) == 8;
     __shared__ T task[8][32 * W][4];
+    __shared__ int wtot[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
     int bad = 0;
     const int64_t nvec = vec_ok ? n / W : 0;
-    // the loop bound is the same for the 32 lanes of a warp (votes below)
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + warp * 32; i0 < nvec; i0 += wstride) {
-        const int64_t i = i0 + lane;
+    // the loop bound is the same for the 32 lanes of a warp (votes below),
+    // and with POOL for the whole block (barriers)
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (POOL ? 0 : warp * 32); i0 < nvec;
+         i0 += wstride) {
+        const int64_t i = i0 + (POOL ? threadIdx.x : lane);
         const bool have = i < nvec;
         T a[W], b[W], c[W], v[W];
         if (have) {
@@ -131,7 +138,7 @@ k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const 
             if (S::easy(V, n1, n2, n3, d)) res[j] = d;
             else need |= 1u << j;
         }
-        // the heavy part on the packed task list of the warp
+        // the heavy part on the packed task list of the warp (of the block)
         unsigned m[W];
         int pre[W + 1];
         pre[0] = 0;
@@ -140,22 +147,51 @@ k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const 
             m[j] = __ballot_sync(0xffffffffu, (need >> j) & 1u);
             pre[j + 1] = pre[j] + __popc(m[j]);
         }
+        if constexpr (POOL) {
+            T (*flat)[4] = &task[0][0];
+            if (lane == 0) wtot[warp] = pre[W];
+            __syncthreads();
+            int base = 0, total = 0;
 #pragma unroll
-        for (int j = 0; j < W; ++j)
-            if ((need >> j) & 1u) {
-                T* q = task[warp][pre[j] + __popc(m[j] & lt)];
-                q[0] = red[j][0]; q[1] = red[j][1]; q[2] = red[j][2]; q[3] = red[j][3];
+            for (int w = 0; w < 8; ++w) {
+                const int x = wtot[w];
+                base += w < warp ? x : 0;
+                total += x;
             }
-        __syncwarp();
-        for (int t = lane; t < pre[W]; t += 32) {
-            T* q = task[warp][t];
-            q[0] = S::hard(q[0], q[1], q[2], q[3]);
-        }
-        __syncwarp();
 #pragma unroll
-        for (int j = 0; j < W; ++j)
-            if ((need >> j) & 1u) res[j] = task[warp][pre[j] + __popc(m[j] & lt)][0];
-        __syncwarp();
+            for (int j = 0; j < W; ++j)
+                if ((need >> j) & 1u) {
+                    T* q = flat[base + pre[j] + __popc(m[j] & lt)];
+                    q[0] = red[j][0]; q[1] = red[j][1]; q[2] = red[j][2]; q[3] = red[j][3];
+                }
+            __syncthreads();
+            for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                T* q = flat[t];
+                q[0] = S::hard(q[0], q[1], q[2], q[3]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if ((need >> j) & 1u) res[j] = flat[base + pre[j] + __popc(m[j] & lt)][0];
+            __syncthreads();
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if ((need >> j) & 1u) {
+                    T* q = task[warp][pre[j] + __popc(m[j] & lt)];
+                    q[0] = red[j][0]; q[1] = red[j][1]; q[2] = red[j][2]; q[3] = red[j][3];
+                }
+            __syncwarp();
+            for (int t = lane; t < pre[W]; t += 32) {
+                T* q = task[warp][t];
+                q[0] = S::hard(q[0], q[1], q[2], q[3]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if ((need >> j) & 1u) res[j] = task[warp][pre[j] + __popc(m[j] & lt)][0];
+            __syncwarp();
+        }
         // polish and the symmetry back to d0 (Eqs. 5-8)
         T r[W];
 #pragma unroll
