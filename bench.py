@@ -174,8 +174,13 @@ class ClockSampler:
 #   the default mode 30 + div (the residual of Eq. 10, the bracket update and
 #   the convergence test; 13 + div in case (1));
 # * nested intervals: halvings until the bracket ends are adjacent
-#   (about 23 in FP32, 52 in FP64 for brackets of width ~0.3), 24 each, one
-#   bracket for cases (3) and (4).
+#   (about 23 in FP32, 52 in FP64 for brackets of width ~0.3), one bracket
+#   for cases (3) and (4); per halving 24 operations in FP32 and 19 FP64
+#   instructions in FP64 (the compare with n1, two subtractions and two
+#   maxima for (d - n2)_+ and (d - n3)_+, nine for the residual, the sign
+#   test, the midpoint (2) and the two adjacency tests) -- the four selects of
+#   the bracket ends act on the 32-bit halves of the doubles, outside the FP64
+#   pipe, and n1^2 is loop-invariant.
 #
 # The FP32 paired kernels (optimised SZ, analytic) evaluate every case for
 # every cell; their counts here are the method's (case-weighted), so the
@@ -188,6 +193,7 @@ POLISH = (22, {"div": 2})
 POLISH5 = (2, {})
 NEWTON_STEPS = {1: 7, 3: 4, 4: 4}
 NESTED_HALVINGS = {"fp32": 23, "fp64": 52}
+NESTED_STEP = {"fp32": 24, "fp64": 19}
 
 # fast FP32 forms of the calls: (FP32 operations, MUFU operations)
 FP32_CALL = {"div": (1, 1), "sqrt": (2, 1), "rsqrt": (0, 1), "cbrt": (6, 3), "sin": (1, 1),
@@ -240,8 +246,8 @@ def ops_per_case(method: str, prec: str):
             if c in CLOSED:
                 cost = _add(cost, CLOSED[c])
             else:
-                h = NESTED_HALVINGS["fp64" if prec == "fp64" else "fp32"]
-                cost = _add(cost, (24 * h + 4, {"div": 1}))
+                p = "fp64" if prec == "fp64" else "fp32"
+                cost = _add(cost, (NESTED_STEP[p] * NESTED_HALVINGS[p] + 4, {"div": 1}))
         else:
             raise ValueError(method)
         tot = _add(base, cost)
