@@ -295,11 +295,14 @@ static const void* cptr() {
 
 // The default solvers run work-compacted (k_plic_offset_compact); the
 // paper-literal ones keep one cell after the other per lane.
-// Kawano's SZ in FP32 stays one cell after the other: its heavy part (one
-// arccosine and one cosine on the FP32 pipes) is too short to repay the
-// packing (measured 102 against 130 G solves/s on 2^26 cells); in FP64, and
-// for the iterative solvers, packing wins (e.g. nested intervals FP32 27 ->
-// 40, FP64 SZ-opt 3.3 -> 4.5 G solves/s).
+// In FP32 the optimised SZ, Kawano's SZ and the analytic solution take the
+// paired kernel (k_plic_offset_pair, chosen in offset_entry); Kawano's SZ in
+// FP32 is packed in no form here: its heavy part (one arccosine and one
+// cosine on the FP32 pipes) is too short to repay the packing (measured 102
+// against 130 G solves/s one cell after the other, on 2^26 cells), and only
+// its faithful form reaches this function in FP32.  In FP64, and for the
+// iterative solvers, packing wins (e.g. nested intervals FP32 27 -> 40, FP64
+// SZ-opt 3.3 -> 4.5 G solves/s).
 template <int METHOD>
 static const void* pick(plic_precision p, bool faithful) {
     if (p == PLIC_FP64_REFINED) return reinterpret_cast<const void*>(&k_plic_offset_refined<METHOD>);
@@ -357,7 +360,11 @@ static plic_status offset_entry(const void* nx, const void* ny, const void* nz, 
                                                             d_invalid_count != nullptr, fused)
                                     : pick<M_ANALYTIC>(p, faithful);
             break;
-        case PLIC_SZ_ORIG: k = pick<M_SZ_ORIG>(p, faithful); break;
+        case PLIC_SZ_ORIG:
+            k = (!dbl && !faithful) ? pick_pair<M_SZ_ORIG>(p == PLIC_FP32_POLISHED, vrt != nullptr,
+                                                           d_invalid_count != nullptr, fused)
+                                    : pick<M_SZ_ORIG>(p, faithful);
+            break;
         case PLIC_SZ_OPT:
             k = (!dbl && !faithful) ? pick_pair<M_SZ_OPT>(p == PLIC_FP32_POLISHED, vrt != nullptr,
                                                           d_invalid_count != nullptr, fused)

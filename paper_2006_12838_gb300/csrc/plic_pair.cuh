@@ -1,6 +1,7 @@
-// plic_pair.cuh -- the FP32 fast paths of the optimised SZ solution (Sec. 2.4)
-// and of the analytic solution (Sec. 2.3) for two cells at once, on the paired FP32 instructions of sm_100+ (one
-// FFMA2/FADD2/FMUL2 issues two FP32 operations).  Comparisons, selects and
+// plic_pair.cuh -- the FP32 fast paths of the optimised and of Kawano's SZ
+// solution (Sec. 2.4) and of the analytic solution (Sec. 2.3) for two cells
+// at once, on the paired FP32 instructions of sm_100+ (one FFMA2/FADD2/FMUL2
+// issues two FP32 operations).  Comparisons, selects and
 // MUFU operations stay per component.
 //
 // The arithmetic is that of solve_sz_opt_default<float> + polish (see
@@ -151,6 +152,59 @@ __device__ __forceinline__ f2 sz_opt(f2 V, f2 n1, f2 n2, f2 n3) {
     return sel(le(n12, n3V2), d5, d);
 }
 
+// Kawano's Scardovelli-Zaleski solution (Sec. 2.4) for two cells, in the
+// L1-normalised reduced space (m1 <= m2 <= m3, w the reduced volume), with
+// the arithmetic of sz_orig_easy/sz_orig_hard<float> (plic_solvers.cuh): its
+// volume thresholds Vb1 = m1^2/(6 m2 m3 + 1e-25) and Vb2 = Vb1 + (m2 -
+// m1)/(2 m3), the case-(3) end Vb3 (the case-(5) threshold m12/(2 m3) when m3
+// >= m1 + m2, else the volume of the plane through the vertex m3), and
+// Viete's root of the monic cubic with s^2 and -q/2 multiplied out.  Every
+// case is evaluated and the selects follow that implementation's order: (1),
+// (2), then (5) unless its offset is 0 (that implementation then solves the
+// case-(4) cubic, which gives NaN for m = (0, 0, 1), w = 0 through s^2 = -1/4),
+// else (3)/(4).  With POLISH the root of cases (3)/(4) gets one Newton step;
+// the closed forms are accurate as they are.
+template <bool POLISH>
+__device__ __forceinline__ f2 sz_orig(f2 w, f2 m1, f2 m2, f2 m3) {
+    typedef Fm<float> F;
+    const f2 m12 = add(m1, m2), m1m2 = mul(m1, m2);
+    const f2 e3 = mul(m1m2, m3), sqm1 = mul(m1, m1);
+    const f2 ir3 = rcp(m3);
+    const f2 vb1 = mul(sqm1, rcp(fma(mk(6.0f), mul(m2, m3), mk(1e-25f))));
+    const f2 vb2 = fma(mul(mk(0.5f), sub(m2, m1)), ir3, vb1);
+    const b2 tall = {!(m3.x < m12.x), !(m3.y < m12.y)};
+    const f2 vb5 = mul(mul(mk(0.5f), m12), ir3);
+    const f2 d31 = sub(m3, m1), d32 = sub(m3, m2);
+    const f2 cub3 = sub(mul(mul(m3, m3), m3),
+                        fma(mul(d31, d31), d31, mul(mul(d32, d32), d32)));
+    const f2 vb3 = sel(tall, vb5, mul(cub3, rcp(mul(mk(6.0f), e3))));
+    const b2 c3 = lt(w, vb3);
+    // Viete: s^2, -q/2 and the shift -a2/3 of the case
+    const f2 s24 = mul(mk(0.25f), fma(m1, fma(mk(2.0f), add(m2, m3), make_float2(-m1.x, -m1.y)),
+                                      make_float2(-d32.x * d32.x, -d32.y * d32.y)));
+    const f2 s2 = sel(c3, add(m1m2, m1m2), s24);
+    const f2 mq2 = sel(c3, mul(mul(mk(1.5f), m1m2), fma(mk(-2.0f), mul(m3, w), m12)),
+                       mul(mul(mk(0.75f), e3), fma(mk(-2.0f), w, mk(1.0f))));
+    const f2 shift = sel(c3, m12, mk(0.5f));
+    const f2 s = make_float2(F::sqrt_(s2.x), F::sqrt_(s2.y));
+    f2 r = mul(mq2, rcp(mul(s2, s)));
+    r = make_float2(fminf(fmaxf(r.x, -1.0f), 1.0f), fminf(fmaxf(r.y, -1.0f), 1.0f));
+    const f2 ang = mul(mk(0.33333333333333333f),
+                       make_float2(F::acos_(r.x) + 12.566370614359172f, F::acos_(r.y) + 12.566370614359172f));
+    f2 d = fma(add(s, s), make_float2(__cosf(ang.x), __cosf(ang.y)), shift);
+    if (POLISH) d = polish34(d, mul(mul(mk(6.0f), e3), w), m1, m2, m3);
+    // case (5): tall and w >= m12 / (2 m3), unless its offset is 0
+    const f2 d5 = fma(m3, w, mul(mk(0.5f), m12));
+    const b2 c5 = {tall.x && !(w.x < vb5.x) && d5.x != 0.0f, tall.y && !(w.y < vb5.y) && d5.y != 0.0f};
+    d = sel(c5, d5, d);
+    // case (2) below Vb2, case (1) below Vb1
+    const f2 d2 = fma(mk(0.5f), m1, sqrtp(fma(mul(mk(2.0f), mul(m2, m3)), w,
+                                              mul(mk(-0.083333333333333333f), sqm1))));
+    d = sel(lt(w, vb2), d2, d);
+    const f2 d1 = cbrt_(mul(mul(mk(6.0f), e3), w));
+    return sel(lt(w, vb1), d1, d);
+}
+
 // The paper's analytic solution (Sec. 2.3, Eq. 25 with the tests of Eq. 24)
 // for two cells, in the reduced space of the unit normal (n1 <= n2 <= n3,
 // |n| = 1, V the reduced volume).  As in sz_opt: case (3) or (4) is decided
@@ -249,9 +303,10 @@ __device__ __forceinline__ f2 volume_reduced(f2 d0, f2 il, f2 m1, f2 m2, f2 m3) 
 }
 
 // Whole cells: two (n, V0) -> d0 in FP32 by the optimised SZ solution
-// (METHOD = M_SZ_OPT, in L1 units) or the analytic solution (M_ANALYTIC, in
-// the unit normal's units); with ROUNDTRIP, also the forward volume of the
-// returned d0 into *vrt; with COUNT, invalid cells are added to `bad`.
+// (METHOD = M_SZ_OPT, in L1 units), Kawano's SZ solution (M_SZ_ORIG, in L1
+// units) or the analytic solution (M_ANALYTIC, in the unit normal's units);
+// with ROUNDTRIP, also the forward volume of the returned d0 into *vrt; with
+// COUNT, invalid cells are added to `bad`.
 template <int METHOD, bool POLISH, bool ROUNDTRIP = false, bool COUNT = true>
 __device__ __forceinline__ f2 offset_pair(f2 nx, f2 ny, f2 nz, f2 V0, int& bad,
                                           f2* vrt = nullptr) {
@@ -274,6 +329,8 @@ __device__ __forceinline__ f2 offset_pair(f2 nx, f2 ny, f2 nz, f2 V0, int& bad,
     f2 h;
     if (METHOD == M_SZ_OPT) {
         h = mul(L, sub(mk(0.5f), sz_opt<POLISH>(V, m1, m2, m3)));
+    } else if (METHOD == M_SZ_ORIG) {
+        h = mul(L, sub(mk(0.5f), sz_orig<POLISH>(V, m1, m2, m3)));
     } else {
         const f2 n2 = fmax0(sub(sub(L, n1), n3));
         const f2 d = analytic<POLISH>(V, n1, n2, n3);
@@ -283,9 +340,11 @@ __device__ __forceinline__ f2 offset_pair(f2 nx, f2 ny, f2 nz, f2 V0, int& bad,
     if (!okx) r.x = __int_as_float(0x7fffffff);
     if (!oky) r.y = __int_as_float(0x7fffffff);
     if (ROUNDTRIP) {
+        // NaN where d0 is NaN: invalid inputs, and Kawano's NaN cells (the
+        // volume's clamp of d would otherwise turn a NaN offset into a number)
         f2 v = volume_reduced(r, il, m1, m2, m3);
-        if (!okx) v.x = __int_as_float(0x7fffffff);
-        if (!oky) v.y = __int_as_float(0x7fffffff);
+        if (r.x != r.x) v.x = __int_as_float(0x7fffffff);
+        if (r.y != r.y) v.y = __int_as_float(0x7fffffff);
         *vrt = v;
     }
     return r;
