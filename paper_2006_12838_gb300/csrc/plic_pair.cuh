@@ -265,8 +265,9 @@ __device__ __forceinline__ f2 analytic(f2 V, f2 n1, f2 n2, f2 n3) {
     const f2 d2 = fma(mk(0.5f), n1, mul(mk(K::inv_sqrt12),
                                         sqrtp(fma(mk(24.0f), mul(n2, n3V), make_float2(-sqn1.x, -sqn1.y)))));
     d = sel(lt(t2a, sqn1), d2, d);
-    // case (1) where 6 n2 n3 V < n1^2
-    const f2 d1 = cbrt_nr(V6n1n2n3);
+    // case (1) where 6 n2 n3 V < n1^2 (the plain cube root: d1 <= n1, so its
+    // relative error leaves an absolute one below 2e-7, as in sz_opt)
+    const f2 d1 = cbrt_(V6n1n2n3);
     d = sel(lt(V6n2n3, sqn1), d1, d);
     // case (5) where n1 + n2 <= 2 n3 V
     const f2 d5 = fma(mk(0.5f), n12, n3V);
