@@ -126,8 +126,9 @@ __device__ __forceinline__ float4 ld_row4(const float* __restrict__ row, bool ok
 // vector path a warp takes two rows at a time and issues the four 16-byte
 // loads per lane of 256 columns of both rows before using any of them, so
 // every lane keeps 64 bytes in flight (the pass is bound by load latency, not
-// by the compare work).
-__global__ void __launch_bounds__(CT_THREADS)
+// by the compare work).  Eight blocks per SM (32 registers, a few bytes
+// spilled) keep more loads in flight than the six that 40 registers allow.
+__global__ void __launch_bounds__(CT_THREADS, 8)
 k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
                 int* __restrict__ tile_count, unsigned* __restrict__ bits, int vec) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
