@@ -72,6 +72,20 @@ int blocks_per_sm(const void* kernel, int threads, size_t smem) {
     return b;
 }
 
+cudaError_t launch_after(const void* kernel, dim3 grid, dim3 block, void** args, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kernel, args);
+}
+
 int stream_grid(const void* kernel, int threads, int64_t work) {
     const int64_t need = (work + threads - 1) / threads;
     const int64_t cap = (int64_t)stride_grid(kernel, threads, work) * STREAM_WAVES;

@@ -39,4 +39,20 @@ int stream_grid(const void* kernel, int threads, int64_t work);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Programmatic dependent launch: a kernel launched with launch_after() may be
+// scheduled while the kernel before it on the stream is still finishing (once
+// that kernel's blocks have all executed pdl_trigger() or exited), and waits
+// in pdl_wait() until that kernel has completed and its writes are visible.
+// Every kernel launched this way calls pdl_wait() before it reads what the
+// kernel before it wrote; the overlap hides the launch of short dependent
+// kernels (the compaction's write pass, the curvature step after it).  After
+// an operation that is not a kernel, or with no kernel before it, the launch
+// is an ordinary one and pdl_wait() returns at once.
+cudaError_t launch_after(const void* kernel, dim3 grid, dim3 block, void** args, cudaStream_t s);
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
 }  // namespace plic

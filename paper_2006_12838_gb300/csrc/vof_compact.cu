@@ -131,6 +131,7 @@ __device__ __forceinline__ float4 ld_row4(const float* __restrict__ row, bool ok
 __global__ void __launch_bounds__(CT_THREADS, 8)
 k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
                 int* __restrict__ tile_count, unsigned* __restrict__ bits, int vec) {
+    pdl_wait();                                     // the kernel that wrote the field complete
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpr = (nx + 31) >> 5;
     const int64_t rbeg = (int64_t)blockIdx.x * R;
@@ -189,6 +190,7 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
         for (int w = 0; w < CT_WARPS; ++w) t += ws[w];
         tile_count[blockIdx.x] = t;
     }
+    pdl_trigger();                                  // the next pass may be scheduled
 }
 
 // Pass 2: exclusive scan of ntiles ints by one block of 1024 threads (four
@@ -196,6 +198,7 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
 __global__ void __launch_bounds__(1024)
 k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict__ d_count) {
     __shared__ long long wsum[32];
+    pdl_wait();                                     // pass 1 complete
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long carry = 0;
     for (int64_t b0 = 0; b0 < ntiles; b0 += 4096) {
@@ -232,6 +235,7 @@ k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict
         __syncthreads();
     }
     if (threadIdx.x == 0) *d_count = carry;
+    pdl_trigger();
 }
 
 // Pass 3 without stored bits: each warp recomputes its rows' interface bits
@@ -246,6 +250,7 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     __shared__ int rowcnt[CT_MAX_ROWS];
     __shared__ long long s_base[CT_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    pdl_wait();                                     // the passes before complete
     // with d_count given, tile_offset holds the per-tile counts of pass 1 and
     // the block sums those of the tiles before its own (few tiles: no scan
     // launch); the last block writes the total
@@ -348,6 +353,7 @@ k_compact_write(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
             pos += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
+    pdl_trigger();
 }
 
 // Pass 3 with pass 1's interface bits: one warp per tile, a block of CT_WARPS
@@ -368,6 +374,7 @@ k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restric
     __shared__ long long s_part[CT_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t t0 = (int64_t)blockIdx.x * CT_WARPS;
+    pdl_wait();                                     // the passes before complete
     const int64_t t = t0 + warp;
     long long base = 0;
     int tcount = 0;
@@ -447,6 +454,30 @@ k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restric
         }
         pos += __shfl_sync(0xffffffffu, incl, 31);
     }
+    pdl_trigger();
+}
+
+// The passes as programmatic dependent launches (launch_after): each waits
+// for the kernel before it on the stream, the first for the one that wrote
+// the field.
+static cudaError_t launch_count(const float* phi, int nx, int ny, int nz, int R, int64_t rows,
+                                int64_t nt, int* tiles, unsigned* bits, int vec, cudaStream_t s) {
+    void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&nz, (void*)&R, (void*)&rows,
+                    (void*)&tiles, (void*)&bits, (void*)&vec};
+    return launch_after(reinterpret_cast<const void*>(&k_compact_count), dim3((unsigned)nt),
+                        dim3(CT_THREADS), args, s);
+}
+static cudaError_t launch_scan(int* tiles, int64_t nt, int64_t* d_count, cudaStream_t s) {
+    void* args[] = {(void*)&tiles, (void*)&nt, (void*)&d_count};
+    return launch_after(reinterpret_cast<const void*>(&k_compact_scan), dim3(1), dim3(1024), args, s);
+}
+static cudaError_t launch_write(const float* phi, int nx, int ny, int nz, int R, int64_t rows, int64_t nt,
+                                const int* tiles, int32_t* idx, int64_t cap, int vec, int64_t* d_count,
+                                cudaStream_t s) {
+    void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&nz, (void*)&R, (void*)&rows,
+                    (void*)&tiles, (void*)&idx, (void*)&cap, (void*)&vec, (void*)&d_count};
+    return launch_after(reinterpret_cast<const void*>(&k_compact_write), dim3((unsigned)nt),
+                        dim3(CT_THREADS), args, s);
 }
 
 // Tiles of a field: whole x-rows, tile_rows(nx) per tile.
@@ -509,20 +540,26 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
     if (nx >= 32 && tile_bytes + bits_bytes <= ws_bytes)
         bits = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + tile_bytes);
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
-    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, bits, vec);
+    cudaError_t e = launch_count(phi, nx, ny, nz, R, rows, nt, tiles, bits, vec, s);
     // up to CT_FUSED_SCAN_TILES tiles pass 3 sums the counts of the tiles
     // before each block (at most that many L2 reads per block); beyond, one
     // block scans them first
     const bool fused = nt <= CT_FUSED_SCAN_TILES;
-    if (!fused) k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
-    if (bits) {
-        const int64_t nb = (nt + CT_WARPS - 1) / CT_WARPS;
-        k_compact_emit<<<(unsigned)nb, CT_THREADS, 0, s>>>(nx, R, rows, nt, tiles, bits, idx,
-                                                           idx_capacity, fused ? 1 : 0, d_count);
-    } else {
-        k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, idx,
-                                                            idx_capacity, vec, fused ? d_count : nullptr);
+    if (e == cudaSuccess && !fused) e = launch_scan(tiles, nt, d_count, s);
+    if (e == cudaSuccess) {
+        int fz = fused ? 1 : 0;
+        if (bits) {
+            const int64_t nb = (nt + CT_WARPS - 1) / CT_WARPS;
+            void* args[] = {(void*)&nx, (void*)&R, (void*)&rows, (void*)&nt, (void*)&tiles, (void*)&bits,
+                            (void*)&idx, (void*)&idx_capacity, (void*)&fz, (void*)&d_count};
+            e = launch_after(reinterpret_cast<const void*>(&k_compact_emit), dim3((unsigned)nb),
+                             dim3(CT_THREADS), args, s);
+        } else {
+            e = launch_write(phi, nx, ny, nz, R, rows, nt, tiles, idx, idx_capacity, vec,
+                             fused ? d_count : nullptr, s);
+        }
     }
+    if (e != cudaSuccess) { set_last_error("vof_interface_compact", e); return PLIC_ERR_CUDA; }
     return check_launch("vof_interface_compact");
 }
 
@@ -600,10 +637,12 @@ extern "C" plic_status vof_interface_compact_noalloc(const float* phi, int nx, i
     }
     // the built-in scratch holds the tile counts only; pass 3 re-reads the field
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
-    k_compact_count<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, nullptr, vec);
+    cudaError_t e = launch_count(phi, nx, ny, nz, R, rows, nt, tiles, nullptr, vec, s);
     const bool fused = nt <= CT_FUSED_SCAN_TILES;
-    if (!fused) k_compact_scan<<<1, 1024, 0, s>>>(tiles, nt, d_count);
-    k_compact_write<<<(unsigned)nt, CT_THREADS, 0, s>>>(phi, nx, ny, nz, R, rows, tiles, idx,
-                                                        idx_capacity, vec, fused ? d_count : nullptr);
+    if (e == cudaSuccess && !fused) e = launch_scan(tiles, nt, d_count, s);
+    if (e == cudaSuccess)
+        e = launch_write(phi, nx, ny, nz, R, rows, nt, tiles, idx, idx_capacity, vec,
+                         fused ? d_count : nullptr, s);
+    if (e != cudaSuccess) { set_last_error("vof_interface_compact_noalloc", e); return PLIC_ERR_CUDA; }
     return check_launch("vof_interface_compact_noalloc");
 }

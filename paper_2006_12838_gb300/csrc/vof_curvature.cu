@@ -128,7 +128,9 @@ static plic_status curvature_entry(const float* phi, int nx, int ny, int nz, con
     const int grid = stride_grid(k, TPC_THREADS, n_iface);
     void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&idx, (void*)&n_iface,
                     (void*)&d_n_iface, (void*)&out, (void*)&flags, (void*)&scale};
-    cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(TPC_THREADS), args, 0, as_stream(stream));
+    // a programmatic dependent launch: the list usually comes from the
+    // compaction launched just before on the same stream
+    cudaError_t e = launch_after(k, dim3(grid), dim3(TPC_THREADS), args, as_stream(stream));
     if (e != cudaSuccess) { set_last_error(who, e); return PLIC_ERR_CUDA; }
     return PLIC_OK;
 }

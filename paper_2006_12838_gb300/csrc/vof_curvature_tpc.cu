@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(TPC_THREADS)
 k_vof_curvature_tpc(const float* __restrict__ phi, int nx, int ny, const int32_t* __restrict__ idx,
                     int64_t n, const int64_t* __restrict__ d_n, float* __restrict__ kappa,
                     uint32_t flags, float scale) {
+    pdl_wait();                  // a kernel before it (the compaction) has completed
     int64_t lim = n;
     if (d_n) {
         const int64_t dn = *d_n;
@@ -198,6 +199,7 @@ k_vof_curvature_tpc(const float* __restrict__ phi, int nx, int ny, const int32_t
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lim;
          k += (int64_t)gridDim.x * blockDim.x)
         kappa[k] = scale * tpc_kappa<METHOD, FIT>(phi, nx, nxy, (int64_t)__ldg(idx + k), flags, tab);
+    pdl_trigger();
 }
 
 // Persistent batched kernel: each warp claims tickets of `chunk` cells (a
