@@ -50,8 +50,9 @@ def _compact(dev, p):
                                    # per tile) and beyond, a 44-cell row (two words)
                                    (6, 7, 32), (3, 4, 8192), (3, 3, 8196), (3, 40, 44),
                                    # > 4096 tiles: the separate scan launch, with the vector
-                                   # loads and with the scalar ones (odd nx)
-                                   (520, 256, 256), (500, 257, 257)])
+                                   # loads and with the scalar ones (odd nx), and with rows of
+                                   # 30 cells, which keep no bits (the recounting write pass)
+                                   (520, 256, 256), (500, 257, 257), (2000, 600, 30)])
 def test_compaction_bit_exact(dev, orc, shape):
     rng = np.random.default_rng(sum(shape))
     p = rng.random(shape).astype(np.float32)
