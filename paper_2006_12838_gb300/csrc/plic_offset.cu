@@ -73,6 +73,41 @@ k_plic_offset(const T* __restrict__ nx, const T* __restrict__ ny, const T* __res
 // part whenever any lane needed it (about every time: 40-60 % of random cells
 // are in cases (3)/(4)), and lanes with closed-form cells would idle through
 // it.  The task list lives in shared memory (4 values per task).
+// The symmetry front end of Sec. 2.1 for one double cell on the bit patterns:
+// the FP64 kernels are bound by the FP64 pipe, so the sort of |n| (the order
+// of non-negative doubles is that of their bits; a NaN sorts last and makes L
+// NaN), the validity tests and the choice V = V0 or 1 - V0 (exact) run as
+// integer instructions; L keeps the FP64 sum |nx| + |ny| + |nz| in that order.
+__device__ __forceinline__ bool front_bits(double nx, double ny, double nz, double V0, double& n1,
+                                           double& n2, double& n3, double& L, double& V) {
+    const unsigned long long S = 0x8000000000000000ull;
+    const unsigned long long ux = (unsigned long long)__double_as_longlong(nx) & ~S;
+    const unsigned long long uy = (unsigned long long)__double_as_longlong(ny) & ~S;
+    const unsigned long long uz = (unsigned long long)__double_as_longlong(nz) & ~S;
+    const unsigned long long lo = ux < uy ? ux : uy, hi = ux < uy ? uy : ux;
+    const unsigned long long b1 = lo < uz ? lo : uz, b3 = hi > uz ? hi : uz;
+    n1 = __longlong_as_double((long long)b1);
+    n3 = __longlong_as_double((long long)b3);
+    n2 = __longlong_as_double((long long)(ux ^ uy ^ uz ^ b1 ^ b3));
+    L = (__longlong_as_double((long long)ux) + __longlong_as_double((long long)uy)) +
+        __longlong_as_double((long long)uz);
+    const unsigned long long bv = (unsigned long long)__double_as_longlong(V0), va = bv & ~S;
+    const unsigned long long bl = (unsigned long long)__double_as_longlong(L);
+    // 0 <= V0 <= 1 (-0 accepted, NaN refused) and 0 < L <= 3
+    const bool ok = ((bv >> 63) == 0ull || va == 0ull) && va <= 0x3FF0000000000000ull && bl != 0ull &&
+                    bl <= 0x4008000000000000ull;
+    V = va <= 0x3FE0000000000000ull ? __longlong_as_double((long long)va) : 1.0 - V0;
+    return ok;
+}
+
+// |h| with the sign of V0 - 1/2 (+ for V0 >= 1/2), on the bits.
+__device__ __forceinline__ double sign_of_side(double h, double V0) {
+    const unsigned long long S = 0x8000000000000000ull;
+    const unsigned long long va = (unsigned long long)__double_as_longlong(V0) & ~S;
+    const unsigned long long m = (unsigned long long)__double_as_longlong(h) & ~S;
+    return __longlong_as_double((long long)(va >= 0x3FE0000000000000ull ? m : (m | S)));
+}
+
 template <int METHOD, typename T, bool POLISH>
 __global__ void __launch_bounds__(256)
 k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const T* __restrict__ nz,
@@ -86,6 +121,9 @@ k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const 
     // to repay the barriers; only the block's last round is partly empty);
     // FP32: one list per warp, no barriers
     constexpr bool POOL = sizeof(T) == 8;
+    // FP64: the front end on the bit patterns (front_bits), except for nested
+    // intervals (4-5 % faster for the other four solvers, 3 % slower there)
+    constexpr bool BITS = sizeof(T) == 8 && METHOD != M_NESTED;
     __shared__ T task[8][32 * W][4];
     __shared__ int wtot[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -114,16 +152,21 @@ k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const 
             res[j] = T(0);
             scale[j] = T(0);
             if (!have) continue;
-            T n1, n2, n3;
-            reduce_normal<T, false>(a[j], b[j], c[j], n1, n2, n3);
-            const T L = fabs(a[j]) + fabs(b[j]) + fabs(c[j]);
-            const bool ok = (v[j] >= T(0)) && (v[j] <= T(1)) && (L > T(0)) && (L <= T(3));
+            T n1, n2, n3, L, V;
+            bool ok;
+            if constexpr (BITS) {
+                ok = front_bits(a[j], b[j], c[j], v[j], n1, n2, n3, L, V);
+            } else {
+                reduce_normal<T, false>(a[j], b[j], c[j], n1, n2, n3);
+                L = fabs(a[j]) + fabs(b[j]) + fabs(c[j]);
+                ok = (v[j] >= T(0)) && (v[j] <= T(1)) && (L > T(0)) && (L <= T(3));
+            }
             if (!ok) {
                 bad += 1;
                 res[j] = T(NAN);
                 continue;
             }
-            const T V = reduce_volume<T, false>(v[j]);
+            if constexpr (!BITS) V = reduce_volume<T, false>(v[j]);
             if (SZ) {
                 const T il = Fm<T>::rcp_(L);
                 n1 *= il;
@@ -131,7 +174,7 @@ k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const 
                 n2 = Fm<T>::fdim_(T(1), n1 + n3);
                 scale[j] = L;
             } else {
-                scale[j] = T(1);
+                scale[j] = BITS ? L : T(1);             // with BITS, L/2 is the offset's origin
             }
             red[j][0] = V; red[j][1] = n1; red[j][2] = n2; red[j][3] = n3;
             T d;
@@ -202,8 +245,13 @@ k_plic_offset_compact(const T* __restrict__ nx, const T* __restrict__ ny, const 
             }
             T x = res[j];
             if (POLISH) x = polish<T>(x, red[j][0], red[j][1], red[j][2], red[j][3]);
-            if (SZ) r[j] = scale[j] * copysign(T(0.5) - x, v[j] - T(0.5));
-            else r[j] = copysign(T(0.5) * (red[j][1] + red[j][2] + red[j][3]) - x, v[j] - T(0.5));
+            if constexpr (BITS) {
+                // the sign of V0 - 1/2 on the bits (no FP64 subtraction)
+                r[j] = sign_of_side(SZ ? scale[j] * (T(0.5) - x) : T(0.5) * scale[j] - x, v[j]);
+            } else {
+                if (SZ) r[j] = scale[j] * copysign(T(0.5) - x, v[j] - T(0.5));
+                else r[j] = copysign(T(0.5) * (red[j][1] + red[j][2] + red[j][3]) - x, v[j] - T(0.5));
+            }
         }
         if (have) st_stream(reinterpret_cast<VT*>(d0) + i, from_arr(r));
     }
