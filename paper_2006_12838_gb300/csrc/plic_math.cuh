@@ -70,6 +70,8 @@ template <> struct Fm<float> {
         return s * fmaf(-(r2 * r - x), rcp_approx(3.0f * r2), r);
     }
     static __device__ __forceinline__ T sin_(T x) { return __sinf(x); }
+    // sine of an angle in [-pi/6, pi/6] (the roots' angles): the MUFU sine
+    static __device__ __forceinline__ T sin_pi6_(T x) { return __sinf(x); }
     static __device__ __forceinline__ T cos_(T x) { return __cosf(x); }
     static __device__ __forceinline__ T asin_(T x) { return fast_asinf(x); }
     static __device__ __forceinline__ T acos_(T x) { return 1.5707963267948966f - fast_asinf(x); }
@@ -108,6 +110,22 @@ template <> struct Fm<double> {
     static __device__ __forceinline__ T rsqrt_(T x) { return rsqrt(x); }
     static __device__ __forceinline__ T cbrt_(T x) { return cbrt(x); }
     static __device__ __forceinline__ T sin_(T x) { return sin(x); }
+    // Sine of an angle |x| <= pi/6 (the trigonometric roots' angles) by its
+    // Taylor series through x^15: the first omitted term, (pi/6)^17 / 17!, is
+    // below 5e-20, so the result is the double rounding of the sum (Horner in
+    // x^2, coefficients -1/(2k+1)!..., exact rationals rounded once); 10 FP64
+    // operations against the library sine's argument reduction and wider range.
+    static __device__ __forceinline__ T sin_pi6_(T x) {
+        const T z = x * x;
+        T p = -7.6471637318198164759e-13;                  // -1/15!
+        p = fma(p, z, 1.6059043836821614599e-10);          //  1/13!
+        p = fma(p, z, -2.5052108385441718775e-08);         // -1/11!
+        p = fma(p, z, 2.7557319223985890653e-06);          //  1/9!
+        p = fma(p, z, -1.9841269841269841270e-04);         // -1/7!
+        p = fma(p, z, 8.3333333333333333333e-03);          //  1/5!
+        p = fma(p, z, -1.6666666666666666667e-01);         // -1/3!
+        return fma(x * z, p, x);
+    }
     static __device__ __forceinline__ T cos_(T x) { return cos(x); }
     static __device__ __forceinline__ T asin_(T x) { return asin(x); }
     static __device__ __forceinline__ T acos_(T x) { return acos(x); }

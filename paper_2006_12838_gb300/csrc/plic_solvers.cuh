@@ -166,7 +166,7 @@ __device__ __forceinline__ T eq11_root(T x, T y2, T a, T b, T c) {
     const T u = F::cbrt_(u3);
     const T ru = F::rsqrt_(u);
     const T theta = F::polar_angle_(x, F::sqrt_(y2));
-    return c - T(2) * (a * ru + b * (u * ru)) * F::sin_(Kc<T>::pi_6 - Kc<T>::third * theta);
+    return c - T(2) * (a * ru + b * (u * ru)) * F::sin_pi6_(Kc<T>::pi_6 - Kc<T>::third * theta);
 }
 
 template <typename T>
@@ -289,6 +289,9 @@ __device__ __forceinline__ T sz_orig_hard(T w, T m1, T m2, T m3) {
     const T s = F::sqrt_(s2);
     T r = F::div_(mq2, s2 * s);
     if (!FAITHFUL) r = fmin(fmax(r, T(-1)), T(1));
+    // cos((acos r + 4 pi)/3) = sin(acos(r)/3 - pi/6), an angle in [-pi/6, pi/6]
+    // (FP64; FP32 keeps the cosine of the angle as written)
+    if constexpr (sizeof(T) == 8) return shift + T(2) * s * F::sin_pi6_(K::third * F::acos_(r) - K::pi_6);
     return shift + T(2) * s * F::cos_(K::third * (F::acos_(r) + K::four_pi));
 }
 
@@ -338,7 +341,7 @@ __device__ __forceinline__ T solve_sz_opt_default(T V, T n1, T n2, T n3) {
     const T t = t2 * rt;
     T arg = q * (rt * rt * rt);
     if (CLAMP) arg = fmin(fmax(arg, T(-1)), T(1));
-    const T d34 = c - T(2) * t * F::sin_(K::third * F::asin_(arg));
+    const T d34 = c - T(2) * t * F::sin_pi6_(K::third * F::asin_(arg));
     if (sizeof(T) == 8) return d34;
     const T d5 = n3V + T(0.5) * n12;
     const T d2 = T(0.5) * (n1 + F::sqrt_(T(8) * n2 * n3V - K::third * sqn1));
@@ -381,7 +384,7 @@ __device__ __forceinline__ T sz_opt_hard(T V, T n1, T n2, T n3) {
     const T rt = F::rsqrt_(t2);
     T arg = q * (rt * rt * rt);
     if (!FAITHFUL) arg = fmin(fmax(arg, T(-1)), T(1));
-    return c - T(2) * (t2 * rt) * F::sin_(K::third * F::asin_(arg));
+    return c - T(2) * (t2 * rt) * F::sin_pi6_(K::third * F::asin_(arg));
 }
 
 // ----------------------------------------------------------------------------
