@@ -126,8 +126,11 @@ __device__ __forceinline__ float4 ld_row4(const float* __restrict__ row, bool ok
 // vector path a warp takes two rows at a time and issues the four 16-byte
 // loads per lane of 256 columns of both rows before using any of them, so
 // every lane keeps 64 bytes in flight (the pass is bound by load latency, not
-// by the compare work).  Eight blocks per SM (32 registers, a few bytes
-// spilled) keep more loads in flight than the six that 40 registers allow.
+// by the compare work); rows of more than 512 cells are cut into 512-cell
+// segments, four loads per lane each (1024-cell rows: 0.26 -> 0.19 ms on a
+// 1 GiB field, the same as for 512-cell rows).  Eight blocks per SM (32
+// registers, a few bytes spilled) keep more loads in flight than the six that
+// 40 registers allow.
 __global__ void __launch_bounds__(CT_THREADS, 8)
 k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
                 int* __restrict__ tile_count, unsigned* __restrict__ bits, int vec) {
@@ -142,7 +145,33 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
         return y >= 1u && y + 2u <= (unsigned)ny && z >= 1u && z + 2u <= (unsigned)nz;
     };
     int cnt = 0;
-    if (vec) {
+    if (vec && nx > 512) {
+        // long rows (fewer than 16 per tile): the tile's rows are cut into
+        // 512-cell segments (the last of a row partial), warp w takes segments
+        // w, w + 8, ..., and each lane issues its four 16-byte loads of a
+        // segment together, as in the two-row form below
+        const int spr = (nx + 511) >> 9;
+        const int nseg = (int)(rend - rbeg) * spr;
+        for (int sg = warp; sg < nseg; sg += CT_WARPS) {
+            const int rr = sg / spr;
+            const int x0 = (sg - rr * spr) << 9;
+            const int64_t r = rbeg + rr;
+            const bool ok = interior(r);
+            const float* row = phi + r * nx;
+            unsigned* br = bits ? bits + r * wpr : nullptr;
+            const int xa = x0 + 4 * lane;
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = ld_row4(row, ok, xa + 128 * u, nx);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned m = ok ? nib4(v[u], xa + 128 * u, nx) : 0u;
+                cnt += __popc(m);
+                emit_nibbles(m, x0 + 128 * u, nx, [&](int w, unsigned b) { if (br) br[w] = b; });
+            }
+        }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+    } else if (vec) {
         for (int64_t ra = rbeg + warp; ra < rend; ra += 2 * CT_WARPS) {
             const int64_t rb = ra + CT_WARPS;
             const bool oka = interior(ra), hasb = rb < rend, okb = hasb && interior(rb);
@@ -193,20 +222,33 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     pdl_trigger();                                  // the next pass may be scheduled
 }
 
-// Pass 2: exclusive scan of ntiles ints by one block of 1024 threads (four
-// consecutive entries per thread and round); total -> *d_count.
+// Pass 2: exclusive scan of ntiles ints by one block of 1024 threads, 32
+// consecutive entries per thread and round (eight 16-byte loads issued
+// together: one round up to 32 768 tiles, about 268 M cells); the total goes
+// to *d_count.  tile_count is 16-byte aligned (the workspace start).
 __global__ void __launch_bounds__(1024)
 k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict__ d_count) {
     __shared__ long long wsum[32];
     pdl_wait();                                     // pass 1 complete
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long carry = 0;
-    for (int64_t b0 = 0; b0 < ntiles; b0 += 4096) {
-        const int64_t i0 = b0 + 4 * (int64_t)threadIdx.x;
-        int v[4];
+    for (int64_t b0 = 0; b0 < ntiles; b0 += 32 * 1024) {
+        const int64_t i0 = b0 + 32 * (int64_t)threadIdx.x;
+        const bool full = i0 + 32 <= ntiles;
+        int v[32];
+        if (full) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = i0 + j < ntiles ? tile_count[i0 + j] : 0;
-        const long long own = (long long)v[0] + v[1] + v[2] + v[3];
+            for (int j = 0; j < 8; ++j) {
+                const int4 x = reinterpret_cast<const int4*>(tile_count + i0)[j];
+                v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = i0 + j < ntiles ? tile_count[i0 + j] : 0;
+        }
+        int own = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) own += v[j];
         long long x = own;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -226,10 +268,22 @@ k_compact_scan(int* __restrict__ tile_count, int64_t ntiles, int64_t* __restrict
         }
         __syncthreads();
         long long run = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - own;
+        if (full) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (i0 + j < ntiles) tile_count[i0 + j] = (int)run;
-            run += v[j];
+            for (int j = 0; j < 8; ++j) {
+                int4 o4;
+                o4.x = (int)run; run += v[4 * j];
+                o4.y = (int)run; run += v[4 * j + 1];
+                o4.z = (int)run; run += v[4 * j + 2];
+                o4.w = (int)run; run += v[4 * j + 3];
+                reinterpret_cast<int4*>(tile_count + i0)[j] = o4;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (i0 + j < ntiles) tile_count[i0 + j] = (int)run;
+                run += v[j];
+            }
         }
         carry += wsum[31];
         __syncthreads();
@@ -376,6 +430,29 @@ k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restric
     const int64_t t0 = (int64_t)blockIdx.x * CT_WARPS;
     pdl_wait();                                     // the passes before complete
     const int64_t t = t0 + warp;
+    const bool live = t < ntiles;
+    const int64_t rbeg = t * R;
+    const int nr = live ? (int)(rbeg + R < rows ? R : rows - rbeg) : 0;
+    const unsigned wpr = ((unsigned)nx + 31u) >> 5;
+    const int nw = nr * (int)wpr;
+    const unsigned* tb = bits + rbeg * (int64_t)wpr;
+    const bool al = ((rbeg * (int64_t)wpr) & 3) == 0;
+    // the lane's 8 words from word wl of the tile (none past the tile's end)
+    auto words = [&](unsigned (&b)[8], int wl) {
+        if (al && wl + 8 <= nw) {
+            const int4 x = __ldg(reinterpret_cast<const int4*>(tb + wl));
+            const int4 y = __ldg(reinterpret_cast<const int4*>(tb + wl + 4));
+            b[0] = x.x; b[1] = x.y; b[2] = x.z; b[3] = x.w;
+            b[4] = y.x; b[5] = y.y; b[6] = y.z; b[7] = y.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) b[k] = wl + k < nw ? __ldg(tb + wl + k) : 0u;
+        }
+    };
+    // the first 256 words of the tile are loaded before the tile counts are
+    // summed (the whole tile for rows of up to 256 cells): one round trip
+    unsigned b[8];
+    words(b, 8 * lane);
     long long base = 0;
     int tcount = 0;
     if (fused) {
@@ -402,32 +479,17 @@ k_compact_emit(int nx, int R, int64_t rows, int64_t ntiles, const int* __restric
         tcount = __shfl_sync(0xffffffffu, cj, warp);
         if (t == ntiles - 1 && lane == 0) *d_count = base + tcount;
     } else {
-        if (t >= ntiles) return;
+        if (!live) return;
         base = __ldg(tiles + t);
         const long long next = t + 1 < ntiles ? (long long)__ldg(tiles + t + 1) : *d_count;
         tcount = (int)(next - base);
     }
-    if (t >= ntiles || tcount == 0) return;
-    const int64_t rbeg = t * R;
-    const int nr = (int)(rbeg + R < rows ? R : rows - rbeg);
-    const unsigned wpr = ((unsigned)nx + 31u) >> 5;
-    const int nw = nr * (int)wpr;
-    const unsigned* tb = bits + rbeg * (int64_t)wpr;
-    const bool al = ((rbeg * (int64_t)wpr) & 3) == 0;
+    if (!live || tcount == 0) return;
     const unsigned invw = wpr > 1u ? 0xFFFFFFFFu / wpr + 1u : 0u;
     long long pos = base;
     for (int w0 = 0; w0 < nw; w0 += 256) {
         const int wl = w0 + 8 * lane;
-        unsigned b[8];
-        if (al && wl + 8 <= nw) {
-            const int4 x = __ldg(reinterpret_cast<const int4*>(tb + wl));
-            const int4 y = __ldg(reinterpret_cast<const int4*>(tb + wl + 4));
-            b[0] = x.x; b[1] = x.y; b[2] = x.z; b[3] = x.w;
-            b[4] = y.x; b[5] = y.y; b[6] = y.z; b[7] = y.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) b[k] = wl + k < nw ? __ldg(tb + wl + k) : 0u;
-        }
+        if (w0 > 0) words(b, wl);
         int c = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) c += __popc(b[k]);

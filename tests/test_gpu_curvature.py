@@ -52,7 +52,12 @@ def _compact(dev, p):
                                    # > 4096 tiles: the separate scan launch, with the vector
                                    # loads and with the scalar ones (odd nx), and with rows of
                                    # 30 cells, which keep no bits (the recounting write pass)
-                                   (520, 256, 256), (500, 257, 257), (2000, 600, 30)])
+                                   (520, 256, 256), (500, 257, 257), (2000, 600, 30),
+                                   # rows of more than 512 cells (the count pass cuts them into
+                                   # 512-cell segments): two, four and a partial last segment,
+                                   # then with the scan launch, then 32 769 tiles (two scan rounds)
+                                   (5, 9, 1024), (4, 6, 2048), (7, 5, 1540), (300, 120, 1024),
+                                   (3, 10923, 4100)])
 def test_compaction_bit_exact(dev, orc, shape):
     rng = np.random.default_rng(sum(shape))
     p = rng.random(shape).astype(np.float32)
