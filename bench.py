@@ -663,6 +663,19 @@ def section_curvature(dev, pk, steps, pp=None):
     secc = timed_cold(compact, steps, s, flush)
     out["compact_cold"] = {"ms": secc * 1e3, "hbm_gbs": cbytes / secc / 1e9,
                            "hbm_frac": frac(cbytes / secc / 1e9, pk["hbm_gbs"])}
+    # the plain streaming read of the same field from the same cache states
+    # (plic_read_probe): the fastest any pass reading the field once can go.
+    # Cold, the flush leaves L2 full of dirty lines whose write-back shares
+    # HBM with the read
+    sink = torch.zeros(1, device=dev)
+    rd = lambda: plic.read_probe(phi, sink)  # noqa: E731
+    secr, _ = timed_graph(rd, steps, 3, s)
+    secrc = timed_cold(rd, steps, s, flush)
+    out["read_ceiling"] = {"warm_ms": secr / steps * 1e3, "cold_ms": secrc * 1e3,
+                           "compact_warm_frac": (secr / steps) / (sec / steps),
+                           "compact_cold_frac": secrc / secc,
+                           "how": "plic_read_probe of the field (one wave of blocks, four 16-byte "
+                                  "loads per thread and trip), timed like the compaction"}
     m_mean = mean_interface_neighbours([(phi, it, k)])
     for fit, name in FITS:
         sec, _ = timed_graph(lambda: plic.curvature(phi, it, kappa=kap, flags=fit), steps, 3, s)
@@ -710,9 +723,11 @@ def section_curvature(dev, pk, steps, pp=None):
     kb = int(cnt2.item())
     secb = timed(cb, steps, 2, s) / steps
     bb = big.numel() * 4 + kb * 4
+    secbr = timed(lambda: plic.read_probe(big, sink), steps, 2, s) / steps
     out["compact_1GiB"] = {"field": "512 x 512 x 1024 (the 256^3 field tiled)", "interface_cells": kb,
                            "ms": secb * 1e3, "hbm_gbs": bb / secb / 1e9,
-                           "hbm_frac": frac(bb / secb / 1e9, pk["hbm_gbs"])}
+                           "hbm_frac": frac(bb / secb / 1e9, pk["hbm_gbs"]),
+                           "read_ceiling_ms": secbr * 1e3, "read_ceiling_frac": secbr / secb}
     del big, idxb, wsb, flush
     torch.cuda.empty_cache()
     return out
@@ -987,9 +1002,11 @@ def run_case(args):
             k = int(cnt.item())
             plic.curvature(phi, idx[:k].contiguous())
     elif args.case == "compact":
-        # the 256^3 curvature field tiled to 256 x 512 x 512 (256 MiB, twice L2)
+        # the 256^3 curvature field tiled to nz, ny, nx = 256, 256, 1024 (256 MiB,
+        # twice L2): rows of 1024 cells (the count pass's 512-cell segments) and
+        # 8192 tiles (the scan launch)
         phi, _ = synth.curvature_field(seed=3, edge=256, device=dev)
-        big = phi.repeat(1, 2, 2)
+        big = phi.repeat(1, 1, 4)
         idx = torch.empty(big.numel() // 8, dtype=torch.int32, device=dev)
         for _ in range(args.steps):
             plic.interface_compact(big, idx=idx)
@@ -1034,6 +1051,11 @@ def summary(line, sec):
     out["curv256_cold_us"] = None if g(c, "curvature_cold", "ms") is None else round(c["curvature_cold"]["ms"] * 1e3, 2)
     out["compact256_cold_hbm_frac"] = g(c, "compact_cold", "hbm_frac")
     out["compact1GiB_hbm_frac"] = g(c, "compact_1GiB", "hbm_frac")
+    # the compaction's time against the plain read of the same field from the
+    # same cache state (warm 256^3, cold 256^3, 1 GiB)
+    out["compact_vs_read"] = [g(c, "read_ceiling", "compact_warm_frac"),
+                              g(c, "read_ceiling", "compact_cold_frac"),
+                              g(c, "compact_1GiB", "read_ceiling_frac")]
     out["compact_plus_curv_cold_us"] = (None if g(c, "compact_plus_curvature_cold", "ms") is None
                                         else round(c["compact_plus_curvature_cold"]["ms"] * 1e3, 2))
     bt = sec.get("batched_64_fields", {})

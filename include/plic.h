@@ -379,6 +379,18 @@ plic_status plic_host_device_pointer(const void *host_ptr, void **dev_ptr);
  * PLIC_ERR_ALIGN, PLIC_ERR_CUDA. */
 plic_status plic_pipe_probe(int kind, int iters, float *d_sink, int64_t *ops, void *stream);
 
+/* plic_read_probe -- the plain streaming read of n floats at buf (device,
+ * 16-byte aligned), for the memory side of the kernels' rooflines (the paper
+ * has no counterpart): one launch on `stream` of one wave of resident blocks,
+ * each thread issuing four independent 16-byte loads per trip of a
+ * grid-stride loop.  Timed with CUDA events from a given cache state (the
+ * buffer in L2, or L2 flushed), it is the fastest that a pass reading the
+ * buffer once can go from that state.  d_sink: a device float written only in
+ * the impossible event that keeps the loads alive.  Errors: PLIC_ERR_ARG
+ * (n < 0, null pointers), PLIC_ERR_ALIGN (buf not 16-byte aligned),
+ * PLIC_ERR_CUDA. */
+plic_status plic_read_probe(const float *buf, int64_t n, float *d_sink, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

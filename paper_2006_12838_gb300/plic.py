@@ -82,6 +82,7 @@ def load():
             "plic_offset_roundtrip": [P, P, P, P, P, P, I64, I32, I32, U32, P, P],
             "plic_sphere_offset": [P, P, I64, I32, P],
             "plic_pipe_probe": [I32, I32, P, ctypes.POINTER(I64), P],
+            "plic_read_probe": [P, I64, P, P],
         }
         for name, args in sigs.items():
             f = getattr(L, name, None)
@@ -437,3 +438,12 @@ def pipe_probe(kind, iters, sink, stream=None) -> int:
     _check(L.plic_pipe_probe(PROBES[kind], int(iters), _ptr(sink), ctypes.byref(ops),
                              _stream(sink, stream)), "plic_pipe_probe")
     return int(ops.value)
+
+
+def read_probe(buf, sink, stream=None):
+    """Launch the plain streaming read of the float32 tensor ``buf`` (the
+    fastest one-pass read from the cache state it finds; time it with CUDA
+    events).  ``sink``: a CUDA float tensor of at least one element."""
+    _cuda(buf, sink, dtype=torch.float32)
+    _check(load().plic_read_probe(_ptr(buf), buf.numel(), _ptr(sink), _stream(buf, stream)),
+           "plic_read_probe")

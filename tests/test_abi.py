@@ -44,7 +44,8 @@ def test_every_declared_symbol_is_exported(lib):
 # entry points with no counterpart in the paper (sizes, status text, version,
 # host-memory addressing)
 PLUMBING = {"plic_workspace_bytes", "plic_curv_bwd_workspace_bytes", "plic_status_string",
-            "plic_last_error", "plic_abi_version", "plic_host_device_pointer", "plic_pipe_probe"}
+            "plic_last_error", "plic_abi_version", "plic_host_device_pointer", "plic_pipe_probe",
+            "plic_read_probe"}
 
 
 # deployment variants of a compute entry: no passage of the paper defines
@@ -124,6 +125,12 @@ def test_host_side_argument_checks(lib):
     assert b"limit" in lib.plic_last_error()
     assert lib.vof_interface_compact_noalloc(ok, -1, 8, 8, ok, 10, ok, None) == ERR_ARG
     assert lib.vof_interface_compact_noalloc(ok, 8, 8, 8, ok, 10, None, None) == ERR_ARG
+    # read probe: negative size, null sink, unaligned buffer (no launch)
+    assert lib.plic_read_probe(ok, -1, ok, None) == ERR_ARG
+    assert lib.plic_read_probe(ok, 16, None, None) == ERR_ARG
+    assert lib.plic_read_probe(None, 16, ok, None) == ERR_ARG
+    assert lib.plic_read_probe(P(260), 16, ok, None) == ERR_ALIGN
+    assert lib.plic_read_probe(ok, 0, ok, None) == 0
     # host-mapped address query: null arguments
     out = ctypes.c_void_p()
     assert lib.plic_host_device_pointer(None, ctypes.byref(out)) == ERR_ARG

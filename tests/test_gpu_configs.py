@@ -174,3 +174,24 @@ def test_pipe_probes_run(dev):
     assert rates["ffma2"] >= 0.8 * rates["ffma"]
     assert all(v > 0 for v in rates.values())
     assert float(sink.item()) == 0.0
+
+
+def test_read_probe_runs(dev):
+    # the plain streaming read of the memory rooflines: a 256 MiB buffer (twice
+    # the L2) at a positive rate below twice the nominal HBM bandwidth; odd
+    # lengths take the tail loads
+    sink = torch.zeros(1, device=dev)
+    for n in (1 << 26, (1 << 20) + 3, 1, 5):
+        buf = torch.rand(n, device=dev)
+        plic.read_probe(buf, sink)
+        torch.cuda.synchronize()
+    buf = torch.rand(1 << 26, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    plic.read_probe(buf, sink)
+    b.record()
+    torch.cuda.synchronize()
+    gbs = buf.numel() * 4 / (a.elapsed_time(b) / 1e3) / 1e9
+    print("read probe %.0f GB/s" % gbs)
+    assert 500.0 < gbs < 16000.0
+    assert float(sink.item()) == 0.0

@@ -57,7 +57,11 @@ def _compact(dev, p):
                                    # 512-cell segments): two, four and a partial last segment,
                                    # then with the scan launch, then 32 769 tiles (two scan rounds)
                                    (5, 9, 1024), (4, 6, 2048), (7, 5, 1540), (300, 120, 1024),
-                                   (3, 10923, 4100)])
+                                   (3, 10923, 4100),
+                                   # the ballot layout of the bits (rows of >= 64 cells, nx % 4
+                                   # == 0): one partial chunk, tiles spanning many z planes
+                                   # (ny = 5 and 3 with 128 rows per tile), an exact chunk
+                                   (40, 5, 64), (9, 11, 68), (130, 3, 64), (6, 50, 128)])
 def test_compaction_bit_exact(dev, orc, shape):
     rng = np.random.default_rng(sum(shape))
     p = rng.random(shape).astype(np.float32)
