@@ -222,6 +222,80 @@ k_compact_count(const float* __restrict__ phi, int nx, int ny, int nz, int R, in
     pdl_trigger();                                  // the next pass may be scheduled
 }
 
+// Pass 1 for 16-byte aligned rows of 128 * 2^k cells (the power-of-two edges
+// of the workloads), streamlined: the tile is a run of 128-cell slots (spr =
+// nx / 128 per row, 2^lspr), slot s of the tile is row s >> lspr at column
+// (s & (spr - 1)) * 128, so no column test is needed and a slot's bit words
+// are contiguous; warp w takes slots 4 w + u + 32 k and issues the four
+// 16-byte loads per lane of a trip together.  A row's (y, z) is stepped from
+// the tile's first row (a division only where the tile wraps to the next z).
+// The bits are the nibble layout of the general pass (word x / 32 of a row,
+// bit x % 32), so pass 3 is the same.
+__global__ void __launch_bounds__(CT_THREADS, 8)
+k_compact_count_p2(const float* __restrict__ phi, int nx, int ny, int nz, int R, int64_t rows,
+                   int lspr, int* __restrict__ tile_count, unsigned* __restrict__ bits) {
+    pdl_wait();                                     // the kernel that wrote the field complete
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t rbeg = (int64_t)blockIdx.x * R;
+    const int nr = (int)(rbeg + R < rows ? R : rows - rbeg);
+    const int nslot = nr << lspr;
+    const unsigned smask = (1u << lspr) - 1u;
+    const unsigned z0 = (unsigned)rbeg / (unsigned)ny, y0 = (unsigned)rbeg - z0 * (unsigned)ny;
+    const float4* base = reinterpret_cast<const float4*>(phi + rbeg * nx) + lane;
+    unsigned* tb = bits + (rbeg * nx >> 5) + (lane >> 3);
+    const unsigned shl = 4u * (unsigned)(lane & 7);
+    const bool writer = (lane & 7) == 0;
+    // the columns x = 0 and x = nx - 1 are lane 0's first and lane 31's last
+    // component of a row's first and last slot
+    const unsigned first_clear = lane == 0 ? 1u : 0u, last_clear = lane == 31 ? 8u : 0u;
+    int cnt = 0;
+    for (int s0 = warp * 4; s0 < nslot; s0 += 4 * CT_WARPS) {
+        float4 v[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int sl = s0 + u;
+            const unsigned row = (unsigned)sl >> lspr;
+            unsigned y = y0 + row, z = z0;
+            if (y >= (unsigned)ny) {                // the tile wraps to the next z plane
+                const unsigned k = y / (unsigned)ny;
+                z += k;
+                y -= k * (unsigned)ny;
+            }
+            ok[u] = sl < nslot && y - 1u < (unsigned)ny - 2u && z - 1u < (unsigned)nz - 2u;
+            v[u] = ok[u] ? __ldg(base + 32 * sl) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int sl = s0 + u;
+            const unsigned col = (unsigned)sl & smask;
+            unsigned m = (unsigned)iface_bits(__float_as_uint(v[u].x)) |
+                         ((unsigned)iface_bits(__float_as_uint(v[u].y)) << 1) |
+                         ((unsigned)iface_bits(__float_as_uint(v[u].z)) << 2) |
+                         ((unsigned)iface_bits(__float_as_uint(v[u].w)) << 3);
+            m &= ~((col == 0u ? first_clear : 0u) | (col == smask ? last_clear : 0u));
+            m = ok[u] ? m : 0u;
+            cnt += __popc(m);
+            unsigned w = m << shl;
+            w |= __shfl_xor_sync(0xffffffffu, w, 1);
+            w |= __shfl_xor_sync(0xffffffffu, w, 2);
+            w |= __shfl_xor_sync(0xffffffffu, w, 4);
+            if (writer && sl < nslot) tb[4 * sl] = w;
+        }
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    __shared__ int ws[CT_WARPS];
+    if (lane == 0) ws[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < CT_WARPS; ++w) t += ws[w];
+        tile_count[blockIdx.x] = t;
+    }
+    pdl_trigger();                                  // the next pass may be scheduled
+}
+
 // Pass 2: exclusive scan of ntiles ints by one block of 1024 threads, 32
 // consecutive entries per thread and round (eight 16-byte loads issued
 // together: one round up to 32 768 tiles, about 268 M cells); the total goes
@@ -602,7 +676,19 @@ extern "C" plic_status vof_interface_compact(const float* phi, int nx, int ny, i
     if (nx >= 32 && tile_bytes + bits_bytes <= ws_bytes)
         bits = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + tile_bytes);
     const int vec = (nx % 4 == 0) && aligned(phi, 16);
-    cudaError_t e = launch_count(phi, nx, ny, nz, R, rows, nt, tiles, bits, vec, s);
+    // rows of 128 * 2^k cells: the streamlined count pass
+    int lspr = -1;
+    if (vec && bits && nx >= 128 && nx % 128 == 0 && ((nx / 128) & (nx / 128 - 1)) == 0)
+        for (lspr = 0; (128 << lspr) < nx; ++lspr) {}
+    cudaError_t e;
+    if (lspr >= 0) {
+        void* args[] = {(void*)&phi, (void*)&nx, (void*)&ny, (void*)&nz, (void*)&R, (void*)&rows,
+                        (void*)&lspr, (void*)&tiles, (void*)&bits};
+        e = launch_after(reinterpret_cast<const void*>(&k_compact_count_p2), dim3((unsigned)nt),
+                         dim3(CT_THREADS), args, s);
+    } else {
+        e = launch_count(phi, nx, ny, nz, R, rows, nt, tiles, bits, vec, s);
+    }
     // up to CT_FUSED_SCAN_TILES tiles pass 3 sums the counts of the tiles
     // before each block (at most that many L2 reads per block); beyond, one
     // block scans them first
