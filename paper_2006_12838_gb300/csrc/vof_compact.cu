@@ -6,7 +6,10 @@
 // whole x-rows (about 8192 cells):
 //   1. k_compact_count : each block counts the interface cells of its tile and,
 //                        with room in the workspace, stores the tile's
-//                        interface bits (one word per 32 cells of a row).
+//                        interface bits (one word per 32 cells of a row);
+//                        k_compact_count_p2 does the same for 16-byte aligned
+//                        rows of 128 * 2^k cells with slot arithmetic in
+//                        shifts and masks.
 //   2. k_compact_scan  : one block turns the per-tile counts into exclusive
 //                        offsets (in place) and writes the total to *d_count;
 //                        only for fields of more than 4096 tiles (about 33 M
