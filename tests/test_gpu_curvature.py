@@ -61,7 +61,10 @@ def _compact(dev, p):
                                    # the ballot layout of the bits (rows of >= 64 cells, nx % 4
                                    # == 0): one partial chunk, tiles spanning many z planes
                                    # (ny = 5 and 3 with 128 rows per tile), an exact chunk
-                                   (40, 5, 64), (9, 11, 68), (130, 3, 64), (6, 50, 128)])
+                                   (40, 5, 64), (9, 11, 68), (130, 3, 64), (6, 50, 128),
+                                   # the slot count pass (rows of 128 * 2^k cells) with tiles
+                                   # that wrap over several z planes (ny = 3, 5)
+                                   (7, 3, 512), (9, 5, 128), (5, 7, 256)])
 def test_compaction_bit_exact(dev, orc, shape):
     rng = np.random.default_rng(sum(shape))
     p = rng.random(shape).astype(np.float32)
